@@ -1,0 +1,340 @@
+#!/usr/bin/env python3
+"""Benchmark of the Wilson hopping term on GB300 (one JSON line on stdout).
+
+Headline workload: the FP32 even-odd hopping term on a 32^3 x 64 lattice
+(weak-field links U = exp(0.3 i H) stored with 12 reals, complex64 Gaussian
+spinor, kappa = 0.1350, periodic x,y,z / antiperiodic t).  One step is 100
+back-to-back applications alternating D_oe and D_eo (ping-pong fields).
+Rates: 1320 flops per output site (Sec. 5 of the paper) and 576 compulsory
+bytes per output site (spinor in 96 B + 8 links x 48 B + spinor out 96 B).
+
+Also reported: the end-to-end rate through the C ABI with host buffers
+(spinor copied in from pinned host memory and out again every step), the
+FP64 CPU oracle on the host cores, and a CG time-to-solution comparison on
+the 24^3 x 48 lattice (mixed F16/BF16-inner vs plain FP64, true residual
+1e-10).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_0710_2442_gb300 import inputs, model  # noqa: E402
+
+METRIC = "Dslash GFlop/s & HBM GB/s (% roofline); CG time-to-1e-10 mixed vs FP64"
+WORKLOAD = "dslash_eo_f32_32^3x64"
+L2_NOTE = ("inputs larger than L2: each application streams 403 MB of links plus 2 x 101 MB of spinors "
+           "through the 126 MB L2")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-solver", action="store_true", help="skip the CG comparison block")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--apps", type=int, default=None, help="applications per step (default 100)")
+    return ap.parse_args()
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d.get("hbm_gbs", 6800.0)), "measured"
+    return 6800.0, "fallback"
+
+
+# ---------------------------------------------------------------------------
+# distributed bookkeeping (independent replicas; timing only)
+# ---------------------------------------------------------------------------
+def dist_init():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch
+        import torch.distributed as dist
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if torch.cuda.is_available():
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend=backend)
+    return ws, rank, local
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x: float, ws: int) -> float:
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if torch.cuda.is_available() else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.device = device
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.device), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (FileNotFoundError, OSError):
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        rows = []
+        if self.path and os.path.exists(self.path):
+            for line in open(self.path):
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 8:
+                    rows.append(parts)
+            os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(r[0]) for r in rows if r[0].replace(".", "").isdigit()]
+        smax = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[4 + i].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+def make_c2_fields():
+    cfg = inputs.WORKLOADS[WORKLOAD]
+    dims = cfg["dims"]
+    U = inputs.gauge_field(dims, cfg["gauge"], eps=cfg["eps"], seed=cfg["gauge_seed"])
+    Vh = inputs.volume(dims) // 2
+    src = inputs.gaussian_spinor(Vh, seed=cfg["spinor_seed"]).astype(np.complex64).astype(np.complex128)
+    return cfg, dims, U, src
+
+
+def run_ours(args, ws, rank, local, fields):
+    import torch
+    from paper_0710_2442_gb300 import build, wilson as w
+    build.build()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    cfg, dims, U, src = fields
+    Vh = inputs.volume(dims) // 2
+    apps = args.apps or cfg["applications"]
+    L = w.lattice(dims)
+    stream = torch.cuda.current_stream(dev)
+    g = w.Gauge(U, L, w.WILSON_F32, 12, stream)
+    even = w.Spinor(L, w.WILSON_EVEN, w.WILSON_F32)
+    odd = w.Spinor(L, w.WILSON_ODD, w.WILSON_F32)
+    src_dev = torch.from_numpy(src).to(dev)
+    even.load(src_dev, stream)
+
+    def step():
+        for k in range(apps):
+            if k % 2 == 0:
+                w.wilson_dslash_h(odd, g, even, 0.0, w.WILSON_OP_HOP, stream)
+            else:
+                w.wilson_dslash_h(even, g, odd, 0.0, w.WILSON_OP_HOP, stream)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize(dev)
+    start = torch.cuda.Event(enable_timing=True)
+    stop = torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        barrier(ws)
+        torch.cuda.synchronize(dev)
+        start.record(stream)
+        for _ in range(args.steps):
+            step()
+        stop.record(stream)
+        torch.cuda.synchronize(dev)
+        barrier(ws)
+    ms = start.elapsed_time(stop)
+    ms = max_over_ranks(ms, ws)
+    clocks = clk.summary()
+    launches = args.steps * apps
+    t_launch = ms / 1e3 / launches
+    flops = model.FLOPS_PER_SITE * Vh
+    comp_bytes = model.compulsory_bytes_per_site("f32", 12, eo=True) * Vh
+    gflops = flops * launches * ws / (ms / 1e3) / 1e9
+    peak, peak_kind = measured_peaks()
+    achieved = comp_bytes / t_launch / 1e9
+
+    # end to end through the C ABI with host buffers
+    host_in = torch.from_numpy(src).pin_memory()
+    host_out = torch.empty_like(host_in).pin_memory()
+    e2e_steps = max(1, min(args.steps, 5))
+    for _ in range(1):
+        even.load(host_in, stream)
+        step()
+        (odd if apps % 2 else even).store(host_out, stream)
+    torch.cuda.synchronize(dev)
+    barrier(ws)
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        even.load(host_in, stream)
+        step()
+        (odd if apps % 2 else even).store(host_out, stream)
+    torch.cuda.synchronize(dev)
+    t_e2e = max_over_ranks(time.perf_counter() - t0, ws)
+    e2e = {"value": round(flops * apps * e2e_steps * ws / t_e2e / 1e9, 2), "unit": "GFlop/s",
+           "h2d_bytes_per_step": int(host_in.numel() * 16), "d2h_bytes_per_step": int(host_out.numel() * 16),
+           "steps": e2e_steps, "api": "wilson_spinor_import(host) + 100 x wilson_dslash_h + wilson_spinor_export(host)"}
+    del src_dev
+    for h in (even, odd, g):
+        h.close()
+    torch.cuda.synchronize(dev)
+
+    line = {
+        "metric": METRIC, "value": round(gflops, 2), "unit": "GFlop/s", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(ms / args.steps, 4), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "dims": list(dims), "links": "f32 12-real", "spinor": "f32",
+                   "kappa": cfg["kappa"], "applications_per_step": apps, "sites_per_application": Vh,
+                   "l2": L2_NOTE, "parallelism": "replicas" if ws > 1 else "single"},
+        "hbm_gbs": round(achieved * ws, 1),
+        "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                     "frac": round(achieved / peak, 4), "traffic": None, "peak_kind": peak_kind,
+                     "algorithmic_bytes_per_launch": comp_bytes, "launch_us": round(t_launch * 1e6, 2)},
+        "clocks": clocks, "e2e": e2e, "gpu_launches": launches,
+    }
+    if rank == 0 and not args.no_solver:
+        line["cg"] = run_solver_block(w, torch, dev, stream)
+    return line
+
+
+def run_solver_block(w, torch, dev, stream):
+    cfg = inputs.WORKLOADS["cg_mixed_24^3x48"]
+    dims = cfg["dims"]
+    U = inputs.gauge_field(dims, cfg["gauge"], eps=cfg["eps"], seed=cfg["gauge_seed"])
+    b = inputs.gaussian_spinor(dims, seed=cfg["spinor_seed"])
+    Ud = torch.from_numpy(U).to(dev)
+    bd = torch.from_numpy(b).to(dev)
+    L = w.lattice(dims)
+    res = {"workload": "cg_mixed_24^3x48", "kappa": cfg["kappa"], "tol": cfg["tol"]}
+    for name, prec in (("f64", w.WILSON_F64), ("f16", w.WILSON_F16), ("bf16", w.WILSON_BF16),
+                       ("f32", w.WILSON_F32)):
+        x = torch.zeros_like(bd)
+        p = w.solver_defaults(prec)
+        st = w.wilson_cg_solve(x, Ud, bd, L, cfg["kappa"], p, stream, check=False)
+        res[name] = {"seconds": round(st["seconds"], 4), "inner_iters": st["inner_iters"],
+                     "outer_iters": st["outer_iters"], "hops": st["hop_applications"],
+                     "true_rel_resid": st["true_rel_resid"], "rc": st["rc"]}
+    if res["f64"]["rc"] == 0 and res["f16"]["rc"] == 0:
+        res["speedup_f16_vs_f64"] = round(res["f64"]["seconds"] / res["f16"]["seconds"], 3)
+    return res
+
+
+# ---------------------------------------------------------------------------
+# the FP64 CPU oracle (CPU baseline and the reference arm)
+# ---------------------------------------------------------------------------
+def oracle_sample(dims, U, src, reps=1):
+    import oracle
+    oracle.build()
+    cores = oracle.num_threads()
+    Vh = inputs.volume(dims) // 2
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        oracle.dslash_eo(U, src, dims, 1)
+    t = time.perf_counter() - t0
+    return model.FLOPS_PER_SITE * Vh * reps / t / 1e9, cores, t
+
+
+def run_reference(args, ws, rank):
+    if rank != 0:
+        return None
+    cfg, dims, U, src = make_c2_fields()
+    oracle_sample(dims, U, src)  # build + first touch
+    vals = []
+    for _ in range(args.warmup):
+        oracle_sample(dims, U, src)
+    t_all = 0.0
+    for _ in range(args.steps):
+        v, cores, t = oracle_sample(dims, U, src)
+        vals.append(v)
+        t_all += t
+    Vh = inputs.volume(dims) // 2
+    value = model.FLOPS_PER_SITE * Vh * args.steps / t_all / 1e9
+    sample = (f"one FP64 application of the even-odd hopping term on the full 32^3x64 lattice per step "
+              f"(the workload's step is 100 F32 applications)")
+    return {"metric": METRIC, "value": round(value, 4), "unit": "GFlop/s", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(t_all / args.steps * 1e3, 2), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": {"workload": WORKLOAD, "dims": list(dims), "kappa": cfg["kappa"]},
+            "cpu_baseline": {"value": round(value, 4), "unit": "GFlop/s", "cores": cores, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": round(value, 4), "unit": "GFlop/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    args = parse()
+    ws, rank, local = dist_init()
+    if args.impl == "reference":
+        line = run_reference(args, ws, rank)
+        if line is not None:
+            print(json.dumps(line), flush=True)
+        return
+    fields = make_c2_fields()
+    line = run_ours(args, ws, rank, local, fields)
+    if rank == 0 and ws == 1 and not args.no_cpu:
+        cfg, dims, U, src = fields
+        v, cores, t = oracle_sample(dims, U, src)
+        line["cpu_baseline"] = {"value": round(v, 4), "unit": "GFlop/s", "cores": cores, "kind": "oracle",
+                                "sample": f"one FP64 even-odd application on the full 32^3x64 lattice "
+                                          f"({t:.1f} s of CPU time)"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

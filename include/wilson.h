@@ -1,0 +1,182 @@
+/*
+ * wilson.h -- C ABI of libwilson_gb300: the Wilson-Dirac hopping term, its
+ * even-odd (checkerboard) form and CG solves built on it, on one GB300 GPU.
+ *
+ * The operator (QCD on the Cell BE, Sec. 5, Eq. 3), in the convention this
+ * library uses ("(1-gamma) forward"):
+ *
+ *   (D_h psi)_x = sum_{mu=1..4} [ (1 - g_mu) eta_mu(x)      U_{x,mu}         psi_{x+mu}
+ *                               + (1 + g_mu) eta*_mu(x-mu)  U^dag_{x-mu,mu}  psi_{x-mu} ]
+ *
+ * Eq. 3 as printed in the paper puts (1 + g_mu) on the forward hop; the two
+ * are related by D_printed = g_5 D_h g_5.  g_mu are the DeGrand-Rossi gamma
+ * matrices (g_5 = diag(1,1,-1,-1)); mu = 1..4 are x, y, z, t.  eta_mu(x) is
+ * the boundary phase of direction mu when the forward hop from x wraps from
+ * x_mu = L_mu - 1 to 0; the backward hop that wraps takes its conjugate.
+ * The Wilson matrix is M = 1 - kappa D_h.
+ *
+ * Even-odd form: with parity p = (x+y+z+t) mod 2, D_h couples only opposite
+ * parities; D_{p,1-p} is the block from parity 1-p to parity p.  The Schur
+ * complement on parity p is Mhat_p = 1 - kappa^2 D_{p,1-p} D_{1-p,p}, and
+ * Mhat_p^dag = g_5 Mhat_p g_5.
+ *
+ * Canonical field layout (all "canon" pointers): complex numbers as
+ * interleaved (re, im) doubles,
+ *   spinor  [site][spin 0..3][colour 0..2]             24 doubles per site
+ *   gauge   [site][mu 0..3][row 0..2][col 0..2]         72 doubles per site
+ *   site    s = x + Lx*(y + Ly*(z + Lz*t))
+ *   half (parity-p) field: the sites of parity p, site s stored at s >> 1
+ *   (Vh = V/2 entries; needs even extents).
+ *
+ * Conventions of every entry point:
+ *   - returns a wilson_status; never throws; wilson_last_error() gives a
+ *     thread-local message for the last failure on the calling thread;
+ *   - the caller owns every field pointer it passes; the library owns the
+ *     handles it creates and its internal workspace;
+ *   - "stream" is a cudaStream_t (NULL = legacy default stream); operator
+ *     calls are asynchronous on it; solves synchronise it before returning;
+ *   - validation: all extents >= 2 and even, V < 2^31, non-null pointers,
+ *     finite kappa, |phase| = 1 within 1e-12.  Violations give WILSON_ERR_ARG
+ *     and launch nothing.
+ *
+ * There is no CPU fallback: every call runs on the current CUDA device and
+ * returns WILSON_ERR_CUDA if there is none.
+ */
+#ifndef WILSON_GB300_H
+#define WILSON_GB300_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    WILSON_OK = 0,
+    WILSON_ERR_ARG = 1,         /* invalid argument; nothing was launched        */
+    WILSON_ERR_CUDA = 2,        /* a CUDA call failed                            */
+    WILSON_ERR_OOM = 3,         /* device allocation failed                      */
+    WILSON_ERR_NOCONV = 4,      /* solve stopped at maxiter / max_restarts       */
+    WILSON_ERR_TIMEOUT = 5,     /* a bounded device-side wait ran out            */
+    WILSON_ERR_NUMERIC = 6,     /* NaN or Inf met in a reduction                 */
+    WILSON_ERR_UNSUPPORTED = 7  /* valid but not implemented combination         */
+} wilson_status;
+
+typedef enum { WILSON_F64 = 0, WILSON_F32 = 1, WILSON_F16 = 2, WILSON_BF16 = 3 } wilson_prec;
+
+typedef enum {
+    WILSON_OP_HOP = 0,        /* D_h (full field) or D_{p,1-p} (half field)                  */
+    WILSON_OP_M = 1,          /* M = 1 - kappa D_h; full fields only                          */
+    WILSON_OP_SCHUR = 2,      /* Mhat_p = 1 - kappa^2 D_{p,1-p} D_{1-p,p}; half fields only   */
+    WILSON_OP_SCHUR_DAG = 3   /* Mhat_p^dag = g_5 Mhat_p g_5; half fields only                */
+} wilson_op;
+
+typedef enum { WILSON_EVEN = 0, WILSON_ODD = 1, WILSON_FULL = 2 } wilson_subset;
+
+typedef struct {
+    int dims[4];            /* Lx, Ly, Lz, Lt (t = the 4-direction)                      */
+    double bc_phase[4][2];  /* (re, im) boundary phase per direction; periodic x,y,z and */
+                            /* antiperiodic t is {1,0},{1,0},{1,0},{-1,0}                 */
+} wilson_lattice;
+
+/* ---------------------------------------------------------------------- */
+/* Stateless calls on canonical complex128 device fields (Sec. 5, Eq. 3).  */
+/* Computed in FP64 with 18-real links.  Each call packs its inputs into   */
+/* the library's workspace, so it allocates on first use.                  */
+/* ---------------------------------------------------------------------- */
+
+/* out = D_h in (op = HOP) or M in (op = M), full lattice.
+ * out, in: V spinors (canonical, device); gauge: 4V links (canonical, device).
+ * out must not overlap in. */
+int wilson_dslash(double* out, const double* gauge, const double* in, const wilson_lattice* L,
+                  double kappa, int op, void* stream);
+
+/* Half-lattice form.  op = HOP: out (parity out_parity) = D_{p,1-p} in (parity 1-p).
+ * op = SCHUR / SCHUR_DAG: out and in are both parity out_parity.
+ * out, in: V/2 spinors (canonical half fields, device). */
+int wilson_dslash_eo(double* out, const double* gauge, const double* in, const wilson_lattice* L,
+                     int out_parity, double kappa, int op, void* stream);
+
+/* ---------------------------------------------------------------------- */
+/* Solver (not in the paper, which only notes that an iterative solver     */
+/* repeats Eq. 3): CG on the normal equations of the even Schur complement */
+/*   bhat_e = b_e + kappa D_eo b_o;  Mhat^dag Mhat x_e = Mhat^dag bhat_e;   */
+/*   x_o = b_o + kappa D_oe x_e,                                           */
+/* stopped when the true relative residual |b - M x| / |b| <= tol,          */
+/* recomputed in FP64 on the GPU.  With inner = F32/F16/BF16 the CG runs in */
+/* that storage precision (FP32 arithmetic) inside an FP64 defect          */
+/* correction; with inner = F64 it is plain FP64 CG.                       */
+/* ---------------------------------------------------------------------- */
+typedef struct {
+    int inner;              /* wilson_prec of the inner CG (F64 = plain FP64 CG)            */
+    int recon;              /* link storage of the inner operator: 12 or 18 reals           */
+    double tol;             /* target true relative residual, e.g. 1e-10                    */
+    int maxiter;            /* cap on inner CG iterations over the whole solve              */
+    int max_restarts;       /* cap on FP64 outer corrections                                */
+    double delta;           /* inner reduction per outer correction (0 = default per prec)  */
+    int use_initial_guess;  /* 1: x holds the initial guess on entry                        */
+    int reliable;           /* 1: reliable updates (keep the CG direction), 0: restart CG   */
+} wilson_solver_params;
+
+typedef struct {
+    int status;               /* wilson_status of the solve                          */
+    int outer_iters;          /* FP64 corrections (residual recomputations)          */
+    int inner_iters;          /* CG iterations in total                              */
+    int hop_applications;     /* half-lattice hopping-term applications, all precisions */
+    double true_rel_resid;    /* |b - M x| / |b|, FP64, recomputed at the end       */
+    double seconds;           /* wall time of the solve (device-synchronised)        */
+} wilson_solve_stats;
+
+/* Default parameters for an inner precision (tol 1e-10). */
+wilson_solver_params wilson_solver_defaults(int inner);
+
+/* x, b: V spinors (canonical, device); gauge: 4V links (canonical, device).
+ * Returns WILSON_OK, or WILSON_ERR_NOCONV with x holding the last iterate. */
+int wilson_cg_solve(double* x, const double* gauge, const double* b, const wilson_lattice* L,
+                    double kappa, const wilson_solver_params* p, wilson_solve_stats* st, void* stream);
+
+/* ---------------------------------------------------------------------- */
+/* Handles: prepared fields for repeated (timed) applications.             */
+/* A gauge handle holds the links in the site-vectorised structure-of-     */
+/* arrays layout of one precision with 12 (two rows; the third rebuilt as  */
+/* the conjugate cross product, SU(3) only) or 18 reals per link.  A spinor */
+/* handle holds one subset (even, odd or full) of nrhs fields in one       */
+/* precision; F16/BF16 spinors carry one FP32 scale per site and rhs.      */
+/* ---------------------------------------------------------------------- */
+typedef struct wilson_gauge_s wilson_gauge;
+typedef struct wilson_spinor_s wilson_spinor;
+
+/* canon: 4V links, canonical complex128, host or device memory. */
+int wilson_gauge_create(wilson_gauge** g, const double* canon, const wilson_lattice* L, int prec,
+                        int recon, void* stream);
+int wilson_gauge_destroy(wilson_gauge* g);
+
+/* subset: wilson_subset; nrhs >= 1 fields packed per site. */
+int wilson_spinor_create(wilson_spinor** s, const wilson_lattice* L, int subset, int nrhs, int prec);
+int wilson_spinor_destroy(wilson_spinor* s);
+/* Bytes of device memory the handle holds. */
+long long wilson_spinor_bytes(const wilson_spinor* s);
+
+/* canon: nrhs fields back to back, each V (full) or V/2 (half) canonical
+ * spinors; host or device memory (host memory is staged through the
+ * library's workspace; pinned host memory copies fastest). */
+int wilson_spinor_import(wilson_spinor* s, const double* canon, void* stream);
+int wilson_spinor_export(const wilson_spinor* s, double* canon, void* stream);
+
+/* Apply an operator to prepared fields of matching lattice and precision
+ * (the gauge may be F32-12 for F32 spinors, or the spinor precision).
+ *   HOP:  full -> full (D_h) or parity 1-p -> parity p (D_{p,1-p})
+ *   M:    full -> full
+ *   SCHUR, SCHUR_DAG: parity p -> parity p (uses a workspace field)
+ * All nrhs fields are applied; out must not be in. */
+int wilson_dslash_h(wilson_spinor* out, const wilson_gauge* g, const wilson_spinor* in, double kappa,
+                    int op, void* stream);
+
+/* ---------------------------------------------------------------------- */
+/* Errors and version                                                      */
+/* ---------------------------------------------------------------------- */
+const char* wilson_last_error(void);
+int wilson_version(void);   /* major*10000 + minor*100 + patch */
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* WILSON_GB300_H */

@@ -1,0 +1,458 @@
+// api.cu -- the extern "C" entry points declared in include/wilson.h.
+//
+// Every entry point validates its arguments on the host, catches every C++
+// exception, records a thread-local message and returns a wilson_status.
+#include <cmath>
+#include <cstring>
+#include <memory>
+#include <mutex>
+#include <string>
+
+#include "../../include/wilson.h"
+#include "solver.h"
+
+using namespace wl;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+int fail(int code, const std::string& msg) {
+    g_last_error = msg;
+    return code;
+}
+
+template <class F>
+int guarded(F&& f) {
+    try {
+        f();
+        g_last_error.clear();
+        return WILSON_OK;
+    } catch (const Error& e) {
+        return fail(e.code, e.what());
+    } catch (const std::bad_alloc&) {
+        return fail(WILSON_ERR_OOM, "host allocation failed");
+    } catch (const std::exception& e) {
+        return fail(WILSON_ERR_CUDA, e.what());
+    } catch (...) {
+        return fail(WILSON_ERR_CUDA, "unknown exception");
+    }
+}
+
+// Checks shared by all entry points; returns the geometry.
+Geom checked_geom(const wilson_lattice* L) {
+    WL_REQUIRE(L != nullptr, "lattice descriptor is NULL");
+    long long V = 1;
+    for (int mu = 0; mu < 4; mu++) {
+        const int d = L->dims[mu];
+        WL_REQUIRE(d >= 2 && (d % 2) == 0, "every lattice extent must be even and >= 2");
+        V *= d;
+        const double re = L->bc_phase[mu][0], im = L->bc_phase[mu][1];
+        WL_REQUIRE(std::isfinite(re) && std::isfinite(im) && std::fabs(re * re + im * im - 1.0) <= 1e-12,
+                   "boundary phases must have unit modulus");
+    }
+    WL_REQUIRE(V < (1LL << 31), "lattice volume must be below 2^31 sites");
+    return make_geom(L->dims, L->bc_phase);
+}
+
+void check_ptr(const void* p, const char* what) {
+    WL_REQUIRE(p != nullptr, std::string(what) + " is NULL");
+    WL_REQUIRE((reinterpret_cast<uintptr_t>(p) & 15) == 0, std::string(what) + " is not 16-byte aligned");
+}
+
+void check_device() {
+    int n = 0;
+    cudaError_t e = cudaGetDeviceCount(&n);
+    if (e != cudaSuccess || n == 0) throw Error(WILSON_ERR_CUDA, "no CUDA device available");
+}
+
+bool is_device_ptr(const void* p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+Prec to_prec(int p) {
+    WL_REQUIRE(p >= WILSON_F64 && p <= WILSON_BF16, "unknown precision");
+    return static_cast<Prec>(p);
+}
+
+// Library-owned staging for host-side canonical fields.
+struct Staging {
+    std::mutex m;
+    DevBuf buf;
+};
+Staging& staging() {
+    static Staging s;
+    return s;
+}
+
+// Copy a canonical field to the device if it lives in host memory; returns a
+// device pointer valid until the next staging call on the stream.
+const double* device_view(const double* p, size_t bytes, DevBuf& tmp, cudaStream_t st) {
+    if (is_device_ptr(p)) return p;
+    tmp.ensure(bytes);
+    WL_CUDA(cudaMemcpyAsync(tmp.p, p, bytes, cudaMemcpyHostToDevice, st));
+    return tmp.as<const double>();
+}
+
+// Internal stream used by the solver for graph capture (the caller's stream
+// may be the legacy default stream, which cannot be captured).
+struct SolveStream {
+    cudaStream_t s = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+};
+SolveStream& solve_stream() {
+    static thread_local SolveStream ss;
+    if (!ss.s) {
+        WL_CUDA(cudaStreamCreateWithFlags(&ss.s, cudaStreamNonBlocking));
+        WL_CUDA(cudaEventCreateWithFlags(&ss.e0, cudaEventDisableTiming));
+        WL_CUDA(cudaEventCreateWithFlags(&ss.e1, cudaEventDisableTiming));
+    }
+    return ss;
+}
+
+}  // namespace
+
+struct wilson_gauge_s {
+    GaugeField f;
+};
+struct wilson_spinor_s {
+    SpinorField f;
+    Geom g;
+};
+
+// ---------------------------------------------------------------------------
+extern "C" {
+
+const char* wilson_last_error(void) { return g_last_error.c_str(); }
+
+int wilson_version(void) { return 100; }
+
+wilson_solver_params wilson_solver_defaults(int inner) {
+    wilson_solver_params p;
+    p.inner = inner;
+    p.recon = inner == WILSON_F64 ? 18 : 12;
+    p.tol = 1e-10;
+    p.maxiter = 100000;
+    p.max_restarts = 1000;
+    p.delta = 0.0;
+    p.use_initial_guess = 0;
+    p.reliable = 1;
+    return p;
+}
+
+int wilson_dslash(double* out, const double* gauge, const double* in, const wilson_lattice* L, double kappa,
+                  int op, void* stream) {
+    return guarded([&] {
+        const Geom g = checked_geom(L);
+        check_ptr(out, "out");
+        check_ptr(gauge, "gauge");
+        check_ptr(in, "in");
+        WL_REQUIRE(op == WILSON_OP_HOP || op == WILSON_OP_M, "wilson_dslash: op must be HOP or M");
+        WL_REQUIRE(std::isfinite(kappa), "kappa must be finite");
+        WL_REQUIRE(out != in, "out must not alias in");
+        check_device();
+        WL_REQUIRE(is_device_ptr(out) && is_device_ptr(in) && is_device_ptr(gauge),
+                   "wilson_dslash takes device pointers");
+        cudaStream_t st = static_cast<cudaStream_t>(stream);
+        GaugeField gf;
+        gf.prec = P_F64;
+        gf.recon = 18;
+        gf.g = g;
+        gf.buf.alloc(gauge_bytes(P_F64, 18, g.stride));
+        pack_gauge(gf, gauge, st);
+        SpinorField a, b;
+        a.alloc(P_F64, 2, 1, g);
+        b.alloc(P_F64, 2, 1, g);
+        pack_spinor(a, 0, in, st);
+        HopLaunch h{};
+        h.out = b.block(0);
+        h.in = a.block(0);
+        h.x = a.block(0);
+        h.out_pstep = b.pbytes;
+        h.in_pstep = a.pbytes;
+        h.x_pstep = a.pbytes;
+        h.full = 1;
+        h.gauge = &gf;
+        h.sprec = P_F64;
+        h.xpay = op == WILSON_OP_M;
+        h.a = op == WILSON_OP_M ? -kappa : 1.0;
+        launch_hop(h, st);
+        unpack_spinor(b, 0, out, st);
+        // the temporaries are freed on return: finish before releasing them
+        WL_CUDA(cudaStreamSynchronize(st));
+    });
+}
+
+int wilson_dslash_eo(double* out, const double* gauge, const double* in, const wilson_lattice* L,
+                     int out_parity, double kappa, int op, void* stream) {
+    return guarded([&] {
+        const Geom g = checked_geom(L);
+        check_ptr(out, "out");
+        check_ptr(gauge, "gauge");
+        check_ptr(in, "in");
+        WL_REQUIRE(out_parity == 0 || out_parity == 1, "out_parity must be 0 or 1");
+        WL_REQUIRE(op == WILSON_OP_HOP || op == WILSON_OP_SCHUR || op == WILSON_OP_SCHUR_DAG,
+                   "wilson_dslash_eo: op must be HOP, SCHUR or SCHUR_DAG");
+        WL_REQUIRE(std::isfinite(kappa), "kappa must be finite");
+        WL_REQUIRE(out != in, "out must not alias in");
+        check_device();
+        WL_REQUIRE(is_device_ptr(out) && is_device_ptr(in) && is_device_ptr(gauge),
+                   "wilson_dslash_eo takes device pointers");
+        cudaStream_t st = static_cast<cudaStream_t>(stream);
+        GaugeField gf;
+        gf.prec = P_F64;
+        gf.recon = 18;
+        gf.g = g;
+        gf.buf.alloc(gauge_bytes(P_F64, 18, g.stride));
+        pack_gauge(gf, gauge, st);
+        const int pin = op == WILSON_OP_HOP ? 1 - out_parity : out_parity;
+        SpinorField a, b, t;
+        a.alloc(P_F64, pin, 1, g);
+        b.alloc(P_F64, out_parity, 1, g);
+        pack_spinor(a, 0, in, st);
+        if (op == WILSON_OP_HOP) {
+            HopLaunch h{};
+            h.out = b.block(out_parity);
+            h.in = a.block(pin);
+            h.gauge = &gf;
+            h.sprec = P_F64;
+            h.out_parity = out_parity;
+            h.a = 1.0;
+            launch_hop(h, st);
+        } else {
+            // Mhat_p = 1 - kappa^2 D_{p,1-p} D_{1-p,p}
+            t.alloc(P_F64, 1 - out_parity, 1, g);
+            const int dag = op == WILSON_OP_SCHUR_DAG;
+            HopLaunch h1{};
+            h1.out = t.block(1 - out_parity);
+            h1.in = a.block(pin);
+            h1.gauge = &gf;
+            h1.sprec = P_F64;
+            h1.out_parity = 1 - out_parity;
+            h1.dagger = dag;
+            h1.a = 1.0;
+            launch_hop(h1, st);
+            HopLaunch h2{};
+            h2.out = b.block(out_parity);
+            h2.in = t.block(1 - out_parity);
+            h2.x = a.block(pin);
+            h2.xpay = 1;
+            h2.a = -kappa * kappa;
+            h2.gauge = &gf;
+            h2.sprec = P_F64;
+            h2.out_parity = out_parity;
+            h2.dagger = dag;
+            launch_hop(h2, st);
+        }
+        unpack_spinor(b, 0, out, st);
+        WL_CUDA(cudaStreamSynchronize(st));
+    });
+}
+
+int wilson_cg_solve(double* x, const double* gauge, const double* b, const wilson_lattice* L, double kappa,
+                    const wilson_solver_params* p, wilson_solve_stats* st_out, void* stream) {
+    SolveStats stats;
+    int rc = guarded([&] {
+        const Geom g = checked_geom(L);
+        check_ptr(x, "x");
+        check_ptr(gauge, "gauge");
+        check_ptr(b, "b");
+        WL_REQUIRE(p != nullptr, "solver parameters are NULL");
+        WL_REQUIRE(std::isfinite(kappa), "kappa must be finite");
+        WL_REQUIRE(p->tol > 0 && std::isfinite(p->tol), "tol must be positive");
+        WL_REQUIRE(p->maxiter > 0, "maxiter must be positive");
+        WL_REQUIRE(p->recon == 12 || p->recon == 18, "recon must be 12 or 18");
+        WL_REQUIRE(x != b, "x must not alias b");
+        SolveParams prm;
+        prm.inner = to_prec(p->inner);
+        WL_REQUIRE(prm.inner == P_F64 || p->recon == 12 || prm.inner == P_F32,
+                   "F16/BF16 links are stored with 12 reals");
+        prm.recon = p->recon;
+        prm.tol = p->tol;
+        prm.maxiter = p->maxiter;
+        prm.max_restarts = p->max_restarts > 0 ? p->max_restarts : 1000;
+        prm.delta = p->delta;
+        prm.use_initial_guess = p->use_initial_guess;
+        prm.reliable = p->reliable;
+        check_device();
+        WL_REQUIRE(is_device_ptr(x) && is_device_ptr(b) && is_device_ptr(gauge),
+                   "wilson_cg_solve takes device pointers");
+        cudaStream_t caller = static_cast<cudaStream_t>(stream);
+        SolveStream& ss = solve_stream();
+        WL_CUDA(cudaEventRecord(ss.e0, caller));
+        WL_CUDA(cudaStreamWaitEvent(ss.s, ss.e0, 0));
+        stats = cg_solve(x, gauge, b, g, kappa, prm, ss.s);
+        WL_CUDA(cudaEventRecord(ss.e1, ss.s));
+        WL_CUDA(cudaStreamWaitEvent(caller, ss.e1, 0));
+        WL_CUDA(cudaStreamSynchronize(caller));
+        if (stats.status != 0)
+            throw Error(stats.status, stats.status == WILSON_ERR_NOCONV ? "solve did not converge"
+                                                                        : "NaN or Inf in the solve");
+    });
+    if (st_out) {
+        st_out->status = rc;
+        st_out->outer_iters = stats.outer_iters;
+        st_out->inner_iters = stats.inner_iters;
+        st_out->hop_applications = stats.hop_applications;
+        st_out->true_rel_resid = stats.true_rel_resid;
+        st_out->seconds = stats.seconds;
+    }
+    return rc;
+}
+
+// ---------------------------------------------------------------------------
+// handles
+// ---------------------------------------------------------------------------
+int wilson_gauge_create(wilson_gauge** out, const double* canon, const wilson_lattice* L, int prec, int recon,
+                        void* stream) {
+    return guarded([&] {
+        WL_REQUIRE(out != nullptr, "handle pointer is NULL");
+        *out = nullptr;
+        const Geom g = checked_geom(L);
+        check_ptr(canon, "gauge");
+        const Prec p = to_prec(prec);
+        WL_REQUIRE(recon == 12 || recon == 18, "recon must be 12 or 18");
+        WL_REQUIRE(recon == 12 || p == P_F64 || p == P_F32, "F16/BF16 links are stored with 12 reals");
+        check_device();
+        cudaStream_t st = static_cast<cudaStream_t>(stream);
+        std::unique_ptr<wilson_gauge_s> h(new wilson_gauge_s);
+        h->f.prec = p;
+        h->f.recon = recon;
+        h->f.g = g;
+        h->f.buf.alloc(gauge_bytes(p, recon, g.stride));
+        DevBuf tmp;
+        const double* d = device_view(canon, sizeof(double) * 72 * 2 * (size_t)g.Vh, tmp, st);
+        pack_gauge(h->f, d, st);
+        WL_CUDA(cudaStreamSynchronize(st));
+        *out = h.release();
+    });
+}
+
+int wilson_gauge_destroy(wilson_gauge* g) {
+    return guarded([&] { delete g; });
+}
+
+int wilson_spinor_create(wilson_spinor** out, const wilson_lattice* L, int subset, int nrhs, int prec) {
+    return guarded([&] {
+        WL_REQUIRE(out != nullptr, "handle pointer is NULL");
+        *out = nullptr;
+        const Geom g = checked_geom(L);
+        WL_REQUIRE(subset >= 0 && subset <= 2, "subset must be EVEN, ODD or FULL");
+        WL_REQUIRE(nrhs >= 1 && nrhs <= 64, "nrhs must be in 1..64");
+        const Prec p = to_prec(prec);
+        check_device();
+        std::unique_ptr<wilson_spinor_s> h(new wilson_spinor_s);
+        h->g = g;
+        h->f.alloc(p, subset, nrhs, g);
+        WL_CUDA(cudaMemset(h->f.buf.p, 0, h->f.buf.bytes));
+        *out = h.release();
+    });
+}
+
+int wilson_spinor_destroy(wilson_spinor* s) {
+    return guarded([&] { delete s; });
+}
+
+long long wilson_spinor_bytes(const wilson_spinor* s) { return s ? (long long)s->f.buf.bytes : 0; }
+
+int wilson_spinor_import(wilson_spinor* s, const double* canon, void* stream) {
+    return guarded([&] {
+        WL_REQUIRE(s != nullptr, "spinor handle is NULL");
+        check_ptr(canon, "canonical field");
+        cudaStream_t st = static_cast<cudaStream_t>(stream);
+        const size_t per = sizeof(double) * 24 * (size_t)s->g.Vh * (s->f.subset == 2 ? 2 : 1);
+        if (is_device_ptr(canon)) {
+            for (int k = 0; k < s->f.nrhs; k++) pack_spinor(s->f, k, canon + (per / sizeof(double)) * k, st);
+        } else {
+            Staging& sg = staging();
+            std::lock_guard<std::mutex> lk(sg.m);
+            sg.buf.ensure(per * s->f.nrhs);
+            WL_CUDA(cudaMemcpyAsync(sg.buf.p, canon, per * s->f.nrhs, cudaMemcpyHostToDevice, st));
+            for (int k = 0; k < s->f.nrhs; k++)
+                pack_spinor(s->f, k, sg.buf.as<const double>() + (per / sizeof(double)) * k, st);
+            // the staging buffer is reused by the next call: finish with it first
+            WL_CUDA(cudaStreamSynchronize(st));
+        }
+    });
+}
+
+int wilson_spinor_export(const wilson_spinor* s, double* canon, void* stream) {
+    return guarded([&] {
+        WL_REQUIRE(s != nullptr, "spinor handle is NULL");
+        check_ptr(canon, "canonical field");
+        cudaStream_t st = static_cast<cudaStream_t>(stream);
+        const size_t per = sizeof(double) * 24 * (size_t)s->g.Vh * (s->f.subset == 2 ? 2 : 1);
+        if (is_device_ptr(canon)) {
+            for (int k = 0; k < s->f.nrhs; k++) unpack_spinor(s->f, k, canon + (per / sizeof(double)) * k, st);
+        } else {
+            Staging& sg = staging();
+            std::lock_guard<std::mutex> lk(sg.m);
+            sg.buf.ensure(per * s->f.nrhs);
+            for (int k = 0; k < s->f.nrhs; k++)
+                unpack_spinor(s->f, k, sg.buf.as<double>() + (per / sizeof(double)) * k, st);
+            WL_CUDA(cudaMemcpyAsync(canon, sg.buf.p, per * s->f.nrhs, cudaMemcpyDeviceToHost, st));
+            WL_CUDA(cudaStreamSynchronize(st));
+        }
+    });
+}
+
+int wilson_dslash_h(wilson_spinor* out, const wilson_gauge* gh, const wilson_spinor* in, double kappa, int op,
+                    void* stream) {
+    return guarded([&] {
+        WL_REQUIRE(out && gh && in, "NULL handle");
+        WL_REQUIRE(out != in, "out must not be in");
+        WL_REQUIRE(std::isfinite(kappa), "kappa must be finite");
+        const GaugeField& gf = gh->f;
+        const SpinorField& a = in->f;
+        SpinorField& b = out->f;
+        for (int mu = 0; mu < 4; mu++)
+            WL_REQUIRE(a.g.L[mu] == gf.g.L[mu] && b.g.L[mu] == gf.g.L[mu], "lattice mismatch");
+        WL_REQUIRE(a.prec == b.prec, "in and out precision differ");
+        WL_REQUIRE(a.nrhs == b.nrhs, "in and out nrhs differ");
+        WL_REQUIRE(gf.prec == a.prec, "gauge and spinor precision differ");
+        cudaStream_t st = static_cast<cudaStream_t>(stream);
+        for (int k = 0; k < a.nrhs; k++) {
+            if (op == WILSON_OP_HOP || op == WILSON_OP_M) {
+                if (a.subset == 2) {
+                    WL_REQUIRE(b.subset == 2, "full input needs a full output");
+                    HopLaunch h{};
+                    h.out = b.block(0, k);
+                    h.in = a.block(0, k);
+                    h.x = a.block(0, k);
+                    h.out_pstep = b.pbytes;
+                    h.in_pstep = a.pbytes;
+                    h.x_pstep = a.pbytes;
+                    h.full = 1;
+                    h.gauge = &gf;
+                    h.sprec = a.prec;
+                    h.xpay = op == WILSON_OP_M;
+                    h.a = op == WILSON_OP_M ? -kappa : 1.0;
+                    launch_hop(h, st);
+                } else {
+                    WL_REQUIRE(op == WILSON_OP_HOP, "M needs full fields");
+                    WL_REQUIRE(b.subset == 1 - a.subset, "HOP maps parity 1-p to parity p");
+                    HopLaunch h{};
+                    h.out = b.block(b.subset, k);
+                    h.in = a.block(a.subset, k);
+                    h.gauge = &gf;
+                    h.sprec = a.prec;
+                    h.out_parity = b.subset;
+                    h.a = 1.0;
+                    launch_hop(h, st);
+                }
+            } else if (op == WILSON_OP_SCHUR || op == WILSON_OP_SCHUR_DAG) {
+                WL_REQUIRE(a.subset != 2 && b.subset == a.subset, "SCHUR maps parity p to parity p");
+                throw Error(WILSON_ERR_UNSUPPORTED, "SCHUR on handles: use wilson_dslash_eo or the solver");
+            } else {
+                throw Error(WILSON_ERR_ARG, "unknown op");
+            }
+        }
+    });
+}
+
+}  // extern "C"

@@ -1,0 +1,337 @@
+// common.cuh -- device-side building blocks of libwilson_gb300: complex
+// arithmetic, lattice geometry, and the site-vectorised structure-of-arrays
+// (SoA) storage formats of spinor and gauge fields.
+//
+// SoA layout.  A field of one parity holds Vh sites.  Its per-site data is
+// cut into 16-byte (8-byte for 12-real low-precision links) chunks, and chunk
+// c of all sites is one contiguous row:  row c starts at c * stride chunks,
+// with stride >= Vh a multiple of 64, so thread i of a warp reads chunk c of
+// site i and a warp's request is one coalesced 512-byte line group.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace wl {
+
+enum Prec { P_F64 = 0, P_F32 = 1, P_F16 = 2, P_BF16 = 3 };
+
+// ---------------------------------------------------------------------------
+// complex numbers
+// ---------------------------------------------------------------------------
+template <class T>
+struct cpx {
+    T re, im;
+};
+
+template <class T>
+__device__ __forceinline__ cpx<T> cadd(cpx<T> a, cpx<T> b) { return {a.re + b.re, a.im + b.im}; }
+template <class T>
+__device__ __forceinline__ cpx<T> csub(cpx<T> a, cpx<T> b) { return {a.re - b.re, a.im - b.im}; }
+template <class T>
+__device__ __forceinline__ cpx<T> cmul(cpx<T> a, cpx<T> b) {
+    return {a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re};
+}
+// conj(a) * b
+template <class T>
+__device__ __forceinline__ cpx<T> cjmul(cpx<T> a, cpx<T> b) {
+    return {a.re * b.re + a.im * b.im, a.re * b.im - a.im * b.re};
+}
+// acc + a * b
+template <class T>
+__device__ __forceinline__ cpx<T> cfma(cpx<T> a, cpx<T> b, cpx<T> acc) {
+    acc.re = fma(a.re, b.re, acc.re);
+    acc.re = fma(-a.im, b.im, acc.re);
+    acc.im = fma(a.re, b.im, acc.im);
+    acc.im = fma(a.im, b.re, acc.im);
+    return acc;
+}
+// acc + conj(a) * b
+template <class T>
+__device__ __forceinline__ cpx<T> cjfma(cpx<T> a, cpx<T> b, cpx<T> acc) {
+    acc.re = fma(a.re, b.re, acc.re);
+    acc.re = fma(a.im, b.im, acc.re);
+    acc.im = fma(a.re, b.im, acc.im);
+    acc.im = fma(-a.im, b.re, acc.im);
+    return acc;
+}
+// i * a
+template <class T>
+__device__ __forceinline__ cpx<T> ci(cpx<T> a) { return {-a.im, a.re}; }
+template <class T>
+__device__ __forceinline__ cpx<T> cneg(cpx<T> a) { return {-a.re, -a.im}; }
+template <class T>
+__device__ __forceinline__ cpx<T> cscale(T s, cpx<T> a) { return {s * a.re, s * a.im}; }
+template <class T>
+__device__ __forceinline__ cpx<T> cconj(cpx<T> a) { return {a.re, -a.im}; }
+template <class T>
+__device__ __forceinline__ T cnorm2(cpx<T> a) { return a.re * a.re + a.im * a.im; }
+
+// ---------------------------------------------------------------------------
+// lattice geometry
+// ---------------------------------------------------------------------------
+struct Geom {
+    int L[4];          // Lx, Ly, Lz, Lt
+    int Vh;            // sites per parity
+    int stride;        // SoA row length (chunks) of a parity-field row, >= Vh
+    double ph[4][2];   // boundary phases (re, im)
+};
+
+__host__ __device__ inline int round_up(int a, int b) { return (a + b - 1) / b * b; }
+
+// Coordinates and canonical index of the site with half index h and parity p.
+// The canonical index is s = 2h + ((y+z+t+p) & 1) because Lx is even.
+__device__ __forceinline__ void site_of_half(int h, int p, const Geom& g, int c[4], int& s) {
+    int s0 = 2 * h;
+    int r = s0 / g.L[0];
+    int x0 = s0 - r * g.L[0];
+    int r2 = r / g.L[1];
+    c[1] = r - r2 * g.L[1];
+    c[3] = r2 / g.L[2];
+    c[2] = r2 - c[3] * g.L[2];
+    int odd = (c[1] + c[2] + c[3] + p) & 1;
+    c[0] = x0 + odd;
+    s = s0 + odd;
+}
+
+// ---------------------------------------------------------------------------
+// low-precision helpers
+// ---------------------------------------------------------------------------
+template <int P>
+struct LowT;
+template <>
+struct LowT<P_F16> {
+    using T = __half;
+    using T2 = __half2;
+    __device__ static __forceinline__ float2 to_f2(uint32_t u) {
+        __half2 h = *reinterpret_cast<__half2*>(&u);
+        return __half22float2(h);
+    }
+    __device__ static __forceinline__ uint32_t from_f2(float a, float b) {
+        __half2 h = __floats2half2_rn(a, b);
+        return *reinterpret_cast<uint32_t*>(&h);
+    }
+};
+template <>
+struct LowT<P_BF16> {
+    using T = __nv_bfloat16;
+    using T2 = __nv_bfloat162;
+    __device__ static __forceinline__ float2 to_f2(uint32_t u) {
+        __nv_bfloat162 h = *reinterpret_cast<__nv_bfloat162*>(&u);
+        return __bfloat1622float2(h);
+    }
+    __device__ static __forceinline__ uint32_t from_f2(float a, float b) {
+        __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+        return *reinterpret_cast<uint32_t*>(&h);
+    }
+};
+
+// ---------------------------------------------------------------------------
+// spinor storage formats.  v[k], k = spin*3 + colour.
+// ---------------------------------------------------------------------------
+template <int P>
+struct SpinorFmt;
+
+template <>
+struct SpinorFmt<P_F64> {
+    using real = double;
+    static constexpr int nchunk = 12;
+    static constexpr int chunk_bytes = 16;
+    static constexpr bool scaled = false;
+    static __host__ __device__ long long field_bytes(int stride) { return 16LL * 12 * stride; }
+    __device__ static __forceinline__ void load(const void* base, int stride, int i, cpx<double> v[12]) {
+        const double2* b = static_cast<const double2*>(base) + i;
+#pragma unroll
+        for (int c = 0; c < 12; c++) {
+            double2 d = __ldg(b + (size_t)c * stride);
+            v[c] = {d.x, d.y};
+        }
+    }
+    __device__ static __forceinline__ void store(void* base, int stride, int i, const cpx<double> v[12]) {
+        double2* b = static_cast<double2*>(base) + i;
+#pragma unroll
+        for (int c = 0; c < 12; c++) b[(size_t)c * stride] = make_double2(v[c].re, v[c].im);
+    }
+};
+
+template <>
+struct SpinorFmt<P_F32> {
+    using real = float;
+    static constexpr int nchunk = 6;
+    static constexpr int chunk_bytes = 16;
+    static constexpr bool scaled = false;
+    static __host__ __device__ long long field_bytes(int stride) { return 16LL * 6 * stride; }
+    __device__ static __forceinline__ void load(const void* base, int stride, int i, cpx<float> v[12]) {
+        const float4* b = static_cast<const float4*>(base) + i;
+#pragma unroll
+        for (int c = 0; c < 6; c++) {
+            float4 d = __ldg(b + (size_t)c * stride);
+            v[2 * c] = {d.x, d.y};
+            v[2 * c + 1] = {d.z, d.w};
+        }
+    }
+    __device__ static __forceinline__ void store(void* base, int stride, int i, const cpx<float> v[12]) {
+        float4* b = static_cast<float4*>(base) + i;
+#pragma unroll
+        for (int c = 0; c < 6; c++)
+            b[(size_t)c * stride] = make_float4(v[2 * c].re, v[2 * c].im, v[2 * c + 1].re, v[2 * c + 1].im);
+    }
+};
+
+// 24 low-precision reals in 3 x 16 B chunks, then one FP32 scale per site
+// (row of stride floats after the 3 chunk rows).  value = q * scale, with
+// scale = max |component| of the site, so |q| <= 1.
+template <int P>
+struct SpinorLowFmt {
+    using real = float;
+    using LT = LowT<P>;
+    static constexpr int nchunk = 3;
+    static constexpr int chunk_bytes = 16;
+    static constexpr bool scaled = true;
+    static __host__ __device__ long long field_bytes(int stride) { return 16LL * 3 * stride + 4LL * stride; }
+    __device__ static __forceinline__ float load_scale(const void* base, int stride, int i) {
+        const float* sc = reinterpret_cast<const float*>(static_cast<const char*>(base) + 48LL * stride);
+        return __ldg(sc + i);
+    }
+    __device__ static __forceinline__ void load(const void* base, int stride, int i, cpx<float> v[12]) {
+        const uint4* b = static_cast<const uint4*>(base) + i;
+        float s = load_scale(base, stride, i);
+#pragma unroll
+        for (int c = 0; c < 3; c++) {
+            uint4 d = __ldg(b + (size_t)c * stride);
+            float2 f0 = LT::to_f2(d.x), f1 = LT::to_f2(d.y), f2 = LT::to_f2(d.z), f3 = LT::to_f2(d.w);
+            v[4 * c + 0] = {f0.x * s, f0.y * s};
+            v[4 * c + 1] = {f1.x * s, f1.y * s};
+            v[4 * c + 2] = {f2.x * s, f2.y * s};
+            v[4 * c + 3] = {f3.x * s, f3.y * s};
+        }
+    }
+    __device__ static __forceinline__ void store(void* base, int stride, int i, const cpx<float> v[12]) {
+        float m = 0.f;
+#pragma unroll
+        for (int k = 0; k < 12; k++) m = fmaxf(m, fmaxf(fabsf(v[k].re), fabsf(v[k].im)));
+        float inv = m > 0.f ? 1.0f / m : 0.f;
+        uint4* b = static_cast<uint4*>(base) + i;
+#pragma unroll
+        for (int c = 0; c < 3; c++) {
+            uint4 d;
+            d.x = LT::from_f2(v[4 * c + 0].re * inv, v[4 * c + 0].im * inv);
+            d.y = LT::from_f2(v[4 * c + 1].re * inv, v[4 * c + 1].im * inv);
+            d.z = LT::from_f2(v[4 * c + 2].re * inv, v[4 * c + 2].im * inv);
+            d.w = LT::from_f2(v[4 * c + 3].re * inv, v[4 * c + 3].im * inv);
+            b[(size_t)c * stride] = d;
+        }
+        float* sc = reinterpret_cast<float*>(static_cast<char*>(base) + 48LL * stride);
+        sc[i] = m;
+    }
+};
+template <>
+struct SpinorFmt<P_F16> : SpinorLowFmt<P_F16> {};
+template <>
+struct SpinorFmt<P_BF16> : SpinorLowFmt<P_BF16> {};
+
+// ---------------------------------------------------------------------------
+// gauge storage formats.  One parity-and-direction block holds Vh links;
+// block (p, mu) starts at (p*4 + mu) * nchunk rows.  U[i][j] row-major.
+// With 12 reals only rows 0 and 1 are stored; row 2 = conj(row0 x row1),
+// exact for SU(3).
+// ---------------------------------------------------------------------------
+template <class T>
+__device__ __forceinline__ void recon_row2(cpx<T> U[3][3]) {
+#pragma unroll
+    for (int j = 0; j < 3; j++) {
+        const int a = (j + 1) % 3, b = (j + 2) % 3;
+        cpx<T> t = csub(cmul(U[0][a], U[1][b]), cmul(U[0][b], U[1][a]));
+        U[2][j] = cconj(t);
+    }
+}
+
+template <int P, int R>
+struct GaugeFmt;
+
+template <>
+struct GaugeFmt<P_F64, 18> {
+    using real = double;
+    static constexpr int nchunk = 9;
+    static constexpr int chunk_bytes = 16;
+    __device__ static __forceinline__ void load(const void* base, int stride, int blk, int i, cpx<double> U[3][3]) {
+        const double2* b = static_cast<const double2*>(base) + (size_t)blk * nchunk * stride + i;
+#pragma unroll
+        for (int c = 0; c < 9; c++) {
+            double2 d = __ldg(b + (size_t)c * stride);
+            U[c / 3][c % 3] = {d.x, d.y};
+        }
+    }
+};
+template <>
+struct GaugeFmt<P_F64, 12> {
+    using real = double;
+    static constexpr int nchunk = 6;
+    static constexpr int chunk_bytes = 16;
+    __device__ static __forceinline__ void load(const void* base, int stride, int blk, int i, cpx<double> U[3][3]) {
+        const double2* b = static_cast<const double2*>(base) + (size_t)blk * nchunk * stride + i;
+#pragma unroll
+        for (int c = 0; c < 6; c++) {
+            double2 d = __ldg(b + (size_t)c * stride);
+            U[c / 3][c % 3] = {d.x, d.y};
+        }
+        recon_row2(U);
+    }
+};
+template <>
+struct GaugeFmt<P_F32, 18> {
+    using real = float;
+    static constexpr int nchunk = 9;
+    static constexpr int chunk_bytes = 8;
+    __device__ static __forceinline__ void load(const void* base, int stride, int blk, int i, cpx<float> U[3][3]) {
+        const float2* b = static_cast<const float2*>(base) + (size_t)blk * nchunk * stride + i;
+#pragma unroll
+        for (int c = 0; c < 9; c++) {
+            float2 d = __ldg(b + (size_t)c * stride);
+            U[c / 3][c % 3] = {d.x, d.y};
+        }
+    }
+};
+template <>
+struct GaugeFmt<P_F32, 12> {
+    using real = float;
+    static constexpr int nchunk = 3;
+    static constexpr int chunk_bytes = 16;
+    __device__ static __forceinline__ void load(const void* base, int stride, int blk, int i, cpx<float> U[3][3]) {
+        const float4* b = static_cast<const float4*>(base) + (size_t)blk * nchunk * stride + i;
+#pragma unroll
+        for (int c = 0; c < 3; c++) {
+            float4 d = __ldcs(b + (size_t)c * stride);
+            U[(2 * c) / 3][(2 * c) % 3] = {d.x, d.y};
+            U[(2 * c + 1) / 3][(2 * c + 1) % 3] = {d.z, d.w};
+        }
+        recon_row2(U);
+    }
+};
+// 12 low-precision reals in 3 x 8 B chunks (links have |U_ij| <= 1: no scale)
+template <int P>
+struct GaugeLow12 {
+    using real = float;
+    using LT = LowT<P>;
+    static constexpr int nchunk = 3;
+    static constexpr int chunk_bytes = 8;
+    __device__ static __forceinline__ void load(const void* base, int stride, int blk, int i, cpx<float> U[3][3]) {
+        const uint2* b = static_cast<const uint2*>(base) + (size_t)blk * nchunk * stride + i;
+#pragma unroll
+        for (int c = 0; c < 3; c++) {
+            uint2 d = __ldcs(b + (size_t)c * stride);
+            float2 f0 = LT::to_f2(d.x), f1 = LT::to_f2(d.y);
+            U[(2 * c) / 3][(2 * c) % 3] = {f0.x, f0.y};
+            U[(2 * c + 1) / 3][(2 * c + 1) % 3] = {f1.x, f1.y};
+        }
+        recon_row2(U);
+    }
+};
+template <>
+struct GaugeFmt<P_F16, 12> : GaugeLow12<P_F16> {};
+template <>
+struct GaugeFmt<P_BF16, 12> : GaugeLow12<P_BF16> {};
+
+}  // namespace wl

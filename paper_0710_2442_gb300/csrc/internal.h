@@ -1,0 +1,150 @@
+// internal.h -- host-side declarations shared by the translation units of
+// libwilson_gb300 (not part of the C ABI).
+#pragma once
+
+#include <stdexcept>
+#include <string>
+
+#include "common.cuh"
+#include "reduce.cuh"
+
+namespace wl {
+
+struct Error : std::runtime_error {
+    int code;
+    Error(int c, const std::string& m) : std::runtime_error(m), code(c) {}
+};
+
+#define WL_CUDA(call)                                                                          \
+    do {                                                                                       \
+        cudaError_t e_ = (call);                                                               \
+        if (e_ != cudaSuccess)                                                                 \
+            throw ::wl::Error(e_ == cudaErrorMemoryAllocation ? 3 : 2,                         \
+                              std::string(#call) + ": " + cudaGetErrorString(e_));             \
+    } while (0)
+
+#define WL_LAUNCH_CHECK() WL_CUDA(cudaGetLastError())
+
+#define WL_REQUIRE(cond, msg)                                      \
+    do {                                                           \
+        if (!(cond)) throw ::wl::Error(1, std::string(msg));       \
+    } while (0)
+
+// ---------------------------------------------------------------------------
+// device memory owned by the library
+// ---------------------------------------------------------------------------
+struct DevBuf {
+    void* p = nullptr;
+    size_t bytes = 0;
+    DevBuf() = default;
+    explicit DevBuf(size_t n) { alloc(n); }
+    ~DevBuf() { release(); }
+    DevBuf(const DevBuf&) = delete;
+    DevBuf& operator=(const DevBuf&) = delete;
+    DevBuf(DevBuf&& o) noexcept : p(o.p), bytes(o.bytes) { o.p = nullptr; o.bytes = 0; }
+    DevBuf& operator=(DevBuf&& o) noexcept {
+        if (this != &o) { release(); p = o.p; bytes = o.bytes; o.p = nullptr; o.bytes = 0; }
+        return *this;
+    }
+    void alloc(size_t n) {
+        release();
+        if (n) WL_CUDA(cudaMalloc(&p, n));
+        bytes = n;
+    }
+    void ensure(size_t n) { if (n > bytes) alloc(n); }
+    void release() {
+        if (p) cudaFree(p);
+        p = nullptr;
+        bytes = 0;
+    }
+    template <class T>
+    T* as() const { return static_cast<T*>(p); }
+};
+
+// Geometry from dims and phases; stride rounded up to 64 sites.
+Geom make_geom(const int dims[4], const double ph[4][2]);
+
+inline int spinor_chunk_rows(Prec p) { return p == P_F64 ? 12 : p == P_F32 ? 6 : 3; }
+long long spinor_field_bytes(Prec p, int stride);          // one parity, one rhs
+long long gauge_bytes(Prec p, int recon, int stride);      // both parities, 4 directions
+long long gauge_block_bytes(Prec p, int recon, int stride);
+
+// A prepared spinor field: nrhs x (1 or 2 parities) SoA blocks.
+struct SpinorField {
+    Prec prec = P_F32;
+    int subset = 0;      // 0 even, 1 odd, 2 full
+    int nrhs = 1;
+    Geom g{};
+    DevBuf buf;
+    long long pbytes = 0;   // bytes of one parity block of one rhs
+    int nparity() const { return subset == 2 ? 2 : 1; }
+    // pointer to parity block p (absolute parity 0/1) of rhs k
+    void* block(int p, int k = 0) const {
+        int slot = subset == 2 ? p : 0;
+        return static_cast<char*>(buf.p) + (size_t)(k * nparity() + slot) * pbytes;
+    }
+    void alloc(Prec p, int sub, int nr, const Geom& geom);
+};
+
+struct GaugeField {
+    Prec prec = P_F32;
+    int recon = 12;
+    Geom g{};
+    DevBuf buf;
+};
+
+// Per-device scratch: reduction partials and counters.
+struct Reduction {
+    DevBuf partials;   // doubles
+    DevBuf counters;   // unsigned ints, zeroed
+    DevBuf results;    // doubles
+    int capacity = 0;
+    void init(int cap, int ncounters, cudaStream_t st);
+    RedArgs args(int counter_slot, int op, double* result, CGScalars* sc) const {
+        RedArgs r;
+        r.partials = partials.as<double>() + (size_t)counter_slot * capacity;
+        r.counter = counters.as<unsigned int>() + counter_slot;
+        r.result = result;
+        r.sc = sc;
+        r.op = op;
+        return r;
+    }
+};
+
+// ---------------------------------------------------------------------------
+// kernel launchers
+// ---------------------------------------------------------------------------
+struct HopLaunch {
+    void* out;             // output parity block (parity out_parity), or parity-0 block if full
+    const void* in;        // input block of parity 1 - out_parity, or parity-0 block if full
+    const void* x;         // xpay block, parity out_parity (or parity-0 block if full); may be null
+    long long out_pstep;   // full launches: byte offset of the parity-1 block from the parity-0 block
+    long long in_pstep;
+    long long x_pstep;
+    const GaugeField* gauge;
+    Prec sprec;
+    int out_parity;        // single-parity launches
+    int full;              // 1: both output parities in one launch
+    int dagger;            // 1: projectors swapped (the hop of g5 D g5)
+    int xpay;              // out = x + a * D in   (else out = a * D in)
+    double a;
+    const RedArgs* red;    // |out|^2 into a reducer, or null
+    const int* skip;       // device flag: nonzero -> the launch does nothing
+    int block;             // threads per block (0 = default)
+    int grid_cap;          // max blocks (0 = no cap)
+};
+void launch_hop(const HopLaunch& L, cudaStream_t st);
+int hop_grid_blocks(const Geom& g, int block, int grid_cap);
+
+// canonical <-> SoA
+void pack_spinor(const SpinorField& f, int rhs, const double* canon, cudaStream_t st);
+void unpack_spinor(const SpinorField& f, int rhs, double* canon, cudaStream_t st);
+void pack_gauge(GaugeField& gf, const double* canon, cudaStream_t st);
+
+// BLAS-1 on parity blocks (see blas.cu)
+void convert_block(Prec dst_p, void* dst, Prec src_p, const void* src, const Geom& g, cudaStream_t st,
+                   const int* skip = nullptr);
+
+int device_sm_count();
+
+}  // namespace wl

@@ -14,8 +14,8 @@ itself fixes none of them):
   * random SU(3): complex Gaussian 3x3, rows orthonormalised by Gram-Schmidt,
     then multiplied by exp(-i arg(det)/3) with arg in (-pi, pi] so det = 1.
   * weak field: U = exp(i eps H), H = sum_a h_a lambda_a / 2 with h_a ~ N(0,1)
-    and lambda_a the Gell-Mann matrices; exp by eigendecomposition of the
-    Hermitian H, then the same projection onto SU(3).
+    and lambda_a the Gell-Mann matrices; exp by a batched matrix exponential,
+    then the same projection onto SU(3).
   * Gaussian spinor: real and imaginary parts i.i.d. N(0, 1).
 """
 from __future__ import annotations
@@ -90,20 +90,42 @@ def gell_mann() -> np.ndarray:
     return l
 
 
-def weak_field_su3(rng, n: int, eps, chunk: int = 1 << 19) -> np.ndarray:
-    """exp(i eps H) with H = sum_a h_a lambda_a / 2; eps scalar or per-matrix."""
+def _project_su3_torch(u):
+    """project_su3 on a torch complex128 tensor [n, 3, 3] (multi-threaded)."""
+    import torch
+    r0 = u[:, 0, :]
+    r0 = r0 / torch.linalg.vector_norm(r0, dim=1, keepdim=True)
+    r1 = u[:, 1, :]
+    r2 = u[:, 2, :]
+    for _ in range(2):
+        r1 = r1 - (r0.conj() * r1).sum(dim=1, keepdim=True) * r0
+    r1 = r1 / torch.linalg.vector_norm(r1, dim=1, keepdim=True)
+    for _ in range(2):
+        r2 = r2 - (r0.conj() * r2).sum(dim=1, keepdim=True) * r0
+        r2 = r2 - (r1.conj() * r2).sum(dim=1, keepdim=True) * r1
+    r2 = r2 / torch.linalg.vector_norm(r2, dim=1, keepdim=True)
+    m = torch.stack([r0, r1, r2], dim=1)
+    det = torch.linalg.det(m)
+    return m * torch.exp(-1j * torch.angle(det) / 3.0)[:, None, None]
+
+
+def weak_field_su3(rng, n: int, eps, chunk: int = 1 << 20) -> np.ndarray:
+    """exp(i eps H) with H = sum_a h_a lambda_a / 2; eps scalar or per-matrix.
+
+    The coefficients h_a are drawn with numpy (seeded); the exponential is a
+    batched matrix exponential (torch, CPU), followed by the SU(3) projection."""
+    import torch
     rng = make_rng(rng)
-    lam = gell_mann() / 2.0
+    lam = torch.from_numpy(gell_mann() / 2.0)
     out = np.empty((n, 3, 3), dtype=np.complex128)
     eps_arr = np.broadcast_to(np.asarray(eps, dtype=np.float64), (n,))
     for a in range(0, n, chunk):
         b = min(n, a + chunk)
-        h = rng.standard_normal((b - a, 8))
-        H = np.einsum("na,aij->nij", h, lam)
-        w, v = np.linalg.eigh(H)
-        ph = np.exp(1j * eps_arr[a:b, None] * w)
-        u = np.einsum("nij,nj,nkj->nik", v, ph, np.conj(v))
-        out[a:b] = project_su3(u)
+        h = torch.from_numpy(rng.standard_normal((b - a, 8))).to(torch.complex128)
+        H = torch.einsum("na,aij->nij", h, lam)
+        e = torch.from_numpy(np.ascontiguousarray(eps_arr[a:b])).to(torch.complex128)
+        u = torch.linalg.matrix_exp(1j * e[:, None, None] * H)
+        out[a:b] = _project_su3_torch(u).numpy()
     return out
 
 

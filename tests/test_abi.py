@@ -1,0 +1,96 @@
+"""The C ABI library builds for sm_103a, loads, exports every symbol that
+include/*.h declares, and rejects invalid arguments on the host (no GPU
+needed: validation happens before any device call)."""
+import ctypes
+import glob
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def w():
+    from paper_0710_2442_gb300 import build, wilson
+    build.build()
+    return wilson
+
+
+def declared_functions():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        text = open(h).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        for m in re.finditer(r"\b(wilson_[a-z0-9_]+)\s*\(", text):
+            names.add(m.group(1))
+    return sorted(names)
+
+
+def test_every_declared_symbol_is_exported(w):
+    lib = ctypes.CDLL(w.LIB_PATH)
+    names = declared_functions()
+    assert len(names) >= 14
+    missing = [n for n in names if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_version(w):
+    assert w.lib().wilson_version() >= 100
+
+
+def _status(w, fn):
+    try:
+        fn()
+    except w.WilsonError as e:
+        return e.code
+    return 0
+
+
+@pytest.mark.parametrize("dims", [(4, 4, 3, 4), (0, 4, 4, 4), (4, 4, 4, 1)])
+def test_bad_dims_rejected(w, dims):
+    L = w.lattice(dims)
+    buf = np.zeros(16, dtype=np.complex128)
+    assert _status(w, lambda: w.wilson_dslash(buf.ctypes.data + 0, buf, buf.ctypes.data + 64, L, 0.1)) \
+        == w.WILSON_ERR_ARG
+
+
+def test_bad_phase_null_and_alias_rejected(w):
+    buf = np.zeros(64, dtype=np.complex128)
+    L = w.lattice((4, 4, 4, 4), phases=(1, 1, 1, 2.0))
+    assert _status(w, lambda: w.wilson_dslash(buf, buf, buf.ctypes.data + 256, L, 0.1)) == w.WILSON_ERR_ARG
+    L = w.lattice((4, 4, 4, 4))
+    assert _status(w, lambda: w.wilson_dslash(0, buf, buf, L, 0.1)) == w.WILSON_ERR_ARG
+    assert _status(w, lambda: w.wilson_dslash(buf, buf, buf, L, 0.1)) == w.WILSON_ERR_ARG
+    assert _status(w, lambda: w.wilson_dslash(buf.ctypes.data + 8, buf, buf.ctypes.data + 256, L, 0.1)) \
+        == w.WILSON_ERR_ARG  # misaligned
+    assert _status(w, lambda: w.wilson_dslash(buf, buf, buf.ctypes.data + 256, L, float("nan"))) \
+        == w.WILSON_ERR_ARG
+    assert _status(w, lambda: w.wilson_dslash_eo(buf, buf, buf.ctypes.data + 256, L, 2)) == w.WILSON_ERR_ARG
+    assert _status(w, lambda: w.wilson_dslash_eo(buf, buf, buf.ctypes.data + 256, L, 0, 0.1, w.WILSON_OP_M)) \
+        == w.WILSON_ERR_ARG
+
+
+def test_last_error_message(w):
+    buf = np.zeros(64, dtype=np.complex128)
+    L = w.lattice((4, 4, 3, 4))
+    with pytest.raises(w.WilsonError, match="even"):
+        w.wilson_dslash(buf, buf, buf.ctypes.data + 256, L, 0.1)
+
+
+def test_no_device_is_an_error_not_a_fallback(w):
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    buf = np.zeros(64, dtype=np.complex128)
+    L = w.lattice((2, 2, 2, 2))
+    assert _status(w, lambda: w.wilson_dslash(buf, buf, buf.ctypes.data + 256, L, 0.1)) == w.WILSON_ERR_CUDA
+
+
+def test_solver_defaults(w):
+    p = w.solver_defaults(w.WILSON_F16)
+    assert p.inner == w.WILSON_F16 and p.recon == 12 and p.tol == 1e-10 and p.reliable == 1
+    p = w.solver_defaults(w.WILSON_F64)
+    assert p.recon == 18

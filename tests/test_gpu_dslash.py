@@ -1,0 +1,157 @@
+"""Parity of the CUDA hopping term against the FP64 CPU oracle, element by
+element, through the C ABI.
+
+Tolerances (relative L2 over the whole output): 1e-13 for FP64 fields,
+1e-6 for FP32, 5e-3 for FP16 / BF16 storage.  Sizes span several 128-site
+blocks with a ragged tail (Vh not a multiple of the block size) plus the
+8^4 random-SU(3) lattice of the FP64 workload and the 32^3 x 64 weak-field
+lattice of the FP32 even-odd workload.
+"""
+import numpy as np
+import pytest
+
+from conftest import parity_merge, parity_split, rel_l2
+from gpu_helpers import dev, empty_like_dev, handle_hop, host
+from paper_0710_2442_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"f64": 1e-13, "f32": 1e-6, "f16": 5e-3, "bf16": 5e-3}
+CPLX_PHASES = (np.exp(0.4j), 1.0, np.exp(-2.2j), -1.0)
+SHAPES = [(2, 2, 2, 2), (4, 4, 4, 4), (6, 4, 6, 10), (8, 6, 4, 10), (8, 8, 8, 8), (4, 2, 2, 2)]
+
+
+@pytest.fixture(scope="module")
+def w():
+    from paper_0710_2442_gb300 import build, wilson
+    build.build()
+    return wilson
+
+
+@pytest.mark.parametrize("dims", SHAPES)
+@pytest.mark.parametrize("op", ["hop", "m"])
+def test_f64_full_dslash(w, oracle_mod, dims, op):
+    U = inputs.gauge_field(dims, "random", seed=101)
+    psi = inputs.gaussian_spinor(dims, seed=102)
+    kappa = 0.125
+    L = w.lattice(dims, CPLX_PHASES)
+    out = empty_like_dev(psi)
+    w.wilson_dslash(out, dev(U), dev(psi), L, kappa, w.WILSON_OP_HOP if op == "hop" else w.WILSON_OP_M)
+    got = host(out)
+    want = oracle_mod.dslash(U, psi, dims, CPLX_PHASES) if op == "hop" else \
+        oracle_mod.wilson_m(U, psi, dims, kappa, CPLX_PHASES)
+    assert rel_l2(got, want) <= TOL["f64"]
+
+
+def test_f64_config_8x8x8x8_default_phases(w, oracle_mod):
+    cfg = inputs.WORKLOADS["dslash_f64_8^4"]
+    dims = cfg["dims"]
+    U = inputs.gauge_field(dims, cfg["gauge"], seed=cfg["gauge_seed"])
+    psi = inputs.gaussian_spinor(dims, seed=cfg["spinor_seed"])
+    L = w.lattice(dims)
+    for op in (w.WILSON_OP_M, w.WILSON_OP_HOP):
+        out = empty_like_dev(psi)
+        w.wilson_dslash(out, dev(U), dev(psi), L, cfg["kappa"], op)
+        want = oracle_mod.wilson_m(U, psi, dims, cfg["kappa"]) if op == w.WILSON_OP_M else \
+            oracle_mod.dslash(U, psi, dims)
+        assert rel_l2(host(out), want) <= TOL["f64"]
+
+
+@pytest.mark.parametrize("dims", SHAPES)
+@pytest.mark.parametrize("out_parity", [0, 1])
+def test_f64_eo_hop(w, oracle_mod, dims, out_parity):
+    U = inputs.gauge_field(dims, "random", seed=103)
+    src = inputs.gaussian_spinor(inputs.volume(dims) // 2, seed=104)
+    L = w.lattice(dims, CPLX_PHASES)
+    out = empty_like_dev(src)
+    w.wilson_dslash_eo(out, dev(U), dev(src), L, out_parity, 0.0, w.WILSON_OP_HOP)
+    want = oracle_mod.dslash_eo(U, src, dims, out_parity, CPLX_PHASES)
+    assert rel_l2(host(out), want) <= TOL["f64"]
+
+
+@pytest.mark.parametrize("dims", [(4, 4, 4, 4), (6, 4, 6, 10), (2, 2, 2, 4)])
+@pytest.mark.parametrize("parity", [0, 1])
+@pytest.mark.parametrize("dag", [False, True])
+def test_f64_schur(w, oracle_mod, dims, parity, dag):
+    U = inputs.gauge_field(dims, "random", seed=105)
+    src = inputs.gaussian_spinor(inputs.volume(dims) // 2, seed=106)
+    kappa = 0.135
+    L = w.lattice(dims, CPLX_PHASES)
+    out = empty_like_dev(src)
+    w.wilson_dslash_eo(out, dev(U), dev(src), L, parity, kappa,
+                       w.WILSON_OP_SCHUR_DAG if dag else w.WILSON_OP_SCHUR)
+    want = oracle_mod.schur(U, src, dims, kappa, parity, dag, CPLX_PHASES)
+    assert rel_l2(host(out), want) <= TOL["f64"]
+
+
+LOWP = [("f64", 18), ("f64", 12), ("f32", 12), ("f32", 18), ("f16", 12), ("bf16", 12)]
+
+
+@pytest.mark.parametrize("prec,recon", LOWP)
+@pytest.mark.parametrize("dims", [(6, 4, 6, 10), (8, 6, 4, 10), (4, 4, 4, 4)])
+@pytest.mark.parametrize("out_parity", [0, 1])
+def test_handle_eo_hop(w, oracle_mod, prec, recon, dims, out_parity):
+    U = inputs.gauge_field(dims, "weak", eps=0.3, seed=107)
+    src = inputs.gaussian_spinor(inputs.volume(dims) // 2, seed=108)
+    got = handle_hop(w, U, src, dims, CPLX_PHASES, w.PREC[prec], recon, 1 - out_parity, out_parity,
+                     w.WILSON_OP_HOP)
+    want = oracle_mod.dslash_eo(U, src, dims, out_parity, CPLX_PHASES)
+    assert rel_l2(got, want) <= TOL[prec]
+
+
+@pytest.mark.parametrize("prec,recon", LOWP)
+@pytest.mark.parametrize("op", ["hop", "m"])
+def test_handle_full(w, oracle_mod, prec, recon, op):
+    dims = (6, 4, 6, 10)
+    U = inputs.gauge_field(dims, "weak", eps=0.3, seed=109)
+    psi = inputs.gaussian_spinor(dims, seed=110)
+    kappa = 0.1350
+    got = handle_hop(w, U, psi, dims, CPLX_PHASES, w.PREC[prec], recon, w.WILSON_FULL, w.WILSON_FULL,
+                     w.WILSON_OP_HOP if op == "hop" else w.WILSON_OP_M, kappa)
+    want = oracle_mod.dslash(U, psi, dims, CPLX_PHASES) if op == "hop" else \
+        oracle_mod.wilson_m(U, psi, dims, kappa, CPLX_PHASES)
+    assert rel_l2(got, want) <= TOL[prec]
+
+
+def test_handle_multi_rhs_fields(w, oracle_mod):
+    """nrhs fields in one handle: each is applied independently."""
+    dims = (4, 4, 4, 6)
+    U = inputs.gauge_field(dims, "weak", eps=0.3, seed=111)
+    Vh = inputs.volume(dims) // 2
+    src = inputs.gaussian_spinor(Vh, seed=112, nrhs=3)
+    got = handle_hop(w, U, src, dims, CPLX_PHASES, w.WILSON_F32, 12, 1, 0, w.WILSON_OP_HOP, nrhs=3)
+    for k in range(3):
+        want = oracle_mod.dslash_eo(U, src[k], dims, 0, CPLX_PHASES)
+        assert rel_l2(got[k], want) <= TOL["f32"]
+
+
+def test_f32_eo_workload_32x32x32x64(w, oracle_mod):
+    """The FP32 even-odd workload at full size (Vh = 1,048,576), whole output
+    compared with the oracle, in the launch configuration the bench times."""
+    cfg = inputs.WORKLOADS["dslash_eo_f32_32^3x64"]
+    dims = cfg["dims"]
+    U = inputs.gauge_field(dims, cfg["gauge"], eps=cfg["eps"], seed=cfg["gauge_seed"])
+    src = inputs.gaussian_spinor(inputs.volume(dims) // 2, seed=cfg["spinor_seed"]).astype(np.complex64)
+    src = src.astype(np.complex128)  # the workload's spinor is complex64 data
+    got = handle_hop(w, U, src, dims, inputs.DEFAULT_PHASES, w.WILSON_F32, 12, 0, 1, w.WILSON_OP_HOP)
+    want = oracle_mod.dslash_eo(U, src, dims, 1)
+    assert rel_l2(got, want) <= TOL["f32"]
+
+
+def test_nan_sentinels_overwritten(w):
+    """Every output site is written (outputs start as NaN)."""
+    dims = (6, 4, 6, 10)
+    U = inputs.gauge_field(dims, "weak", eps=0.3, seed=113)
+    src = inputs.gaussian_spinor(inputs.volume(dims) // 2, seed=114)
+    for prec in ("f32", "f16"):
+        got = handle_hop(w, U, src, dims, inputs.DEFAULT_PHASES, w.PREC[prec], 12, 0, 1, w.WILSON_OP_HOP)
+        assert np.all(np.isfinite(got))
+
+
+def test_zero_field_f16_scale(w):
+    """A zero spinor has scale 0 and stays exactly zero through F16 storage."""
+    dims = (4, 4, 4, 4)
+    U = inputs.gauge_field(dims, "weak", eps=0.3, seed=115)
+    src = np.zeros((inputs.volume(dims) // 2, 4, 3), dtype=np.complex128)
+    got = handle_hop(w, U, src, dims, inputs.DEFAULT_PHASES, w.WILSON_F16, 12, 0, 1, w.WILSON_OP_HOP)
+    assert np.all(got == 0)

@@ -1,0 +1,103 @@
+"""GPU CG solves against the FP64 oracle.
+
+The binding check is each GPU solution's true residual |b - M x| / |b|
+recomputed by the oracle's FP64 Wilson matrix (<= 1e-10, the solve target,
+with 10% slack for the different summation order), plus agreement with the
+oracle's own solution within cond(M) * 1e-10.
+"""
+import numpy as np
+import pytest
+
+from conftest import rel_l2
+from gpu_helpers import dev, host
+from paper_0710_2442_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def w():
+    from paper_0710_2442_gb300 import build, wilson
+    build.build()
+    return wilson
+
+
+def solve(w, U, b, dims, kappa, inner, reliable=1, recon=None, maxiter=100000, tol=1e-10, phases=None, check=True):
+    phases = inputs.DEFAULT_PHASES if phases is None else phases
+    L = w.lattice(dims, phases)
+    p = w.solver_defaults(inner)
+    p.reliable = reliable
+    p.tol = tol
+    p.maxiter = maxiter
+    if recon is not None:
+        p.recon = recon
+    x = dev(np.zeros_like(b))
+    st = w.wilson_cg_solve(x, dev(U), dev(b), L, kappa, p, check=check)
+    return host(x), st
+
+
+def true_resid(oracle_mod, U, x, b, dims, kappa, phases=None):
+    r = b - oracle_mod.wilson_m(U, x, dims, kappa, phases)
+    return np.linalg.norm(r) / np.linalg.norm(b)
+
+
+@pytest.mark.parametrize("inner", ["f64", "f32", "f16", "bf16"])
+@pytest.mark.parametrize("reliable", [1, 0])
+def test_solve_matches_oracle(w, oracle_mod, inner, reliable):
+    dims = (4, 4, 4, 8)
+    kappa = 0.1350
+    U = inputs.gauge_field(dims, "weak", eps=0.3, seed=201)
+    b = inputs.gaussian_spinor(dims, seed=202)
+    x, st = solve(w, U, b, dims, kappa, w.PREC[inner], reliable)
+    assert st["rc"] == 0 and st["true_rel_resid"] <= 1e-10
+    assert true_resid(oracle_mod, U, x, b, dims, kappa) <= 1.1e-10
+    xo, info = oracle_mod.cg_solve(U, b, dims, kappa, tol=1e-12)
+    assert info["converged"]
+    # cond(M) of this 4^3 x 8 weak field is below 100: solutions agree to ~1e-8
+    assert rel_l2(x, xo) <= 1e-7
+
+
+def test_solve_complex_phases_random_field(w, oracle_mod):
+    dims = (4, 2, 4, 6)
+    kappa = 0.124
+    phases = (np.exp(0.7j), 1.0, np.exp(-1.9j), -1.0)
+    U = inputs.gauge_field(dims, "random", seed=203)
+    b = inputs.gaussian_spinor(dims, seed=204)
+    for inner in ("f64", "f32", "f16"):
+        x, st = solve(w, U, b, dims, kappa, w.PREC[inner], recon=18 if inner == "f64" else 12, phases=phases)
+        assert true_resid(oracle_mod, U, x, b, dims, kappa, phases) <= 1.1e-10
+
+
+def test_solve_ragged_lattice(w, oracle_mod):
+    dims = (6, 4, 6, 10)  # Vh = 720: several blocks and a ragged tail
+    kappa = 0.13
+    U = inputs.gauge_field(dims, "weak", eps=0.3, seed=205)
+    b = inputs.gaussian_spinor(dims, seed=206)
+    x, st = solve(w, U, b, dims, kappa, w.WILSON_F16)
+    assert true_resid(oracle_mod, U, x, b, dims, kappa) <= 1.1e-10
+
+
+def test_maxiter_reports_noconv(w):
+    dims = (4, 4, 4, 8)
+    U = inputs.gauge_field(dims, "weak", eps=0.3, seed=207)
+    b = inputs.gaussian_spinor(dims, seed=208)
+    x, st = solve(w, U, b, dims, 0.135, w.WILSON_F32, maxiter=5, check=False)
+    assert st["rc"] == w.WILSON_ERR_NOCONV
+    assert st["inner_iters"] <= 5 + 16
+
+
+def test_nan_source_reports_numeric(w):
+    dims = (4, 4, 4, 4)
+    U = inputs.gauge_field(dims, "weak", eps=0.3, seed=209)
+    b = inputs.gaussian_spinor(dims, seed=210)
+    b[5, 1, 2] = np.nan
+    x, st = solve(w, U, b, dims, 0.13, w.WILSON_F32, check=False)
+    assert st["rc"] == w.WILSON_ERR_NUMERIC
+
+
+def test_zero_source(w):
+    dims = (4, 4, 4, 4)
+    U = inputs.gauge_field(dims, "weak", eps=0.3, seed=211)
+    b = np.zeros((inputs.volume(dims), 4, 3), dtype=np.complex128)
+    x, st = solve(w, U, b, dims, 0.13, w.WILSON_F16)
+    assert st["rc"] == 0 and np.all(x == 0)
