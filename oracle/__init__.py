@@ -51,27 +51,31 @@ def build(force: bool = False) -> str:
     return _LIB_PATH
 
 
+def declare(lib):
+    """Set the ctypes signatures of an oracle library handle."""
+    dp = ctypes.POINTER(ctypes.c_double)
+    ip = ctypes.POINTER(ctypes.c_int)
+    lib.oracle_gamma.argtypes = [ctypes.c_int, dp]
+    lib.oracle_gamma.restype = None
+    lib.oracle_set_num_threads.argtypes = [ctypes.c_int]
+    lib.oracle_get_num_threads.restype = ctypes.c_int
+    lib.oracle_dslash.argtypes = [dp, dp, dp, ip, dp, ctypes.c_int]
+    lib.oracle_wilson_m.argtypes = [dp, dp, dp, ip, dp, ctypes.c_double]
+    lib.oracle_dslash_eo.argtypes = [dp, dp, dp, ip, dp, ctypes.c_int, ctypes.c_int]
+    lib.oracle_schur.argtypes = [dp, dp, dp, ip, dp, ctypes.c_double, ctypes.c_int, ctypes.c_int]
+    lib.oracle_cg.argtypes = [dp, dp, dp, ip, dp, ctypes.c_double, ctypes.c_double,
+                              ctypes.c_int, ip, dp]
+    for f in (lib.oracle_dslash, lib.oracle_wilson_m, lib.oracle_dslash_eo,
+              lib.oracle_schur, lib.oracle_cg):
+        f.restype = ctypes.c_int
+    return lib
+
+
 def _load():
     global _lib
     with _lock:
         if _lib is None:
-            lib = ctypes.CDLL(build())
-            dp = ctypes.POINTER(ctypes.c_double)
-            ip = ctypes.POINTER(ctypes.c_int)
-            lib.oracle_gamma.argtypes = [ctypes.c_int, dp]
-            lib.oracle_gamma.restype = None
-            lib.oracle_set_num_threads.argtypes = [ctypes.c_int]
-            lib.oracle_get_num_threads.restype = ctypes.c_int
-            lib.oracle_dslash.argtypes = [dp, dp, dp, ip, dp, ctypes.c_int]
-            lib.oracle_wilson_m.argtypes = [dp, dp, dp, ip, dp, ctypes.c_double]
-            lib.oracle_dslash_eo.argtypes = [dp, dp, dp, ip, dp, ctypes.c_int, ctypes.c_int]
-            lib.oracle_schur.argtypes = [dp, dp, dp, ip, dp, ctypes.c_double, ctypes.c_int, ctypes.c_int]
-            lib.oracle_cg.argtypes = [dp, dp, dp, ip, dp, ctypes.c_double, ctypes.c_double,
-                                      ctypes.c_int, ip, dp]
-            for f in (lib.oracle_dslash, lib.oracle_wilson_m, lib.oracle_dslash_eo,
-                      lib.oracle_schur, lib.oracle_cg):
-                f.restype = ctypes.c_int
-            _lib = lib
+            _lib = declare(ctypes.CDLL(build()))
     return _lib
 
 
