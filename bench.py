@@ -49,6 +49,8 @@ def parse():
     ap.add_argument("--no-solver", action="store_true", help="skip the CG comparison block")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--apps", type=int, default=None, help="applications per step (default 100)")
+    ap.add_argument("--prec", choices=["f32", "f16", "bf16"], default="f32",
+                    help="storage precision of spinors and links (the workload is f32)")
     return ap.parse_args()
 
 
@@ -169,9 +171,10 @@ def run_ours(args, ws, rank, local, fields):
     apps = args.apps or cfg["applications"]
     L = w.lattice(dims)
     stream = torch.cuda.current_stream(dev)
-    g = w.Gauge(U, L, w.WILSON_F32, 12, stream)
-    even = w.Spinor(L, w.WILSON_EVEN, w.WILSON_F32)
-    odd = w.Spinor(L, w.WILSON_ODD, w.WILSON_F32)
+    P = w.PREC[args.prec]
+    g = w.Gauge(U, L, P, 12, stream)
+    even = w.Spinor(L, w.WILSON_EVEN, P)
+    odd = w.Spinor(L, w.WILSON_ODD, P)
     src_dev = torch.from_numpy(src).to(dev)
     even.load(src_dev, stream)
 
@@ -202,7 +205,7 @@ def run_ours(args, ws, rank, local, fields):
     launches = args.steps * apps
     t_launch = ms / 1e3 / launches
     flops = model.FLOPS_PER_SITE * Vh
-    comp_bytes = model.compulsory_bytes_per_site("f32", 12, eo=True) * Vh
+    comp_bytes = model.compulsory_bytes_per_site(args.prec, 12, eo=True) * Vh
     gflops = flops * launches * ws / (ms / 1e3) / 1e9
     peak, peak_kind = measured_peaks()
     achieved = comp_bytes / t_launch / 1e9
@@ -235,8 +238,9 @@ def run_ours(args, ws, rank, local, fields):
     line = {
         "metric": METRIC, "value": round(gflops, 2), "unit": "GFlop/s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(ms / args.steps, 4), "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "dims": list(dims), "links": "f32 12-real", "spinor": "f32",
+        "scaling": "weak", "vs_baseline": None, "dtype": args.prec, "data": "synthetic",
+        "config": {"workload": WORKLOAD if args.prec == "f32" else WORKLOAD.replace("f32", args.prec),
+                   "dims": list(dims), "links": f"{args.prec} 12-real", "spinor": args.prec,
                    "kappa": cfg["kappa"], "applications_per_step": apps, "sites_per_application": Vh,
                    "l2": L2_NOTE, "parallelism": "replicas" if ws > 1 else "single"},
         "hbm_gbs": round(achieved * ws, 1),
