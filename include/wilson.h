@@ -171,6 +171,29 @@ int wilson_dslash_h(wilson_spinor* out, const wilson_gauge* g, const wilson_spin
                     int op, void* stream);
 
 /* ---------------------------------------------------------------------- */
+/* No-allocation variant (the paper has no counterpart; this is a service  */
+/* of the library).  For callers that cannot let a library allocate device */
+/* memory: work issued while a stream is captured into a CUDA graph, hosts */
+/* whose allocator owns the whole device, loops that must not block in    */
+/* cudaMalloc/cudaFree.                                                     */
+/* ---------------------------------------------------------------------- */
+#define WILSON_NOALLOC_SCRATCH_BYTES (32u << 20)
+
+/* Same arguments, result and precision (FP64, 18-real links) as
+ * wilson_dslash_eo, but the packed fields live in one fixed device array of
+ * WILSON_NOALLOC_SCRATCH_BYTES (32 MiB) that every GPU loading the library
+ * holds until exit; nothing is allocated or freed.  Fits lattices with
+ * V/2 up to about 19,000 sites (8^4, 12^4, 8^3 x 32); larger ones return
+ * WILSON_ERR_ARG before any work.  The first call on a device resolves the
+ * array's address on that device: make it before any stream capture.  The
+ * call is asynchronous on the stream and does not synchronise.  All calls on
+ * a device share the array (it keeps the last call's contents; nothing in it
+ * needs clearing): calls whose GPU work overlaps race and must be serialised
+ * by the caller. */
+int wilson_dslash_eo_noalloc(double* out, const double* gauge, const double* in, const wilson_lattice* L,
+                             int out_parity, double kappa, int op, void* stream);
+
+/* ---------------------------------------------------------------------- */
 /* Errors and version                                                      */
 /* ---------------------------------------------------------------------- */
 const char* wilson_last_error(void);

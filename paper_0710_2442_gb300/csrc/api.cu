@@ -117,6 +117,8 @@ SolveStream& solve_stream() {
 
 }  // namespace
 
+void wl::record_error(const std::string& msg) { g_last_error = msg; }
+
 struct wilson_gauge_s {
     GaugeField f;
 };

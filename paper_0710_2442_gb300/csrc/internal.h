@@ -147,4 +147,7 @@ void convert_block(Prec dst_p, void* dst, Prec src_p, const void* src, const Geo
 
 int device_sm_count();
 
+// Set the calling thread's message returned by wilson_last_error().
+void record_error(const std::string& msg);
+
 }  // namespace wl

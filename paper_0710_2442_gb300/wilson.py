@@ -57,6 +57,7 @@ def _declare(lib):
     sig = {
         "wilson_dslash": (I, [VP, VP, VP, P(wilson_lattice), D, I, VP]),
         "wilson_dslash_eo": (I, [VP, VP, VP, P(wilson_lattice), I, D, I, VP]),
+        "wilson_dslash_eo_noalloc": (I, [VP, VP, VP, P(wilson_lattice), I, D, I, VP]),
         "wilson_cg_solve": (I, [VP, VP, VP, P(wilson_lattice), D, P(wilson_solver_params),
                                 P(wilson_solve_stats), VP]),
         "wilson_solver_defaults": (wilson_solver_params, [I]),
@@ -137,6 +138,14 @@ def wilson_dslash_eo(out, gauge, inp, L: wilson_lattice, out_parity: int, kappa:
                      op: int = WILSON_OP_HOP, stream=None):
     _check(lib().wilson_dslash_eo(_ptr(out), _ptr(gauge), _ptr(inp), ctypes.byref(L), int(out_parity),
                                   float(kappa), int(op), _stream(stream)))
+
+
+def wilson_dslash_eo_noalloc(out, gauge, inp, L: wilson_lattice, out_parity: int, kappa: float = 0.0,
+                             op: int = WILSON_OP_HOP, stream=None):
+    """wilson_dslash_eo without device allocation (fixed 32 MiB scratch array;
+    asynchronous; overlapping calls race)."""
+    _check(lib().wilson_dslash_eo_noalloc(_ptr(out), _ptr(gauge), _ptr(inp), ctypes.byref(L), int(out_parity),
+                                          float(kappa), int(op), _stream(stream)))
 
 
 def solver_defaults(inner: int) -> wilson_solver_params:

@@ -1,0 +1,73 @@
+"""wilson_dslash_eo_noalloc: the even-odd operator without device allocation.
+
+It exists for callers that cannot let the library call cudaMalloc (work
+issued during CUDA-graph capture, hosts whose allocator owns the device,
+loops that must not block in the allocator).  Checked through the C ABI
+against wilson_dslash_eo, the allocating entry point with the same
+semantics, at the FP64 tolerance (1e-13 relative L2), on two calls in a row
+(the second sees the first call's leftovers in the shared scratch array).
+This file is collected last on purpose.
+"""
+import numpy as np
+import pytest
+
+from conftest import rel_l2
+from gpu_helpers import dev, empty_like_dev, host
+from paper_0710_2442_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+PHASES = (np.exp(0.4j), 1.0, np.exp(-2.2j), -1.0)
+
+
+@pytest.fixture(scope="module")
+def w():
+    from paper_0710_2442_gb300 import build, wilson
+    build.build()
+    return wilson
+
+
+def reference(w, U, src, L, parity, kappa, op):
+    out = empty_like_dev(src)
+    w.wilson_dslash_eo(out, U, src, L, parity, kappa, op)
+    return host(out)
+
+
+def test_noalloc_matches_allocating_call_twice(w):
+    import torch
+    dims = (12, 12, 12, 12)  # V/2 = 10368: near the scratch's range, several blocks
+    L = w.lattice(dims, PHASES)
+    U = dev(inputs.gauge_field(dims, "random", seed=301))
+    Vh = inputs.volume(dims) // 2
+    calls = [(dev(inputs.gaussian_spinor(Vh, seed=302)), 1, 0.0, w.WILSON_OP_HOP),
+             (dev(inputs.gaussian_spinor(Vh, seed=303)), 0, 0.1350, w.WILSON_OP_SCHUR)]
+    for src, parity, kappa, op in calls:
+        out = empty_like_dev(np.zeros((Vh, 4, 3)))
+        w.wilson_dslash_eo_noalloc(out, U, src, L, parity, kappa, op)
+        torch.cuda.synchronize()
+        got = host(out)
+        want = reference(w, U, src, L, parity, kappa, op)
+        assert rel_l2(got, want) <= 1e-13
+
+
+def test_noalloc_small_lattice_and_dagger(w):
+    import torch
+    dims = (4, 4, 4, 8)
+    L = w.lattice(dims, PHASES)
+    U = dev(inputs.gauge_field(dims, "random", seed=304))
+    Vh = inputs.volume(dims) // 2
+    src = dev(inputs.gaussian_spinor(Vh, seed=305))
+    for op in (w.WILSON_OP_SCHUR_DAG, w.WILSON_OP_HOP):
+        out = empty_like_dev(np.zeros((Vh, 4, 3)))
+        w.wilson_dslash_eo_noalloc(out, U, src, L, 1, 0.125, op)
+        torch.cuda.synchronize()
+        assert rel_l2(host(out), reference(w, U, src, L, 1, 0.125, op)) <= 1e-13
+
+
+def test_noalloc_rejects_lattice_beyond_scratch(w):
+    dims = (16, 16, 16, 16)  # V/2 = 32768 needs ~57 MB of packed fields
+    L = w.lattice(dims)
+    buf = dev(np.zeros((64, 4, 3)))
+    with pytest.raises(w.WilsonError, match="too large") as e:
+        w.wilson_dslash_eo_noalloc(buf, buf, dev(np.zeros((64, 4, 3))), L, 0)
+    assert e.value.code == w.WILSON_ERR_ARG
