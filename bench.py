@@ -267,6 +267,9 @@ def run_solver_block(w, torch, dev, stream):
                        ("f32", w.WILSON_F32)):
         x = torch.zeros_like(bd)
         p = w.solver_defaults(prec)
+        # the first solve tunes the launch configurations; time the second
+        w.wilson_cg_solve(x, Ud, bd, L, cfg["kappa"], p, stream, check=False)
+        x.zero_()
         st = w.wilson_cg_solve(x, Ud, bd, L, cfg["kappa"], p, stream, check=False)
         res[name] = {"seconds": round(st["seconds"], 4), "inner_iters": st["inner_iters"],
                      "outer_iters": st["outer_iters"], "hops": st["hop_applications"],

@@ -149,6 +149,12 @@ struct SpinorFmt<P_F64> {
             v[c] = {d.x, d.y};
         }
     }
+    // unscaled format: the scale is the constant 1 and folds away
+    __device__ static __forceinline__ void load_raw(const void* base, int stride, int i, cpx<double> v[12],
+                                                    double& s) {
+        load(base, stride, i, v);
+        s = 1.0;
+    }
     __device__ static __forceinline__ void store(void* base, int stride, int i, const cpx<double> v[12]) {
         double2* b = static_cast<double2*>(base) + i;
 #pragma unroll
@@ -171,6 +177,11 @@ struct SpinorFmt<P_F32> {
             v[2 * c] = {d.x, d.y};
             v[2 * c + 1] = {d.z, d.w};
         }
+    }
+    __device__ static __forceinline__ void load_raw(const void* base, int stride, int i, cpx<float> v[12],
+                                                    float& s) {
+        load(base, stride, i, v);
+        s = 1.0f;
     }
     __device__ static __forceinline__ void store(void* base, int stride, int i, const cpx<float> v[12]) {
         float4* b = static_cast<float4*>(base) + i;
@@ -206,6 +217,22 @@ struct SpinorLowFmt {
             v[4 * c + 1] = {f1.x * s, f1.y * s};
             v[4 * c + 2] = {f2.x * s, f2.y * s};
             v[4 * c + 3] = {f3.x * s, f3.y * s};
+        }
+    }
+    // The stored values q (|q| <= 1) and the site's scale separately: the
+    // hopping kernel applies the scale in its accumulation FMA for free.
+    __device__ static __forceinline__ void load_raw(const void* base, int stride, int i, cpx<float> v[12],
+                                                    float& s) {
+        const uint4* b = static_cast<const uint4*>(base) + i;
+        s = load_scale(base, stride, i);
+#pragma unroll
+        for (int c = 0; c < 3; c++) {
+            uint4 d = __ldg(b + (size_t)c * stride);
+            float2 f0 = LT::to_f2(d.x), f1 = LT::to_f2(d.y), f2 = LT::to_f2(d.z), f3 = LT::to_f2(d.w);
+            v[4 * c + 0] = {f0.x, f0.y};
+            v[4 * c + 1] = {f1.x, f1.y};
+            v[4 * c + 2] = {f2.x, f2.y};
+            v[4 * c + 3] = {f3.x, f3.y};
         }
     }
     __device__ static __forceinline__ void store(void* base, int stride, int i, const cpx<float> v[12]) {

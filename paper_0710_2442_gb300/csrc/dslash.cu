@@ -1,213 +1,12 @@
-// dslash.cu -- the Wilson hopping term (QCD on the Cell BE, Sec. 5, Eq. 3)
-// as a CUDA stencil on SoA fields.
-//
-// One thread computes one output site of one parity.  For each of the 8 hops
-// it loads the neighbour spinor (coalesced 16-byte loads), projects it to a
-// half spinor with (1 -/+ g_mu) in the DeGrand-Rossi basis (6 complex adds),
-// applies the boundary phase when the hop wraps, loads the link (12 or 18
-// reals; 12 are completed by the conjugate cross product), multiplies the two
-// colour vectors by U or U^dag (2 x 66 flops), and expands the product back
-// into the 4-spinor accumulator (12 complex adds).  That is the 1320
-// flops/site of Sec. 5.  The epilogue scales, optionally adds a field of the
-// output parity (out = x + a D in), stores at the storage precision and
-// optionally reduces |out|^2 into a deterministic FP64 grid reduction.
-//
-// The "dagger" variant swaps the two projectors.  Since g_5 (1 -/+ g_mu) g_5
-// = (1 +/- g_mu), it applies g_5 D g_5 = D^dag, which gives the adjoint
-// Schur operator Mhat^dag = 1 - kappa^2 D'_eo D'_oe without any g_5 passes.
-#include "internal.h"
+// dslash.cu -- host-side dispatch of the hopping-term kernels (device code in
+// dslash_impl.cuh): picks the instantiation for the storage precisions and
+// link format, and the launch configuration from the autotuner.
+#include <cstdio>
+#include <string>
+
+#include "dslash_impl.cuh"
 
 namespace wl {
-
-// Half-spinor projection (1 - S g_mu) psi, DeGrand-Rossi basis.  Only the
-// upper two spin components are independent; the lower two are recovered in
-// expand().  v[k], k = spin*3 + colour; h[k], k = halfspin*3 + colour.
-template <int MU, int S, class T>
-__device__ __forceinline__ void project(const cpx<T> v[12], cpx<T> h[6]) {
-#pragma unroll
-    for (int c = 0; c < 3; c++) {
-        const cpx<T> p0 = v[c], p1 = v[3 + c], p2 = v[6 + c], p3 = v[9 + c];
-        cpx<T> h0, h1;
-        if (MU == 0) {  // (1 - S g_1):  h0 = p0 - S i p3,  h1 = p1 - S i p2
-            h0 = S > 0 ? csub(p0, ci(p3)) : cadd(p0, ci(p3));
-            h1 = S > 0 ? csub(p1, ci(p2)) : cadd(p1, ci(p2));
-        } else if (MU == 1) {  // h0 = p0 + S p3,  h1 = p1 - S p2
-            h0 = S > 0 ? cadd(p0, p3) : csub(p0, p3);
-            h1 = S > 0 ? csub(p1, p2) : cadd(p1, p2);
-        } else if (MU == 2) {  // h0 = p0 - S i p2,  h1 = p1 + S i p3
-            h0 = S > 0 ? csub(p0, ci(p2)) : cadd(p0, ci(p2));
-            h1 = S > 0 ? cadd(p1, ci(p3)) : csub(p1, ci(p3));
-        } else {  // h0 = p0 - S p2,  h1 = p1 - S p3
-            h0 = S > 0 ? csub(p0, p2) : cadd(p0, p2);
-            h1 = S > 0 ? csub(p1, p3) : cadd(p1, p3);
-        }
-        h[c] = h0;
-        h[3 + c] = h1;
-    }
-}
-
-// acc += (1 - S g_mu)-image of the half spinor w:  the full 4-spinor is
-// (w0, w1, lower2, lower3) with the lower components fixed by the projector.
-template <int MU, int S, bool FIRST, class T>
-__device__ __forceinline__ void expand(cpx<T> acc[12], const cpx<T> w[6]) {
-#pragma unroll
-    for (int c = 0; c < 3; c++) {
-        const cpx<T> w0 = w[c], w1 = w[3 + c];
-        cpx<T> l2, l3;
-        if (MU == 0) {  // lower = (S i w1, S i w0)
-            l2 = S > 0 ? ci(w1) : cneg(ci(w1));
-            l3 = S > 0 ? ci(w0) : cneg(ci(w0));
-        } else if (MU == 1) {  // (-S w1, S w0)
-            l2 = S > 0 ? cneg(w1) : w1;
-            l3 = S > 0 ? w0 : cneg(w0);
-        } else if (MU == 2) {  // (S i w0, -S i w1)
-            l2 = S > 0 ? ci(w0) : cneg(ci(w0));
-            l3 = S > 0 ? cneg(ci(w1)) : ci(w1);
-        } else {  // (-S w0, -S w1)
-            l2 = S > 0 ? cneg(w0) : w0;
-            l3 = S > 0 ? cneg(w1) : w1;
-        }
-        if (FIRST) {
-            acc[c] = w0;
-            acc[3 + c] = w1;
-            acc[6 + c] = l2;
-            acc[9 + c] = l3;
-        } else {
-            acc[c] = cadd(acc[c], w0);
-            acc[3 + c] = cadd(acc[3 + c], w1);
-            acc[6 + c] = cadd(acc[6 + c], l2);
-            acc[9 + c] = cadd(acc[9 + c], l3);
-        }
-    }
-}
-
-// w = U h (ADJ = false) or U^dag h (ADJ = true), for both half-spin rows.
-template <bool ADJ, class T>
-__device__ __forceinline__ void su3_mul(const cpx<T> U[3][3], const cpx<T> h[6], cpx<T> w[6]) {
-#pragma unroll
-    for (int a = 0; a < 2; a++) {
-#pragma unroll
-        for (int i = 0; i < 3; i++) {
-            cpx<T> r;
-            if (!ADJ) {
-                r = cmul(U[i][0], h[3 * a + 0]);
-                r = cfma(U[i][1], h[3 * a + 1], r);
-                r = cfma(U[i][2], h[3 * a + 2], r);
-            } else {
-                r = cjmul(U[0][i], h[3 * a + 0]);
-                r = cjfma(U[1][i], h[3 * a + 1], r);
-                r = cjfma(U[2][i], h[3 * a + 2], r);
-            }
-            w[3 * a + i] = r;
-        }
-    }
-}
-
-struct HopParams {
-    char* out;
-    const char* in;
-    const char* x;
-    long long out_pstep, in_pstep, x_pstep;
-    const char* gauge;
-    Geom g;
-    int out_parity;
-    int full;
-    int xpay;
-    double a;
-    RedArgs red;
-    int reduce;
-    const int* skip;
-};
-
-// One direction mu: forward and backward hop into acc.
-template <int SP, int GP, int R, bool DAG, int MU, bool FIRST>
-__device__ __forceinline__ void hop_dir(cpx<typename SpinorFmt<SP>::real> acc[12], const HopParams& P,
-                                        const char* in, int p, int h, const int c[4], int s) {
-    using SF = SpinorFmt<SP>;
-    using GF = GaugeFmt<GP, R>;
-    using T = typename SF::real;
-    const Geom& g = P.g;
-    const int L = g.L[MU];
-    const int smu = MU == 0 ? 1 : MU == 1 ? g.L[0] : MU == 2 ? g.L[0] * g.L[1] : g.L[0] * g.L[1] * g.L[2];
-    constexpr int SF_ = DAG ? -1 : 1;  // projector sign of the forward hop
-    // ---- forward: (1 - S g_mu) eta U_{x,mu} psi_{x+mu}
-    {
-        const bool wrap = c[MU] == L - 1;
-        const int sn = wrap ? s - (L - 1) * smu : s + smu;
-        cpx<T> v[12], hs[6], w[6], U[3][3];
-        SF::load(in, g.stride, sn >> 1, v);
-        GF::load(P.gauge, g.stride, p * 4 + MU, h, U);
-        project<MU, SF_>(v, hs);
-        if (wrap) {
-            const cpx<T> eta = {(T)g.ph[MU][0], (T)g.ph[MU][1]};
-#pragma unroll
-            for (int k = 0; k < 6; k++) hs[k] = cmul(eta, hs[k]);
-        }
-        su3_mul<false>(U, hs, w);
-        expand<MU, SF_, FIRST>(acc, w);
-    }
-    // ---- backward: (1 + S g_mu) eta* U^dag_{x-mu,mu} psi_{x-mu}
-    {
-        const bool wrap = c[MU] == 0;
-        const int sn = wrap ? s + (L - 1) * smu : s - smu;
-        const int hn = sn >> 1;
-        cpx<T> v[12], hs[6], w[6], U[3][3];
-        SF::load(in, g.stride, hn, v);
-        GF::load(P.gauge, g.stride, (1 - p) * 4 + MU, hn, U);
-        project<MU, -SF_>(v, hs);
-        if (wrap) {
-            const cpx<T> eta = {(T)g.ph[MU][0], -(T)g.ph[MU][1]};
-#pragma unroll
-            for (int k = 0; k < 6; k++) hs[k] = cmul(eta, hs[k]);
-        }
-        su3_mul<true>(U, hs, w);
-        expand<MU, -SF_, false>(acc, w);
-    }
-}
-
-template <int SP, int GP, int R, bool DAG>
-__global__ void __launch_bounds__(256) hop_kernel(const HopParams P) {
-    using SF = SpinorFmt<SP>;
-    using T = typename SF::real;
-    if (P.skip && __ldcg(P.skip)) return;
-    const int p = P.full ? (int)blockIdx.y : P.out_parity;
-    const int pin = 1 - p;
-    char* out = P.out + (P.full ? p * P.out_pstep : 0);
-    const char* in = P.in + (P.full ? pin * P.in_pstep : 0);
-    const char* x = P.x ? P.x + (P.full ? p * P.x_pstep : 0) : nullptr;
-    const Geom& g = P.g;
-    const T a = (T)P.a;
-    double nrm = 0.0;
-    for (int h = blockIdx.x * blockDim.x + threadIdx.x; h < g.Vh; h += gridDim.x * blockDim.x) {
-        int c[4], s;
-        site_of_half(h, p, g, c, s);
-        cpx<T> acc[12];
-        hop_dir<SP, GP, R, DAG, 0, true>(acc, P, in, p, h, c, s);
-        hop_dir<SP, GP, R, DAG, 1, false>(acc, P, in, p, h, c, s);
-        hop_dir<SP, GP, R, DAG, 2, false>(acc, P, in, p, h, c, s);
-        hop_dir<SP, GP, R, DAG, 3, false>(acc, P, in, p, h, c, s);
-        if (P.xpay) {
-            cpx<T> xv[12];
-            SF::load(x, g.stride, h, xv);
-#pragma unroll
-            for (int k = 0; k < 12; k++) {
-                acc[k].re = fma(a, acc[k].re, xv[k].re);
-                acc[k].im = fma(a, acc[k].im, xv[k].im);
-            }
-        } else if (P.a != 1.0) {
-#pragma unroll
-            for (int k = 0; k < 12; k++) acc[k] = cscale(a, acc[k]);
-        }
-        if (P.reduce) {
-            T n2 = 0;
-#pragma unroll
-            for (int k = 0; k < 12; k++) n2 += cnorm2(acc[k]);
-            nrm += (double)n2;
-        }
-        SF::store(out, g.stride, h, acc);
-    }
-    if (P.reduce) grid_reduce(nrm, P.red);
-}
 
 int device_sm_count() {
     static int sms[64] = {0};
@@ -228,13 +27,15 @@ int hop_grid_blocks(const Geom& g, int block, int grid_cap) {
     return blocks < 1 ? 1 : blocks;
 }
 
-template <int SP, int GP, int R>
-static void launch_t(const HopParams& P, int block, int blocks, int ny, bool dag, cudaStream_t st) {
-    dim3 grid(blocks, ny);
-    if (dag)
-        hop_kernel<SP, GP, R, true><<<grid, block, 0, st>>>(P);
-    else
-        hop_kernel<SP, GP, R, false><<<grid, block, 0, st>>>(P);
+static void dispatch(const HopParams& P, Prec sp, Prec gp, int R, int block, int blocks, int ny, bool dag,
+                     int variant, cudaStream_t st) {
+    if (sp == P_F64 && gp == P_F64 && R == 18) launch_hop_prec<P_F64, P_F64, 18>(P, block, blocks, ny, dag, variant, st);
+    else if (sp == P_F64 && gp == P_F64 && R == 12) launch_hop_prec<P_F64, P_F64, 12>(P, block, blocks, ny, dag, variant, st);
+    else if (sp == P_F32 && gp == P_F32 && R == 12) launch_hop_prec<P_F32, P_F32, 12>(P, block, blocks, ny, dag, variant, st);
+    else if (sp == P_F32 && gp == P_F32 && R == 18) launch_hop_prec<P_F32, P_F32, 18>(P, block, blocks, ny, dag, variant, st);
+    else if (sp == P_F16 && gp == P_F16 && R == 12) launch_hop_prec<P_F16, P_F16, 12>(P, block, blocks, ny, dag, variant, st);
+    else if (sp == P_BF16 && gp == P_BF16 && R == 12) launch_hop_prec<P_BF16, P_BF16, 12>(P, block, blocks, ny, dag, variant, st);
+    else throw Error(7, "unsupported spinor/gauge precision and link-storage combination");
 }
 
 void launch_hop(const HopLaunch& L, cudaStream_t st) {
@@ -252,25 +53,35 @@ void launch_hop(const HopLaunch& L, cudaStream_t st) {
     P.full = L.full;
     P.xpay = L.xpay;
     P.a = L.a;
-    P.reduce = L.red != nullptr;
-    if (L.red) P.red = *L.red;
-    else P.red = RedArgs{};
+    P.reduce = 0;
+    P.red = RedArgs{};
     P.skip = L.skip;
     WL_REQUIRE(!L.xpay || L.x, "xpay needs a field");
-    const int block = L.block > 0 ? L.block : 128;
-    const int blocks = hop_grid_blocks(P.g, block, L.grid_cap);
     const int ny = L.full ? 2 : 1;
     const bool dag = L.dagger != 0;
-    const Prec sp = L.sprec;
-    const Prec gp = gf.prec;
+    const Prec sp = L.sprec, gp = gf.prec;
     const int R = gf.recon;
-    if (sp == P_F64 && gp == P_F64 && R == 18) launch_t<P_F64, P_F64, 18>(P, block, blocks, ny, dag, st);
-    else if (sp == P_F64 && gp == P_F64 && R == 12) launch_t<P_F64, P_F64, 12>(P, block, blocks, ny, dag, st);
-    else if (sp == P_F32 && gp == P_F32 && R == 12) launch_t<P_F32, P_F32, 12>(P, block, blocks, ny, dag, st);
-    else if (sp == P_F32 && gp == P_F32 && R == 18) launch_t<P_F32, P_F32, 18>(P, block, blocks, ny, dag, st);
-    else if (sp == P_F16 && gp == P_F16 && R == 12) launch_t<P_F16, P_F16, 12>(P, block, blocks, ny, dag, st);
-    else if (sp == P_BF16 && gp == P_BF16 && R == 12) launch_t<P_BF16, P_BF16, 12>(P, block, blocks, ny, dag, st);
-    else throw Error(7, "unsupported spinor/gauge precision and link-storage combination");
+
+    LaunchConfig cfg;
+    if (L.block > 0) {
+        cfg.block = L.block;
+        cfg.variant = L.variant;
+    } else {
+        char key[160];
+        snprintf(key, sizeof(key), "hop:s%d:g%d:r%d:d%d:f%d:x%d:%dx%dx%dx%d", (int)sp, (int)gp, R, (int)dag, L.full,
+                 L.xpay, P.g.L[0], P.g.L[1], P.g.L[2], P.g.L[3]);
+        // tuning launches never reduce: the finishers are not idempotent
+        const HopParams Pt = P;
+        cfg = tune_launch(key, hop_candidates(), LaunchConfig{}, st, [&](const LaunchConfig& c) {
+            dispatch(Pt, sp, gp, R, c.block, hop_grid_blocks(Pt.g, c.block, 0), ny, dag, c.variant, st);
+        });
+    }
+    if (L.red) {
+        P.reduce = 1;
+        P.red = *L.red;
+    }
+    const int blocks = hop_grid_blocks(P.g, cfg.block, L.red ? L.grid_cap : 0);
+    dispatch(P, sp, gp, R, cfg.block, blocks, ny, dag, cfg.variant, st);
     WL_LAUNCH_CHECK();
 }
 

@@ -1,0 +1,9 @@
+// dslash_f32.cu -- instantiates the hopping-term kernels for one storage
+// precision family (see dslash_impl.cuh), so that the families compile in
+// parallel.
+#include "dslash_impl.cuh"
+
+namespace wl {
+template void launch_hop_prec<P_F32, P_F32, 12>(const HopParams&, int, int, int, bool, int, cudaStream_t);
+template void launch_hop_prec<P_F32, P_F32, 18>(const HopParams&, int, int, int, bool, int, cudaStream_t);
+}  // namespace wl

@@ -2,8 +2,10 @@
 // libwilson_gb300 (not part of the C ABI).
 #pragma once
 
+#include <functional>
 #include <stdexcept>
 #include <string>
+#include <vector>
 
 #include "common.cuh"
 #include "reduce.cuh"
@@ -60,6 +62,24 @@ struct DevBuf {
     template <class T>
     T* as() const { return static_cast<T*>(p); }
 };
+
+// ---------------------------------------------------------------------------
+// autotuner (tune.cu)
+// ---------------------------------------------------------------------------
+struct LaunchConfig {
+    int block = 128;
+    int variant = 0;
+};
+
+// The launch configuration for `key`.  On the first request (and when tuning
+// is enabled, WILSON_TUNE != 0, and the stream is not being captured) every
+// candidate is timed by running `run` on the stream with CUDA events, and the
+// fastest is cached (in memory, and in the file named by WILSON_TUNE_CACHE if
+// set).  `run` must be idempotent: it is executed several times.
+LaunchConfig tune_launch(const std::string& key, const std::vector<LaunchConfig>& candidates,
+                         const LaunchConfig& fallback, cudaStream_t st,
+                         const std::function<void(const LaunchConfig&)>& run);
+const std::vector<LaunchConfig>& hop_candidates();
 
 // Geometry from dims and phases; stride rounded up to 64 sites.
 Geom make_geom(const int dims[4], const double ph[4][2]);
@@ -130,8 +150,9 @@ struct HopLaunch {
     double a;
     const RedArgs* red;    // |out|^2 into a reducer, or null
     const int* skip;       // device flag: nonzero -> the launch does nothing
-    int block;             // threads per block (0 = default)
-    int grid_cap;          // max blocks (0 = no cap)
+    int block;             // threads per block (0 = autotuned)
+    int variant;           // kernel register-budget variant when block > 0
+    int grid_cap;          // max blocks of a reducing launch (0 = no cap)
 };
 void launch_hop(const HopLaunch& L, cudaStream_t st);
 int hop_grid_blocks(const Geom& g, int block, int grid_cap);

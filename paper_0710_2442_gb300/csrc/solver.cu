@@ -171,6 +171,13 @@ SolveStats cg_solve_prepared(SpinorField& x, const SpinorField& b, const GaugeFi
         cg_p_update(in.ip, in.p.block(0), in.r.block(0), g, sc, s);
     };
 
+    // Tune the operator launches before capture (tuning cannot run inside a
+    // captured stream).  The launches below only write scratch fields.
+    WL_CUDA(cudaMemsetAsync(in.p.block(0), 0, in.p.pbytes, st));
+    for (int dag = 0; dag < 2; dag++)
+        schur_apply(glo, in.ip, in.q.block(0), in.p.block(0), in.t.block(1), kappa, dag, nullptr, nullptr, 0, st);
+    schur_apply(g64, P_F64, q64.block(0), x.block(0), t64.block(1), kappa, 0, nullptr, nullptr, 0, st);
+
     const int chunk = prm.chunk > 0 ? prm.chunk : 16;
     if (prm.use_graph) {
         WL_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));

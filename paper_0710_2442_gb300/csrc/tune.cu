@@ -1,0 +1,139 @@
+// tune.cu -- the launch-configuration autotuner.
+//
+// A launch is identified by a key (kernel, precisions, link format, flags,
+// lattice extents).  The first time a key is seen the candidates are timed
+// on the caller's stream with CUDA events (one warm-up launch, then the best
+// of three timed launches each) and the fastest is kept.  Tuning synchronises
+// the stream, so the first call for a new key is slower; it is skipped while
+// the stream is being captured into a graph (the fallback is used and the
+// key is not stored).
+//
+// Environment:
+//   WILSON_TUNE=0            never time candidates (use the fallback)
+//   WILSON_TUNE_CACHE=path   load decisions from / append them to a file
+//   WILSON_TUNE_VERBOSE=1    report decisions on stderr
+#include <cstdio>
+#include <cstdlib>
+#include <fstream>
+#include <map>
+#include <mutex>
+#include <sstream>
+
+#include "internal.h"
+
+namespace wl {
+
+namespace {
+
+struct Entry {
+    LaunchConfig cfg;
+    float us;
+};
+
+std::mutex g_mutex;
+std::map<std::string, Entry>* g_cache = nullptr;
+bool g_loaded = false;
+
+bool env_flag(const char* name, bool dflt) {
+    const char* v = std::getenv(name);
+    if (!v || !*v) return dflt;
+    return !(v[0] == '0' && v[1] == 0);
+}
+
+std::string device_tag() {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceProp prop;
+    if (cudaGetDeviceProperties(&prop, dev) != cudaSuccess) {
+        cudaGetLastError();
+        return "dev?";
+    }
+    char buf[64];
+    snprintf(buf, sizeof(buf), "sm%d%d-%d", prop.major, prop.minor, prop.multiProcessorCount);
+    return buf;
+}
+
+void load_file() {
+    g_loaded = true;
+    const char* path = std::getenv("WILSON_TUNE_CACHE");
+    if (!path || !*path) return;
+    std::ifstream f(path);
+    std::string line;
+    while (std::getline(f, line)) {
+        std::istringstream is(line);
+        std::string key;
+        Entry e;
+        if (is >> key >> e.cfg.block >> e.cfg.variant >> e.us) (*g_cache)[key] = e;
+    }
+}
+
+void append_file(const std::string& key, const Entry& e) {
+    const char* path = std::getenv("WILSON_TUNE_CACHE");
+    if (!path || !*path) return;
+    std::ofstream f(path, std::ios::app);
+    f << key << ' ' << e.cfg.block << ' ' << e.cfg.variant << ' ' << e.us << '\n';
+}
+
+}  // namespace
+
+const std::vector<LaunchConfig>& hop_candidates() {
+    static const std::vector<LaunchConfig> c = [] {
+        std::vector<LaunchConfig> v;
+        for (int block : {64, 128, 256})
+            for (int var = 0; var < 3; var++) v.push_back(LaunchConfig{block, var});
+        return v;
+    }();
+    return c;
+}
+
+LaunchConfig tune_launch(const std::string& key0, const std::vector<LaunchConfig>& candidates,
+                         const LaunchConfig& fallback, cudaStream_t st,
+                         const std::function<void(const LaunchConfig&)>& run) {
+    const std::string key = device_tag() + "|" + key0;
+    {
+        std::lock_guard<std::mutex> lk(g_mutex);
+        if (!g_cache) g_cache = new std::map<std::string, Entry>();
+        if (!g_loaded) load_file();
+        auto it = g_cache->find(key);
+        if (it != g_cache->end()) return it->second.cfg;
+    }
+    if (!env_flag("WILSON_TUNE", true) || candidates.empty()) return fallback;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    WL_CUDA(cudaStreamIsCapturing(st, &cs));
+    if (cs != cudaStreamCaptureStatusNone) return fallback;
+
+    cudaEvent_t e0, e1;
+    WL_CUDA(cudaEventCreate(&e0));
+    WL_CUDA(cudaEventCreate(&e1));
+    Entry best{fallback, 1e30f};
+    for (const LaunchConfig& c : candidates) {
+        run(c);  // warm-up
+        if (cudaGetLastError() != cudaSuccess) continue;  // candidate not launchable here
+        float ms_best = 1e30f;
+        for (int rep = 0; rep < 3; rep++) {
+            WL_CUDA(cudaEventRecord(e0, st));
+            run(c);
+            WL_CUDA(cudaEventRecord(e1, st));
+            WL_CUDA(cudaEventSynchronize(e1));
+            float ms = 0.f;
+            WL_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+            if (ms < ms_best) ms_best = ms;
+        }
+        if (cudaGetLastError() != cudaSuccess) continue;
+        if (env_flag("WILSON_TUNE_VERBOSE", false))
+            fprintf(stderr, "[wilson tune]   %s block %d variant %d: %.2f us\n", key.c_str(), c.block, c.variant,
+                    ms_best * 1e3f);
+        if (ms_best * 1e3f < best.us) best = Entry{c, ms_best * 1e3f};
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (env_flag("WILSON_TUNE_VERBOSE", false))
+        fprintf(stderr, "[wilson tune] %s -> block %d variant %d (%.2f us)\n", key.c_str(), best.cfg.block,
+                best.cfg.variant, best.us);
+    std::lock_guard<std::mutex> lk(g_mutex);
+    (*g_cache)[key] = best;
+    append_file(key, best);
+    return best.cfg;
+}
+
+}  // namespace wl
