@@ -133,6 +133,14 @@ wilson_solver_params wilson_solver_defaults(int inner);
 int wilson_cg_solve(double* x, const double* gauge, const double* b, const wilson_lattice* L,
                     double kappa, const wilson_solver_params* p, wilson_solve_stats* st, void* stream);
 
+/* Several right-hand sides sharing one gauge field, solved as independent
+ * CGs in lockstep (each launch covers all of them; a finished one is
+ * skipped).  x, b: nrhs canonical full fields back to back (device);
+ * st: nrhs entries (outer_iters, hop_applications and seconds are shared).
+ * Returns WILSON_OK only if every right-hand side converged. */
+int wilson_cg_solve_multi(double* x, const double* gauge, const double* b, int nrhs, const wilson_lattice* L,
+                          double kappa, const wilson_solver_params* p, wilson_solve_stats* st, void* stream);
+
 /* ---------------------------------------------------------------------- */
 /* Handles: prepared fields for repeated (timed) applications.             */
 /* A gauge handle holds the links in the site-vectorised structure-of-     */
@@ -162,11 +170,14 @@ int wilson_spinor_import(wilson_spinor* s, const double* canon, void* stream);
 int wilson_spinor_export(const wilson_spinor* s, double* canon, void* stream);
 
 /* Apply an operator to prepared fields of matching lattice and precision
- * (the gauge may be F32-12 for F32 spinors, or the spinor precision).
+ * (links stored in the spinors' precision, 12 or 18 reals).
  *   HOP:  full -> full (D_h) or parity 1-p -> parity p (D_{p,1-p})
  *   M:    full -> full
- *   SCHUR, SCHUR_DAG: parity p -> parity p (uses a workspace field)
- * All nrhs fields are applied; out must not be in. */
+ *   SCHUR, SCHUR_DAG: parity p -> parity p (the intermediate field of the
+ *         other parity is allocated once and kept with the gauge handle)
+ * All nrhs fields are applied in one launch per hop, right-hand sides of a
+ * site tile back to back so that they share the tile's link loads; out must
+ * not be in. */
 int wilson_dslash_h(wilson_spinor* out, const wilson_gauge* g, const wilson_spinor* in, double kappa,
                     int op, void* stream);
 

@@ -7,6 +7,7 @@
 #include <memory>
 #include <mutex>
 #include <string>
+#include <vector>
 
 #include "../../include/wilson.h"
 #include "solver.h"
@@ -121,6 +122,8 @@ void wl::record_error(const std::string& msg) { g_last_error = msg; }
 
 struct wilson_gauge_s {
     GaugeField f;
+    mutable std::mutex m;
+    mutable SpinorField tmp;  // intermediate field of the Schur operator
 };
 struct wilson_spinor_s {
     SpinorField f;
@@ -256,6 +259,34 @@ int wilson_dslash_eo(double* out, const double* gauge, const double* in, const w
     });
 }
 
+static SolveParams checked_params(const wilson_solver_params* p, double kappa) {
+    WL_REQUIRE(p != nullptr, "solver parameters are NULL");
+    WL_REQUIRE(std::isfinite(kappa), "kappa must be finite");
+    WL_REQUIRE(p->tol > 0 && std::isfinite(p->tol), "tol must be positive");
+    WL_REQUIRE(p->maxiter > 0, "maxiter must be positive");
+    WL_REQUIRE(p->recon == 12 || p->recon == 18, "recon must be 12 or 18");
+    SolveParams prm;
+    prm.inner = to_prec(p->inner);
+    WL_REQUIRE(prm.inner == P_F64 || p->recon == 12 || prm.inner == P_F32, "F16/BF16 links are stored with 12 reals");
+    prm.recon = p->recon;
+    prm.tol = p->tol;
+    prm.maxiter = p->maxiter;
+    prm.max_restarts = p->max_restarts > 0 ? p->max_restarts : 1000;
+    prm.delta = p->delta;
+    prm.use_initial_guess = p->use_initial_guess;
+    prm.reliable = p->reliable;
+    return prm;
+}
+
+static void copy_stats(wilson_solve_stats* o, const SolveStats& s, int rc) {
+    o->status = rc;
+    o->outer_iters = s.outer_iters;
+    o->inner_iters = s.inner_iters;
+    o->hop_applications = s.hop_applications;
+    o->true_rel_resid = s.true_rel_resid;
+    o->seconds = s.seconds;
+}
+
 int wilson_cg_solve(double* x, const double* gauge, const double* b, const wilson_lattice* L, double kappa,
                     const wilson_solver_params* p, wilson_solve_stats* st_out, void* stream) {
     SolveStats stats;
@@ -264,23 +295,8 @@ int wilson_cg_solve(double* x, const double* gauge, const double* b, const wilso
         check_ptr(x, "x");
         check_ptr(gauge, "gauge");
         check_ptr(b, "b");
-        WL_REQUIRE(p != nullptr, "solver parameters are NULL");
-        WL_REQUIRE(std::isfinite(kappa), "kappa must be finite");
-        WL_REQUIRE(p->tol > 0 && std::isfinite(p->tol), "tol must be positive");
-        WL_REQUIRE(p->maxiter > 0, "maxiter must be positive");
-        WL_REQUIRE(p->recon == 12 || p->recon == 18, "recon must be 12 or 18");
         WL_REQUIRE(x != b, "x must not alias b");
-        SolveParams prm;
-        prm.inner = to_prec(p->inner);
-        WL_REQUIRE(prm.inner == P_F64 || p->recon == 12 || prm.inner == P_F32,
-                   "F16/BF16 links are stored with 12 reals");
-        prm.recon = p->recon;
-        prm.tol = p->tol;
-        prm.maxiter = p->maxiter;
-        prm.max_restarts = p->max_restarts > 0 ? p->max_restarts : 1000;
-        prm.delta = p->delta;
-        prm.use_initial_guess = p->use_initial_guess;
-        prm.reliable = p->reliable;
+        const SolveParams prm = checked_params(p, kappa);
         check_device();
         WL_REQUIRE(is_device_ptr(x) && is_device_ptr(b) && is_device_ptr(gauge),
                    "wilson_cg_solve takes device pointers");
@@ -288,7 +304,7 @@ int wilson_cg_solve(double* x, const double* gauge, const double* b, const wilso
         SolveStream& ss = solve_stream();
         WL_CUDA(cudaEventRecord(ss.e0, caller));
         WL_CUDA(cudaStreamWaitEvent(ss.s, ss.e0, 0));
-        stats = cg_solve(x, gauge, b, g, kappa, prm, ss.s);
+        stats = cg_solve(x, gauge, b, 1, g, kappa, prm, ss.s)[0];
         WL_CUDA(cudaEventRecord(ss.e1, ss.s));
         WL_CUDA(cudaStreamWaitEvent(caller, ss.e1, 0));
         WL_CUDA(cudaStreamSynchronize(caller));
@@ -296,14 +312,41 @@ int wilson_cg_solve(double* x, const double* gauge, const double* b, const wilso
             throw Error(stats.status, stats.status == WILSON_ERR_NOCONV ? "solve did not converge"
                                                                         : "NaN or Inf in the solve");
     });
-    if (st_out) {
-        st_out->status = rc;
-        st_out->outer_iters = stats.outer_iters;
-        st_out->inner_iters = stats.inner_iters;
-        st_out->hop_applications = stats.hop_applications;
-        st_out->true_rel_resid = stats.true_rel_resid;
-        st_out->seconds = stats.seconds;
-    }
+    if (st_out) copy_stats(st_out, stats, rc);
+    return rc;
+}
+
+int wilson_cg_solve_multi(double* x, const double* gauge, const double* b, int nrhs, const wilson_lattice* L,
+                          double kappa, const wilson_solver_params* p, wilson_solve_stats* st_out, void* stream) {
+    std::vector<SolveStats> stats;
+    int rc = guarded([&] {
+        const Geom g = checked_geom(L);
+        check_ptr(x, "x");
+        check_ptr(gauge, "gauge");
+        check_ptr(b, "b");
+        WL_REQUIRE(nrhs >= 1 && nrhs <= 64, "nrhs must be in 1..64");
+        WL_REQUIRE(x != b, "x must not alias b");
+        const SolveParams prm = checked_params(p, kappa);
+        check_device();
+        WL_REQUIRE(is_device_ptr(x) && is_device_ptr(b) && is_device_ptr(gauge),
+                   "wilson_cg_solve_multi takes device pointers");
+        cudaStream_t caller = static_cast<cudaStream_t>(stream);
+        SolveStream& ss = solve_stream();
+        WL_CUDA(cudaEventRecord(ss.e0, caller));
+        WL_CUDA(cudaStreamWaitEvent(ss.s, ss.e0, 0));
+        stats = cg_solve(x, gauge, b, nrhs, g, kappa, prm, ss.s);
+        WL_CUDA(cudaEventRecord(ss.e1, ss.s));
+        WL_CUDA(cudaStreamWaitEvent(caller, ss.e1, 0));
+        WL_CUDA(cudaStreamSynchronize(caller));
+        int worst = 0;
+        for (const SolveStats& s : stats)
+            if (s.status != 0 && (worst == 0 || s.status == WILSON_ERR_NUMERIC)) worst = s.status;
+        if (worst != 0)
+            throw Error(worst, worst == WILSON_ERR_NOCONV ? "a right-hand side did not converge"
+                                                          : "NaN or Inf in a right-hand side's solve");
+    });
+    if (st_out)
+        for (int k = 0; k < (int)stats.size(); k++) copy_stats(st_out + k, stats[k], stats[k].status);
     return rc;
 }
 
@@ -418,41 +461,61 @@ int wilson_dslash_h(wilson_spinor* out, const wilson_gauge* gh, const wilson_spi
         WL_REQUIRE(a.nrhs == b.nrhs, "in and out nrhs differ");
         WL_REQUIRE(gf.prec == a.prec, "gauge and spinor precision differ");
         cudaStream_t st = static_cast<cudaStream_t>(stream);
-        for (int k = 0; k < a.nrhs; k++) {
-            if (op == WILSON_OP_HOP || op == WILSON_OP_M) {
-                if (a.subset == 2) {
-                    WL_REQUIRE(b.subset == 2, "full input needs a full output");
-                    HopLaunch h{};
-                    h.out = b.block(0, k);
-                    h.in = a.block(0, k);
-                    h.x = a.block(0, k);
-                    h.out_pstep = b.pbytes;
-                    h.in_pstep = a.pbytes;
-                    h.x_pstep = a.pbytes;
-                    h.full = 1;
-                    h.gauge = &gf;
-                    h.sprec = a.prec;
-                    h.xpay = op == WILSON_OP_M;
-                    h.a = op == WILSON_OP_M ? -kappa : 1.0;
-                    launch_hop(h, st);
-                } else {
-                    WL_REQUIRE(op == WILSON_OP_HOP, "M needs full fields");
-                    WL_REQUIRE(b.subset == 1 - a.subset, "HOP maps parity 1-p to parity p");
-                    HopLaunch h{};
-                    h.out = b.block(b.subset, k);
-                    h.in = a.block(a.subset, k);
-                    h.gauge = &gf;
-                    h.sprec = a.prec;
-                    h.out_parity = b.subset;
-                    h.a = 1.0;
-                    launch_hop(h, st);
-                }
-            } else if (op == WILSON_OP_SCHUR || op == WILSON_OP_SCHUR_DAG) {
-                WL_REQUIRE(a.subset != 2 && b.subset == a.subset, "SCHUR maps parity p to parity p");
-                throw Error(WILSON_ERR_UNSUPPORTED, "SCHUR on handles: use wilson_dslash_eo or the solver");
+        HopLaunch h{};
+        h.gauge = &gf;
+        h.sprec = a.prec;
+        h.nrhs = a.nrhs;
+        h.out_rstep = b.rstep();
+        h.in_rstep = a.rstep();
+        h.x_rstep = a.rstep();
+        h.a = 1.0;
+        if (op == WILSON_OP_HOP || op == WILSON_OP_M) {
+            if (a.subset == 2) {
+                WL_REQUIRE(b.subset == 2, "full input needs a full output");
+                h.out = b.block(0);
+                h.in = a.block(0);
+                h.x = a.block(0);
+                h.out_pstep = b.pbytes;
+                h.in_pstep = a.pbytes;
+                h.x_pstep = a.pbytes;
+                h.full = 1;
+                h.xpay = op == WILSON_OP_M;
+                h.a = op == WILSON_OP_M ? -kappa : 1.0;
             } else {
-                throw Error(WILSON_ERR_ARG, "unknown op");
+                WL_REQUIRE(op == WILSON_OP_HOP, "M needs full fields");
+                WL_REQUIRE(b.subset == 1 - a.subset, "HOP maps parity 1-p to parity p");
+                h.out = b.block(b.subset);
+                h.in = a.block(a.subset);
+                h.out_parity = b.subset;
             }
+            launch_hop(h, st);
+        } else if (op == WILSON_OP_SCHUR || op == WILSON_OP_SCHUR_DAG) {
+            WL_REQUIRE(a.subset != 2 && b.subset == a.subset, "SCHUR maps parity p to parity p");
+            // the intermediate field of the other parity lives with the gauge handle
+            std::lock_guard<std::mutex> lk(gh->m);
+            SpinorField& t = gh->tmp;
+            if (!t.buf.p || t.prec != a.prec || t.nrhs < a.nrhs || t.subset != 1 - a.subset)
+                t.alloc(a.prec, 1 - a.subset, a.nrhs, a.g);
+            const int dag = op == WILSON_OP_SCHUR_DAG;
+            HopLaunch h1 = h;
+            h1.out = t.block(1 - a.subset);
+            h1.in = a.block(a.subset);
+            h1.out_rstep = t.rstep();
+            h1.out_parity = 1 - a.subset;
+            h1.dagger = dag;
+            launch_hop(h1, st);
+            HopLaunch h2 = h;
+            h2.out = b.block(b.subset);
+            h2.in = t.block(1 - a.subset);
+            h2.in_rstep = t.rstep();
+            h2.x = a.block(a.subset);
+            h2.xpay = 1;
+            h2.a = -kappa * kappa;
+            h2.out_parity = b.subset;
+            h2.dagger = dag;
+            launch_hop(h2, st);
+        } else {
+            throw Error(WILSON_ERR_ARG, "unknown op");
         }
     });
 }

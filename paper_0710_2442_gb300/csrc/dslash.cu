@@ -47,6 +47,11 @@ void launch_hop(const HopLaunch& L, cudaStream_t st) {
     P.out_pstep = L.out_pstep;
     P.in_pstep = L.in_pstep;
     P.x_pstep = L.x_pstep;
+    P.nrhs = L.nrhs > 1 ? L.nrhs : 1;
+    P.out_rstep = L.out_rstep;
+    P.in_rstep = L.in_rstep;
+    P.x_rstep = L.x_rstep;
+    P.skip_stride = L.skip_stride;
     P.gauge = gf.buf.as<const char>();
     P.g = gf.g;
     P.out_parity = L.out_parity;
@@ -68,19 +73,21 @@ void launch_hop(const HopLaunch& L, cudaStream_t st) {
         cfg.variant = L.variant;
     } else {
         char key[160];
-        snprintf(key, sizeof(key), "hop:s%d:g%d:r%d:d%d:f%d:x%d:%dx%dx%dx%d", (int)sp, (int)gp, R, (int)dag, L.full,
-                 L.xpay, P.g.L[0], P.g.L[1], P.g.L[2], P.g.L[3]);
+        snprintf(key, sizeof(key), "hop:s%d:g%d:r%d:d%d:f%d:x%d:n%d:%dx%dx%dx%d", (int)sp, (int)gp, R, (int)dag,
+                 L.full, L.xpay, P.nrhs, P.g.L[0], P.g.L[1], P.g.L[2], P.g.L[3]);
         // tuning launches never reduce: the finishers are not idempotent
         const HopParams Pt = P;
         cfg = tune_launch(key, hop_candidates(), LaunchConfig{}, st, [&](const LaunchConfig& c) {
-            dispatch(Pt, sp, gp, R, c.block, hop_grid_blocks(Pt.g, c.block, 0), ny, dag, c.variant, st);
+            dispatch(Pt, sp, gp, R, c.block, hop_grid_blocks(Pt.g, c.block, 0) * Pt.nrhs, ny, dag, c.variant, st);
         });
     }
     if (L.red) {
         P.reduce = 1;
         P.red = *L.red;
+        WL_REQUIRE(!L.full, "reducing hop launches are single-parity");
     }
-    const int blocks = hop_grid_blocks(P.g, cfg.block, L.red ? L.grid_cap : 0);
+    const int blocks = hop_grid_blocks(P.g, cfg.block, L.red ? L.grid_cap : 0) * P.nrhs;
+    WL_REQUIRE(!L.red || blocks / P.nrhs <= L.red->slot_cap, "reduction capacity below the grid size");
     dispatch(P, sp, gp, R, cfg.block, blocks, ny, dag, cfg.variant, st);
     WL_LAUNCH_CHECK();
 }

@@ -124,6 +124,9 @@ struct HopParams {
     const char* in;
     const char* x;
     long long out_pstep, in_pstep, x_pstep;
+    long long out_rstep, in_rstep, x_rstep;
+    int nrhs;
+    int skip_stride;
     const char* gauge;
     Geom g;
     int out_parity;
@@ -183,20 +186,27 @@ __device__ __forceinline__ void hop_dir(cpx<typename SpinorFmt<SP>::real> acc[12
     }
 }
 
+// Grid: blockIdx.x = site_block * nrhs + rhs (right-hand sides fastest, so
+// the blocks of all right-hand sides of one site tile run back to back and
+// share the tile's link loads through L2); blockIdx.y = output parity for
+// full-lattice launches.
 template <int SP, int GP, int R, bool DAG, int MINB>
 __global__ void __launch_bounds__(256, MINB) hop_kernel(const HopParams P) {
     using SF = SpinorFmt<SP>;
     using T = typename SF::real;
-    if (P.skip && __ldcg(P.skip)) return;
+    const int k = blockIdx.x % P.nrhs;
+    const int sb = blockIdx.x / P.nrhs;
+    const int nb = gridDim.x / P.nrhs;
+    if (P.skip && __ldcg(P.skip + (size_t)k * P.skip_stride)) return;
     const int p = P.full ? (int)blockIdx.y : P.out_parity;
     const int pin = 1 - p;
-    char* out = P.out + (P.full ? p * P.out_pstep : 0);
-    const char* in = P.in + (P.full ? pin * P.in_pstep : 0);
-    const char* x = P.x ? P.x + (P.full ? p * P.x_pstep : 0) : nullptr;
+    char* out = P.out + (P.full ? p * P.out_pstep : 0) + k * P.out_rstep;
+    const char* in = P.in + (P.full ? pin * P.in_pstep : 0) + k * P.in_rstep;
+    const char* x = P.x ? P.x + (P.full ? p * P.x_pstep : 0) + k * P.x_rstep : nullptr;
     const Geom& g = P.g;
     const T a = (T)P.a;
     double nrm = 0.0;
-    for (int h = blockIdx.x * blockDim.x + threadIdx.x; h < g.Vh; h += gridDim.x * blockDim.x) {
+    for (int h = sb * blockDim.x + threadIdx.x; h < g.Vh; h += nb * blockDim.x) {
         int c[4], s;
         site_of_half(h, p, g, c, s);
         cpx<T> acc[12];
@@ -224,7 +234,7 @@ __global__ void __launch_bounds__(256, MINB) hop_kernel(const HopParams P) {
         }
         SF::store(out, g.stride, h, acc);
     }
-    if (P.reduce) grid_reduce(nrm, P.red);
+    if (P.reduce) grid_reduce(nrm, P.red, k, nb * gridDim.y, sb + nb * blockIdx.y);
 }
 
 // Kernel variants: blocks of 256 threads guaranteed resident per SM, i.e. a

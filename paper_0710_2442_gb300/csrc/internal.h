@@ -103,6 +103,8 @@ struct SpinorField {
         int slot = subset == 2 ? p : 0;
         return static_cast<char*>(buf.p) + (size_t)(k * nparity() + slot) * pbytes;
     }
+    // bytes from one right-hand side's blocks to the next one's
+    long long rstep() const { return (long long)nparity() * pbytes; }
     void alloc(Prec p, int sub, int nr, const Geom& geom);
 };
 
@@ -120,6 +122,7 @@ struct Reduction {
     DevBuf results;    // doubles
     int capacity = 0;
     void init(int cap, int ncounters, cudaStream_t st);
+    // Slots counter_slot .. counter_slot + nrhs - 1 (one per right-hand side).
     RedArgs args(int counter_slot, int op, double* result, CGScalars* sc) const {
         RedArgs r;
         r.partials = partials.as<double>() + (size_t)counter_slot * capacity;
@@ -127,6 +130,7 @@ struct Reduction {
         r.result = result;
         r.sc = sc;
         r.op = op;
+        r.slot_cap = capacity;
         return r;
     }
 };
@@ -141,6 +145,11 @@ struct HopLaunch {
     long long out_pstep;   // full launches: byte offset of the parity-1 block from the parity-0 block
     long long in_pstep;
     long long x_pstep;
+    int nrhs;              // right-hand sides in one launch (0 or 1: one)
+    long long out_rstep;   // byte offset between consecutive right-hand sides
+    long long in_rstep;
+    long long x_rstep;
+    int skip_stride;       // ints between the per-rhs skip flags
     const GaugeField* gauge;
     Prec sprec;
     int out_parity;        // single-parity launches
@@ -149,7 +158,7 @@ struct HopLaunch {
     int xpay;              // out = x + a * D in   (else out = a * D in)
     double a;
     const RedArgs* red;    // |out|^2 into a reducer, or null
-    const int* skip;       // device flag: nonzero -> the launch does nothing
+    const int* skip;       // device flags (one per rhs): nonzero -> that rhs does nothing
     int block;             // threads per block (0 = autotuned)
     int variant;           // kernel register-budget variant when block > 0
     int grid_cap;          // max blocks of a reducing launch (0 = no cap)
@@ -161,10 +170,6 @@ int hop_grid_blocks(const Geom& g, int block, int grid_cap);
 void pack_spinor(const SpinorField& f, int rhs, const double* canon, cudaStream_t st);
 void unpack_spinor(const SpinorField& f, int rhs, double* canon, cudaStream_t st);
 void pack_gauge(GaugeField& gf, const double* canon, cudaStream_t st);
-
-// BLAS-1 on parity blocks (see blas.cu)
-void convert_block(Prec dst_p, void* dst, Prec src_p, const void* src, const Geom& g, cudaStream_t st,
-                   const int* skip = nullptr);
 
 int device_sm_count();
 

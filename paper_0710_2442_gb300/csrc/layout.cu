@@ -214,45 +214,4 @@ void pack_gauge(GaugeField& gf, const double* canon, cudaStream_t st) {
     WL_LAUNCH_CHECK();
 }
 
-// ---------------------------------------------------------------------------
-// precision conversion of one parity block
-// ---------------------------------------------------------------------------
-template <int DP, int SP>
-__global__ void convert_kernel(char* dst, const char* src, Geom g, const int* skip) {
-    if (skip && __ldcg(skip)) return;
-    using TS = typename SpinorFmt<SP>::real;
-    using TD = typename SpinorFmt<DP>::real;
-    for (int h = blockIdx.x * blockDim.x + threadIdx.x; h < g.Vh; h += gridDim.x * blockDim.x) {
-        cpx<TS> v[12];
-        SpinorFmt<SP>::load(src, g.stride, h, v);
-        cpx<TD> w[12];
-#pragma unroll
-        for (int k = 0; k < 12; k++) w[k] = {(TD)v[k].re, (TD)v[k].im};
-        SpinorFmt<DP>::store(dst, g.stride, h, w);
-    }
-}
-
-template <int DP>
-static void convert_from(Prec sp, char* dst, const char* src, const Geom& g, cudaStream_t st, const int* skip) {
-    const int block = 256, grid = grid_for(g.Vh, block);
-    switch (sp) {
-        case P_F64: convert_kernel<DP, P_F64><<<grid, block, 0, st>>>(dst, src, g, skip); break;
-        case P_F32: convert_kernel<DP, P_F32><<<grid, block, 0, st>>>(dst, src, g, skip); break;
-        case P_F16: convert_kernel<DP, P_F16><<<grid, block, 0, st>>>(dst, src, g, skip); break;
-        case P_BF16: convert_kernel<DP, P_BF16><<<grid, block, 0, st>>>(dst, src, g, skip); break;
-    }
-}
-
-void convert_block(Prec dp, void* dst, Prec sp, const void* src, const Geom& g, cudaStream_t st, const int* skip) {
-    char* d = static_cast<char*>(dst);
-    const char* s = static_cast<const char*>(src);
-    switch (dp) {
-        case P_F64: convert_from<P_F64>(sp, d, s, g, st, skip); break;
-        case P_F32: convert_from<P_F32>(sp, d, s, g, st, skip); break;
-        case P_F16: convert_from<P_F16>(sp, d, s, g, st, skip); break;
-        case P_BF16: convert_from<P_BF16>(sp, d, s, g, st, skip); break;
-    }
-    WL_LAUNCH_CHECK();
-}
-
 }  // namespace wl

@@ -19,7 +19,8 @@ enum FinOp {
     FIN_CG_ALPHA = 1,  // |q|^2: alpha = gam / |q|^2
     FIN_CG_RES = 2,    // |s|^2: convergence test, iteration count
     FIN_CG_BETA = 3,   // |r|^2: beta = |r|^2 / gam, gam = |r|^2
-    FIN_ADD = 4        // result[0] += sum
+    FIN_ADD = 4,       // result[0] += sum
+    FIN_CG_GAM = 5     // |r|^2: gam = |r|^2 (start of a CG)
 };
 
 // Scalars of one CG solve, kept on the device so that iterations never wait
@@ -31,18 +32,21 @@ struct CGScalars {
     double pq;       // |Mhat p|^2
     double snorm2;   // |s|^2, recursively updated Schur residual
     double stop2;    // the inner iteration ends when snorm2 <= stop2
-    int done;        // 1: converged (snorm2 <= stop2), 2: maxiter, 3: NaN/Inf
+    int done;        // 1: converged (snorm2 <= stop2), 2: maxiter, 3: NaN/Inf, 4: finished earlier
     int iter;        // iterations completed since the counter was last reset
     int maxiter;     // iteration cap for this inner solve
     int pad;
 };
 
+// A reduction may have several independent slots (one per right-hand side):
+// slot k uses partials[k * slot_cap ...], counter[k], result[k] and sc[k].
 struct RedArgs {
-    double* partials;       // one slot per block (capacity >= grid size)
-    unsigned int* counter;  // 0 before the launch; reset to 0 by the last block
-    double* result;         // FIN_STORE / FIN_ADD target
-    CGScalars* sc;          // FIN_CG_* target
+    double* partials;       // slot_cap partials per slot (slot_cap >= blocks per slot)
+    unsigned int* counter;  // one per slot: 0 before the launch; reset to 0 by the last block
+    double* result;         // FIN_STORE / FIN_ADD targets (one per slot)
+    CGScalars* sc;          // FIN_CG_* targets (one per slot)
     int op;
+    int slot_cap;
 };
 
 __device__ __forceinline__ double warp_sum(double v) {
@@ -67,11 +71,11 @@ __device__ __forceinline__ double block_sum(double v) {
     return v;
 }
 
-__device__ inline void run_finisher(const RedArgs& r, double sum) {
-    CGScalars* sc = r.sc;
+__device__ inline void run_finisher(const RedArgs& r, int slot, double sum) {
+    CGScalars* sc = r.sc ? r.sc + slot : nullptr;
     switch (r.op) {
-        case FIN_STORE: r.result[0] = sum; break;
-        case FIN_ADD: r.result[0] += sum; break;
+        case FIN_STORE: r.result[slot] = sum; break;
+        case FIN_ADD: r.result[slot] += sum; break;
         case FIN_CG_ALPHA:
             sc->pq = sum;
             if (!(sum > 0.0) || !isfinite(sum)) {
@@ -89,6 +93,10 @@ __device__ inline void run_finisher(const RedArgs& r, double sum) {
             else if (sum <= sc->stop2) sc->done = 1;
             else if (sc->iter >= sc->maxiter) sc->done = 2;
             break;
+        case FIN_CG_GAM:
+            sc->gam = sum;
+            if (!isfinite(sum)) sc->done = 3;
+            break;
         case FIN_CG_BETA:
             if (!isfinite(sum)) { sc->done = 3; sc->beta = 0.0; break; }
             sc->beta = sc->gam > 0.0 ? sum / sc->gam : 0.0;
@@ -97,29 +105,34 @@ __device__ inline void run_finisher(const RedArgs& r, double sum) {
     }
 }
 
-// Called by all threads of every block of the grid (uniformly).
-__device__ inline void grid_reduce(double v, const RedArgs& r) {
+// Called by all threads of every block that reduces into `slot` (uniformly):
+// nblocks blocks contribute to the slot, this block is number bid of them.
+__device__ inline void grid_reduce(double v, const RedArgs& r, int slot, unsigned int nblocks, unsigned int bid) {
     const double bs = block_sum(v);
     __shared__ int s_last;
-    const unsigned int nblocks = gridDim.x * gridDim.y;
-    const unsigned int bid = blockIdx.x + gridDim.x * blockIdx.y;
+    double* part = r.partials + (size_t)slot * r.slot_cap;
     if (threadIdx.x == 0) {
-        r.partials[bid] = bs;
+        part[bid] = bs;
         __threadfence();
-        const unsigned int ticket = atomicAdd(r.counter, 1u);
+        const unsigned int ticket = atomicAdd(r.counter + slot, 1u);
         s_last = (ticket == nblocks - 1);
     }
     __syncthreads();
     if (!s_last) return;
     __threadfence();
     double acc = 0.0;
-    for (unsigned int i = threadIdx.x; i < nblocks; i += blockDim.x) acc += __ldcg(r.partials + i);
+    for (unsigned int i = threadIdx.x; i < nblocks; i += blockDim.x) acc += __ldcg(part + i);
     const double total = block_sum(acc);
     if (threadIdx.x == 0) {
-        run_finisher(r, total);
-        *r.counter = 0u;
+        run_finisher(r, slot, total);
+        r.counter[slot] = 0u;
         __threadfence();
     }
+}
+
+// Single-slot form: every block of the grid contributes.
+__device__ inline void grid_reduce(double v, const RedArgs& r) {
+    grid_reduce(v, r, 0, gridDim.x * gridDim.y, blockIdx.x + gridDim.x * blockIdx.y);
 }
 
 }  // namespace wl

@@ -1,5 +1,6 @@
 // solver.cu -- CG on the normal equations of the even-odd Schur complement,
-// with an FP64 defect correction around a reduced-precision inner CG.
+// with an FP64 defect correction around a reduced-precision inner CG, for one
+// or several right-hand sides.
 //
 // The paper (Sec. 5) only notes that an iterative solver repeats Eq. 3; the
 // algorithm here is textbook CG in its residual-tracking form for the normal
@@ -10,19 +11,24 @@
 //   x_o = b_o + kappa D_oe x_e
 //
 // Outer loop (FP64, on the GPU): r = bhat - Mhat x_e with FP64 links and
-// FP64 reductions; stop when |r| <= tol |b| (equal to the full-system
-// residual |b - M x|, whose odd part vanishes by construction).  Inner loop
-// (storage precision F32/F16/BF16, FP32 arithmetic; or FP64 for the plain
-// FP64 solve) solves Mhat e = r until |s| <= delta |r| where s is the
-// recursively updated inner residual; then x_e += e in FP64.
+// FP64 reductions; a right-hand side is finished when |r| <= tol |b| (equal
+// to the full-system residual |b - M x|, whose odd part vanishes by
+// construction).  Inner loop (storage precision F32/F16/BF16 with FP32
+// arithmetic, or FP64 for the plain FP64 solve) solves Mhat e = r until
+// |s| <= delta |r| where s is the recursively updated inner residual; then
+// x_e += e in FP64.
 //
 // Reliable updates (default): the inner CG keeps its search direction p
 // across outer corrections and only replaces its residual by the recomputed
 // FP64 one (the scheme of Sleijpen & van der Vorst 1996 as used for lattice
 // QCD mixed-precision solvers); with reliable = 0 every correction restarts CG.
 //
+// Several right-hand sides run as independent CGs in lockstep: every launch
+// covers all of them (one grid, right-hand sides fastest), each has its own
+// scalars and done flag, and a finished one is skipped by every kernel.
+//
 // One inner iteration is six launches, all reading their scalars from device
-// memory and exiting at once when the solve's done flag is set:
+// memory and exiting at once when their right-hand side is done:
 //   t = D_oe p;  q = p - k^2 D_eo t, |q|^2 -> alpha
 //   x += alpha p, s -= alpha q, |s|^2 -> convergence test
 //   t = D'_oe s;  r = s - k^2 D'_eo t, |r|^2 -> beta      (D' = g5 D g5)
@@ -39,22 +45,30 @@
 
 namespace wl {
 
-void schur_apply(const GaugeField& gf, Prec sp, void* out, const void* in, void* tmp, double kappa, int dag,
-                 const RedArgs* red, const int* skip, int grid_cap, cudaStream_t st) {
+void schur_apply(const GaugeField& gf, Prec sp, Vec out, Vec in, Vec tmp, int nrhs, double kappa, int dag,
+                 const RedArgs* red, const int* skip, int skip_stride, int grid_cap, cudaStream_t st) {
     HopLaunch a{};
-    a.out = tmp;
-    a.in = in;
+    a.out = tmp.p;
+    a.in = in.p;
+    a.nrhs = nrhs;
+    a.out_rstep = tmp.rstep;
+    a.in_rstep = in.rstep;
     a.gauge = &gf;
     a.sprec = sp;
     a.out_parity = 1;
     a.dagger = dag;
     a.a = 1.0;
     a.skip = skip;
+    a.skip_stride = skip_stride;
     launch_hop(a, st);
     HopLaunch b{};
-    b.out = out;
-    b.in = tmp;
-    b.x = in;
+    b.out = out.p;
+    b.in = tmp.p;
+    b.x = in.p;
+    b.nrhs = nrhs;
+    b.out_rstep = out.rstep;
+    b.in_rstep = tmp.rstep;
+    b.x_rstep = in.rstep;
     b.xpay = 1;
     b.a = -kappa * kappa;
     b.gauge = &gf;
@@ -63,6 +77,7 @@ void schur_apply(const GaugeField& gf, Prec sp, void* out, const void* in, void*
     b.dagger = dag;
     b.red = red;
     b.skip = skip;
+    b.skip_stride = skip_stride;
     b.grid_cap = red ? grid_cap : 0;
     launch_hop(b, st);
 }
@@ -77,114 +92,120 @@ struct Pinned {
 
 struct Inner {
     Prec ip, xp;
-    Geom g;
     SpinorField xin, s, slow, p, q, r, t;
     bool has_slow;
-    void alloc(Prec inner, const Geom& geom) {
+    void alloc(Prec inner, const Geom& g, int nr) {
         ip = inner;
         xp = inner == P_F64 ? P_F64 : P_F32;
-        g = geom;
         has_slow = (ip != xp);
-        xin.alloc(xp, 0, 1, g);
-        s.alloc(xp, 0, 1, g);
-        if (has_slow) slow.alloc(ip, 0, 1, g);
-        p.alloc(ip, 0, 1, g);
-        q.alloc(ip, 0, 1, g);
-        r.alloc(ip, 0, 1, g);
-        t.alloc(ip, 1, 1, g);
+        xin.alloc(xp, 0, nr, g);
+        s.alloc(xp, 0, nr, g);
+        if (has_slow) slow.alloc(ip, 0, nr, g);
+        p.alloc(ip, 0, nr, g);
+        q.alloc(ip, 0, nr, g);
+        r.alloc(ip, 0, nr, g);
+        t.alloc(ip, 1, nr, g);
     }
-    void* s_in() { return has_slow ? slow.block(0) : s.block(0); }
+    Vec s_in() const { return has_slow ? vec(slow, 0) : vec(s, 0); }
 };
+
+constexpr int kSkipStride = sizeof(CGScalars) / sizeof(int);
 
 }  // namespace
 
-SolveStats cg_solve_prepared(SpinorField& x, const SpinorField& b, const GaugeField& g64, const GaugeField& glo,
-                             double kappa, const SolveParams& prm, cudaStream_t st) {
+std::vector<SolveStats> cg_solve_prepared(SpinorField& x, const SpinorField& b, const GaugeField& g64,
+                                          const GaugeField& glo, double kappa, const SolveParams& prm,
+                                          cudaStream_t st) {
     auto t0 = std::chrono::steady_clock::now();
-    SolveStats stats;
+    const int nr = b.nrhs;
+    std::vector<SolveStats> stats(nr);
     const Geom g = g64.g;
-    const int sms = device_sm_count();
-    const int grid_cap = 8 * sms;          // blocks of reducing launches (<= Reduction capacity / 2)
+    const int grid_cap = 8 * device_sm_count();  // blocks per rhs of reducing launches
     Reduction red;
-    red.init(2 * grid_cap, 8, st);
-    DevBuf scbuf(sizeof(CGScalars));
+    red.init(grid_cap, 8 * nr, st);               // logical reduction j uses slots j*nr .. j*nr+nr-1
+    auto slot = [nr](int j) { return j * nr; };
+    DevBuf scbuf(sizeof(CGScalars) * nr);
     CGScalars* sc = scbuf.as<CGScalars>();
-    Pinned hbuf(sizeof(CGScalars) + 8 * sizeof(double));
+    DevBuf resbuf(sizeof(double) * 8 * nr);
+    double* d_res = resbuf.as<double>();
+    Pinned hbuf(sizeof(CGScalars) * nr + sizeof(double) * 8 * nr);
     CGScalars* h_sc = static_cast<CGScalars*>(hbuf.p);
-    double* h_res = reinterpret_cast<double*>(h_sc + 1);
-    double* d_res = red.results.as<double>();
+    double* h_res = reinterpret_cast<double*>(h_sc + nr);
+    int hops = 0;
 
-    // FP64 work fields
     SpinorField bhat, r64, q64, t64;
-    bhat.alloc(P_F64, 0, 1, g);
-    r64.alloc(P_F64, 0, 1, g);
-    q64.alloc(P_F64, 0, 1, g);
-    t64.alloc(P_F64, 1, 1, g);
+    bhat.alloc(P_F64, 0, nr, g);
+    r64.alloc(P_F64, 0, nr, g);
+    q64.alloc(P_F64, 0, nr, g);
+    t64.alloc(P_F64, 1, nr, g);
 
-    // |b|^2 over both parities
-    {
-        RedArgs ra = red.args(0, FIN_STORE, d_res + 0, nullptr);
-        norm2(P_F64, b.block(0), g, ra, grid_cap, st);
-        RedArgs rb = red.args(1, FIN_STORE, d_res + 1, nullptr);
-        norm2(P_F64, b.block(1), g, rb, grid_cap, st);
-    }
+    // |b_k|^2 over both parities
+    norm2(P_F64, vec(b, 0), g, nr, red.args(slot(0), FIN_STORE, d_res, nullptr), grid_cap, st);
+    norm2(P_F64, vec(b, 1), g, nr, red.args(slot(1), FIN_STORE, d_res + nr, nullptr), grid_cap, st);
     // bhat_e = b_e + kappa D_eo b_o
     {
         HopLaunch h{};
         h.out = bhat.block(0);
         h.in = b.block(1);
         h.x = b.block(0);
+        h.nrhs = nr;
+        h.out_rstep = bhat.rstep();
+        h.in_rstep = b.rstep();
+        h.x_rstep = b.rstep();
         h.xpay = 1;
         h.a = kappa;
         h.gauge = &g64;
         h.sprec = P_F64;
         h.out_parity = 0;
         launch_hop(h, st);
-        stats.hop_applications += 1;
+        hops += 1;
     }
-    if (!prm.use_initial_guess) WL_CUDA(cudaMemsetAsync(x.block(0), 0, x.pbytes, st));
-    WL_CUDA(cudaMemcpyAsync(h_res, d_res, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
+    if (!prm.use_initial_guess)
+        for (int k = 0; k < nr; k++) WL_CUDA(cudaMemsetAsync(x.block(0, k), 0, x.pbytes, st));
+    WL_CUDA(cudaMemcpyAsync(h_res, d_res, 2 * nr * sizeof(double), cudaMemcpyDeviceToHost, st));
     WL_CUDA(cudaStreamSynchronize(st));
-    const double bnorm = std::sqrt(h_res[0] + h_res[1]);
-    const double target = prm.tol * bnorm;
+    std::vector<double> bnorm(nr), target(nr);
+    for (int k = 0; k < nr; k++) {
+        bnorm[k] = std::sqrt(h_res[k] + h_res[nr + k]);
+        target[k] = prm.tol * bnorm[k];
+    }
 
     Inner in;
-    in.alloc(prm.inner, g);
+    in.alloc(prm.inner, g, nr);
     double delta = prm.delta;
     if (!(delta > 0.0)) delta = prm.inner == P_F64 ? 0.0 : prm.inner == P_F32 ? 1e-3 : 0.1;
 
-    cudaGraphExec_t gexec = nullptr;
-    cudaGraph_t graph = nullptr;
-    int total_inner = 0;
-    int status = 0;
-    bool first = true;
+    // Tune the operator launches before capture (tuning cannot run inside a
+    // captured stream).  The launches below only write scratch fields.
+    for (int k = 0; k < nr; k++) WL_CUDA(cudaMemsetAsync(in.p.block(0, k), 0, in.p.pbytes, st));
+    for (int dag = 0; dag < 2; dag++)
+        schur_apply(glo, in.ip, vec(in.q, 0), vec(in.p, 0), vec(in.t, 1), nr, kappa, dag, nullptr, nullptr, 0, 0,
+                    st);
+    schur_apply(g64, P_F64, vec(q64, 0), vec(x, 0), vec(t64, 1), nr, kappa, 0, nullptr, nullptr, 0, 0, st);
 
     auto iteration = [&](cudaStream_t s) {
         const int* skip = &sc->done;
-        RedArgs ra = red.args(2, FIN_CG_ALPHA, nullptr, sc);
-        schur_apply(glo, in.ip, in.q.block(0), in.p.block(0), in.t.block(1), kappa, 0, &ra, skip, grid_cap, s);
-        RedArgs rs = red.args(3, FIN_CG_RES, nullptr, sc);
-        cg_xs_update(in.xp, in.ip, in.xin.block(0), in.p.block(0), in.s.block(0), in.q.block(0),
-                     in.has_slow ? in.slow.block(0) : nullptr, g, sc, rs, grid_cap, s);
-        RedArgs rb = red.args(4, FIN_CG_BETA, nullptr, sc);
-        schur_apply(glo, in.ip, in.r.block(0), in.s_in(), in.t.block(1), kappa, 1, &rb, skip, grid_cap, s);
-        cg_p_update(in.ip, in.p.block(0), in.r.block(0), g, sc, s);
+        RedArgs ra = red.args(slot(2), FIN_CG_ALPHA, nullptr, sc);
+        schur_apply(glo, in.ip, vec(in.q, 0), vec(in.p, 0), vec(in.t, 1), nr, kappa, 0, &ra, skip, kSkipStride,
+                    grid_cap, s);
+        RedArgs rs = red.args(slot(3), FIN_CG_RES, nullptr, sc);
+        cg_xs_update(in.xp, in.ip, vec(in.xin, 0), vec(in.p, 0), vec(in.s, 0), vec(in.q, 0),
+                     in.has_slow ? vec(in.slow, 0) : Vec{nullptr, 0}, g, nr, sc, rs, grid_cap, s);
+        RedArgs rb = red.args(slot(4), FIN_CG_BETA, nullptr, sc);
+        schur_apply(glo, in.ip, vec(in.r, 0), in.s_in(), vec(in.t, 1), nr, kappa, 1, &rb, skip, kSkipStride,
+                    grid_cap, s);
+        cg_p_update(in.ip, vec(in.p, 0), vec(in.r, 0), g, nr, sc, s);
     };
 
-    // Tune the operator launches before capture (tuning cannot run inside a
-    // captured stream).  The launches below only write scratch fields.
-    WL_CUDA(cudaMemsetAsync(in.p.block(0), 0, in.p.pbytes, st));
-    for (int dag = 0; dag < 2; dag++)
-        schur_apply(glo, in.ip, in.q.block(0), in.p.block(0), in.t.block(1), kappa, dag, nullptr, nullptr, 0, st);
-    schur_apply(g64, P_F64, q64.block(0), x.block(0), t64.block(1), kappa, 0, nullptr, nullptr, 0, st);
-
+    cudaGraphExec_t gexec = nullptr;
+    cudaGraph_t graph = nullptr;
     const int chunk = prm.chunk > 0 ? prm.chunk : 16;
     if (prm.use_graph) {
         WL_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
         try {
             for (int k = 0; k < chunk; k++) iteration(st);
         } catch (...) {
-            cudaGraph_t junk;
+            cudaGraph_t junk = nullptr;
             cudaStreamEndCapture(st, &junk);
             if (junk) cudaGraphDestroy(junk);
             throw;
@@ -193,57 +214,99 @@ SolveStats cg_solve_prepared(SpinorField& x, const SpinorField& b, const GaugeFi
         WL_CUDA(cudaGraphInstantiate(&gexec, graph, 0));
     }
 
+    std::vector<int> total_inner(nr, 0), finished(nr, 0);
+    int outer = 0;
+    bool first = true;
     try {
         while (true) {
             // r64 = bhat - Mhat x_e (FP64)
-            schur_apply(g64, P_F64, q64.block(0), x.block(0), t64.block(1), kappa, 0, nullptr, nullptr, 0, st);
-            stats.hop_applications += 2;
-            RedArgs rr = red.args(5, FIN_STORE, d_res + 2, nullptr);
-            xmy_norm64(r64.block(0), bhat.block(0), q64.block(0), g, rr, grid_cap, st);
-            WL_CUDA(cudaMemcpyAsync(h_res + 2, d_res + 2, sizeof(double), cudaMemcpyDeviceToHost, st));
+            schur_apply(g64, P_F64, vec(q64, 0), vec(x, 0), vec(t64, 1), nr, kappa, 0, nullptr, nullptr, 0, 0, st);
+            hops += 2;
+            xmy_norm64(vec(r64, 0), vec(bhat, 0), vec(q64, 0), g, nr,
+                       red.args(slot(5), FIN_STORE, d_res + 2 * nr, nullptr), grid_cap, st);
+            WL_CUDA(cudaMemcpyAsync(h_res + 2 * nr, d_res + 2 * nr, nr * sizeof(double), cudaMemcpyDeviceToHost,
+                                    st));
             WL_CUDA(cudaStreamSynchronize(st));
-            const double rnorm = std::sqrt(h_res[2]);
-            if (!std::isfinite(rnorm)) { status = 6; break; }
-            if (rnorm <= target) break;
-            if (stats.outer_iters >= prm.max_restarts || total_inner >= prm.maxiter) { status = 4; break; }
-            stats.outer_iters++;
+            std::vector<double> rnorm(nr, 0.0);
+            bool all_done = true;
+            const bool budget = outer < prm.max_restarts;
+            for (int k = 0; k < nr; k++) {
+                if (finished[k]) continue;
+                rnorm[k] = std::sqrt(h_res[2 * nr + k]);
+                if (!std::isfinite(rnorm[k])) {
+                    finished[k] = 1;
+                    stats[k].status = 6;
+                } else if (rnorm[k] <= target[k]) {
+                    finished[k] = 1;
+                } else if (total_inner[k] >= prm.maxiter || !budget) {
+                    finished[k] = 1;
+                    stats[k].status = 4;
+                } else {
+                    all_done = false;
+                }
+            }
+            if (all_done) break;
+            outer++;
 
-            // inner start: s = r64, xin = 0, r = Mhat^dag s, p = r (first / restart)
-            convert_block(in.xp, in.s.block(0), P_F64, r64.block(0), g, st);
-            if (in.has_slow) convert_block(in.ip, in.slow.block(0), P_F64, r64.block(0), g, st);
-            WL_CUDA(cudaMemsetAsync(in.xin.block(0), 0, in.xin.pbytes, st));
-            // Reset the iteration state; keep gam (|r|^2 that produced p) for
-            // a reliable update, which continues p = r + beta p.
+            // inner start: s = r64, xin = 0, r = Mhat^dag s, p = r (first / restart) or
+            // p = r + beta p (reliable update, keeps the direction)
+            convert(in.xp, vec(in.s, 0), P_F64, vec(r64, 0), g, nr, st);
+            if (in.has_slow) convert(in.ip, vec(in.slow, 0), P_F64, vec(r64, 0), g, nr, st);
+            for (int k = 0; k < nr; k++) WL_CUDA(cudaMemsetAsync(in.xin.block(0, k), 0, in.xin.pbytes, st));
             const bool restart = first || !prm.reliable;
-            const double stop = std::max(delta * rnorm, target);
-            *h_sc = CGScalars{};
-            h_sc->stop2 = stop * stop;
-            h_sc->snorm2 = rnorm * rnorm;
-            h_sc->maxiter = prm.maxiter - total_inner;
-            const size_t off = restart ? 0 : offsetof(CGScalars, snorm2);
-            WL_CUDA(cudaMemcpyAsync(reinterpret_cast<char*>(sc) + off, reinterpret_cast<char*>(h_sc) + off,
-                                    sizeof(CGScalars) - off, cudaMemcpyHostToDevice, st));
-            RedArgs rg = restart ? red.args(6, FIN_STORE, &sc->gam, nullptr) : red.args(6, FIN_CG_BETA, nullptr, sc);
-            schur_apply(glo, in.ip, in.r.block(0), in.s_in(), in.t.block(1), kappa, 1, &rg, nullptr, grid_cap, st);
-            stats.hop_applications += 2;
-            if (restart) convert_block(in.ip, in.p.block(0), in.ip, in.r.block(0), g, st);
-            else cg_p_update(in.ip, in.p.block(0), in.r.block(0), g, sc, st);
+            for (int k = 0; k < nr; k++) {
+                h_sc[k] = CGScalars{};
+                if (finished[k]) {
+                    h_sc[k].done = 4;
+                    continue;
+                }
+                const double stop = std::max(delta * rnorm[k], target[k]);
+                h_sc[k].stop2 = stop * stop;
+                h_sc[k].snorm2 = rnorm[k] * rnorm[k];
+                h_sc[k].maxiter = prm.maxiter - total_inner[k];
+            }
+            if (restart) {
+                WL_CUDA(cudaMemcpyAsync(sc, h_sc, sizeof(CGScalars) * nr, cudaMemcpyHostToDevice, st));
+            } else {
+                // keep gam/alpha/beta/pq (the direction's history); reset the rest
+                const size_t off = offsetof(CGScalars, snorm2);
+                for (int k = 0; k < nr; k++)
+                    WL_CUDA(cudaMemcpyAsync(reinterpret_cast<char*>(sc + k) + off,
+                                            reinterpret_cast<char*>(h_sc + k) + off, sizeof(CGScalars) - off,
+                                            cudaMemcpyHostToDevice, st));
+            }
+            RedArgs rg = red.args(slot(6), restart ? FIN_CG_GAM : FIN_CG_BETA, nullptr, sc);
+            schur_apply(glo, in.ip, vec(in.r, 0), in.s_in(), vec(in.t, 1), nr, kappa, 1, &rg, nullptr, 0, grid_cap,
+                        st);
+            hops += 2;
+            if (restart) convert(in.ip, vec(in.p, 0), in.ip, vec(in.r, 0), g, nr, st);
+            else cg_p_update(in.ip, vec(in.p, 0), vec(in.r, 0), g, nr, sc, st);
             first = false;
 
             while (true) {
                 if (gexec) {
                     WL_CUDA(cudaGraphLaunch(gexec, st));
                 } else {
-                    for (int k = 0; k < chunk; k++) iteration(st);
+                    for (int it = 0; it < chunk; it++) iteration(st);
                 }
-                WL_CUDA(cudaMemcpyAsync(h_sc, sc, sizeof(CGScalars), cudaMemcpyDeviceToHost, st));
+                WL_CUDA(cudaMemcpyAsync(h_sc, sc, sizeof(CGScalars) * nr, cudaMemcpyDeviceToHost, st));
                 WL_CUDA(cudaStreamSynchronize(st));
-                if (h_sc->done) break;
+                bool all = true;
+                for (int k = 0; k < nr; k++) all = all && h_sc[k].done != 0;
+                if (all) break;
             }
-            total_inner += h_sc->iter;
-            stats.hop_applications += 4 * h_sc->iter;
-            axpy(P_F64, x.block(0), in.xp, in.xin.block(0), 1.0, g, st);
-            if (h_sc->done == 3) { status = 6; break; }
+            int most = 0;
+            for (int k = 0; k < nr; k++) {
+                if (finished[k]) continue;
+                total_inner[k] += h_sc[k].iter;
+                most = std::max(most, h_sc[k].iter);
+                if (h_sc[k].done == 3) {
+                    finished[k] = 1;
+                    stats[k].status = 6;
+                }
+            }
+            hops += 4 * most;
+            axpy(P_F64, vec(x, 0), in.xp, vec(in.xin, 0), 1.0, g, nr, st);
         }
     } catch (...) {
         if (gexec) cudaGraphExecDestroy(gexec);
@@ -259,18 +322,22 @@ SolveStats cg_solve_prepared(SpinorField& x, const SpinorField& b, const GaugeFi
         h.out = x.block(1);
         h.in = x.block(0);
         h.x = b.block(1);
+        h.nrhs = nr;
+        h.out_rstep = x.rstep();
+        h.in_rstep = x.rstep();
+        h.x_rstep = b.rstep();
         h.xpay = 1;
         h.a = kappa;
         h.gauge = &g64;
         h.sprec = P_F64;
         h.out_parity = 1;
         launch_hop(h, st);
-        stats.hop_applications += 1;
+        hops += 1;
     }
     // true residual |b - M x| / |b| over the full lattice, FP64
     {
         SpinorField mx;
-        mx.alloc(P_F64, 2, 1, g);
+        mx.alloc(P_F64, 2, nr, g);
         HopLaunch h{};
         h.out = mx.block(0);
         h.in = x.block(0);
@@ -278,31 +345,41 @@ SolveStats cg_solve_prepared(SpinorField& x, const SpinorField& b, const GaugeFi
         h.out_pstep = mx.pbytes;
         h.in_pstep = x.pbytes;
         h.x_pstep = x.pbytes;
+        h.nrhs = nr;
+        h.out_rstep = mx.rstep();
+        h.in_rstep = x.rstep();
+        h.x_rstep = x.rstep();
         h.full = 1;
         h.xpay = 1;
         h.a = -kappa;
         h.gauge = &g64;
         h.sprec = P_F64;
         launch_hop(h, st);
-        stats.hop_applications += 2;
-        RedArgs r0 = red.args(0, FIN_STORE, d_res + 3, nullptr);
-        xmy_norm64(nullptr, b.block(0), mx.block(0), g, r0, grid_cap, st);
-        RedArgs r1 = red.args(1, FIN_STORE, d_res + 4, nullptr);
-        xmy_norm64(nullptr, b.block(1), mx.block(1), g, r1, grid_cap, st);
-        WL_CUDA(cudaMemcpyAsync(h_res + 3, d_res + 3, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
+        hops += 2;
+        xmy_norm64(Vec{nullptr, 0}, vec(b, 0), vec(mx, 0), g, nr,
+                   red.args(slot(0), FIN_STORE, d_res + 3 * nr, nullptr), grid_cap, st);
+        xmy_norm64(Vec{nullptr, 0}, vec(b, 1), vec(mx, 1), g, nr,
+                   red.args(slot(1), FIN_STORE, d_res + 4 * nr, nullptr), grid_cap, st);
+        WL_CUDA(cudaMemcpyAsync(h_res + 3 * nr, d_res + 3 * nr, 2 * nr * sizeof(double), cudaMemcpyDeviceToHost,
+                                st));
         WL_CUDA(cudaStreamSynchronize(st));
-        const double rr = std::sqrt(h_res[3] + h_res[4]);
-        stats.true_rel_resid = bnorm > 0 ? rr / bnorm : rr;
     }
-    stats.inner_iters = total_inner;
-    if (status == 0 && !(stats.true_rel_resid <= prm.tol)) status = std::isfinite(stats.true_rel_resid) ? 4 : 6;
-    stats.status = status;
-    stats.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    for (int k = 0; k < nr; k++) {
+        SolveStats& s = stats[k];
+        const double rr = std::sqrt(h_res[3 * nr + k] + h_res[4 * nr + k]);
+        s.true_rel_resid = bnorm[k] > 0 ? rr / bnorm[k] : rr;
+        s.inner_iters = total_inner[k];
+        s.outer_iters = outer;
+        s.hop_applications = hops;
+        s.seconds = secs;
+        if (s.status == 0 && !(s.true_rel_resid <= prm.tol)) s.status = std::isfinite(s.true_rel_resid) ? 4 : 6;
+    }
     return stats;
 }
 
-SolveStats cg_solve(double* xc, const double* gauge_canon, const double* bc, const Geom& g, double kappa,
-                    const SolveParams& prm, cudaStream_t st) {
+std::vector<SolveStats> cg_solve(double* xc, const double* gauge_canon, const double* bc, int nrhs, const Geom& g,
+                                 double kappa, const SolveParams& prm, cudaStream_t st) {
     GaugeField g64;
     g64.prec = P_F64;
     g64.recon = 18;
@@ -320,12 +397,15 @@ SolveStats cg_solve(double* xc, const double* gauge_canon, const double* bc, con
         inner_gauge = &glo;
     }
     SpinorField b, x;
-    b.alloc(P_F64, 2, 1, g);
-    x.alloc(P_F64, 2, 1, g);
-    pack_spinor(b, 0, bc, st);
-    if (prm.use_initial_guess) pack_spinor(x, 0, xc, st);
-    SolveStats stats = cg_solve_prepared(x, b, g64, *inner_gauge, kappa, prm, st);
-    unpack_spinor(x, 0, xc, st);
+    b.alloc(P_F64, 2, nrhs, g);
+    x.alloc(P_F64, 2, nrhs, g);
+    const size_t per = (size_t)24 * 2 * g.Vh;  // doubles per canonical full field
+    for (int k = 0; k < nrhs; k++) {
+        pack_spinor(b, k, bc + per * k, st);
+        if (prm.use_initial_guess) pack_spinor(x, k, xc + per * k, st);
+    }
+    std::vector<SolveStats> stats = cg_solve_prepared(x, b, g64, *inner_gauge, kappa, prm, st);
+    for (int k = 0; k < nrhs; k++) unpack_spinor(x, k, xc + per * k, st);
     WL_CUDA(cudaStreamSynchronize(st));
     return stats;
 }

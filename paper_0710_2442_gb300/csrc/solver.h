@@ -1,6 +1,8 @@
 // solver.h -- the even-odd CG solve (host orchestration of device kernels).
 #pragma once
 
+#include <vector>
+
 #include "blas.h"
 #include "internal.h"
 
@@ -11,7 +13,7 @@ struct SolveParams {
     int recon = 12;
     double tol = 1e-10;
     int maxiter = 100000;
-    int max_restarts = 100;
+    int max_restarts = 1000;
     double delta = 0.0;       // 0: default per precision
     int use_initial_guess = 0;
     int reliable = 1;
@@ -28,18 +30,22 @@ struct SolveStats {
     double seconds = 0.0;
 };
 
-// Mhat (dag = 0) or Mhat^dag (dag = 1) on even blocks: out = in - kappa^2 D_eo D_oe in.
-// tmp is an odd block of the same precision.  Optional |out|^2 reduction.
-void schur_apply(const GaugeField& gf, Prec sp, void* out, const void* in, void* tmp, double kappa, int dag,
-                 const RedArgs* red, const int* skip, int grid_cap, cudaStream_t st);
+// Mhat (dag = 0) or Mhat^dag (dag = 1) on even blocks of nrhs right-hand
+// sides: out = in - kappa^2 D_eo D_oe in.  tmp: odd blocks of the same
+// precision.  Optional per-rhs |out|^2 reduction and per-rhs skip flags.
+void schur_apply(const GaugeField& gf, Prec sp, Vec out, Vec in, Vec tmp, int nrhs, double kappa, int dag,
+                 const RedArgs* red, const int* skip, int skip_stride, int grid_cap, cudaStream_t st);
 
-// Solve M x = b on canonical complex128 device fields (x: V spinors, in/out).
-SolveStats cg_solve(double* x, const double* gauge_canon, const double* b, const Geom& g, double kappa,
-                    const SolveParams& prm, cudaStream_t caller);
+// Solve M x_k = b_k for the nrhs right-hand sides of b (full F64 fields; x:
+// full F64, in/out) with independent CGs run in lockstep.  g64: FP64 links;
+// glo: the inner operator's links (may be g64).  Returns one SolveStats per
+// right-hand side (outer_iters, hop_applications and seconds are shared).
+std::vector<SolveStats> cg_solve_prepared(SpinorField& x, const SpinorField& b, const GaugeField& g64,
+                                          const GaugeField& glo, double kappa, const SolveParams& prm,
+                                          cudaStream_t st);
 
-// The same solve on already-prepared fields: b full F64, x full F64 (in/out);
-// g64: F64 links; glo: the inner operator's links (may be g64).
-SolveStats cg_solve_prepared(SpinorField& x, const SpinorField& b, const GaugeField& g64, const GaugeField& glo,
-                             double kappa, const SolveParams& prm, cudaStream_t st);
+// The same on canonical complex128 device fields (nrhs fields back to back).
+std::vector<SolveStats> cg_solve(double* x, const double* gauge_canon, const double* b, int nrhs, const Geom& g,
+                                 double kappa, const SolveParams& prm, cudaStream_t st);
 
 }  // namespace wl

@@ -60,6 +60,8 @@ def _declare(lib):
         "wilson_dslash_eo_noalloc": (I, [VP, VP, VP, P(wilson_lattice), I, D, I, VP]),
         "wilson_cg_solve": (I, [VP, VP, VP, P(wilson_lattice), D, P(wilson_solver_params),
                                 P(wilson_solve_stats), VP]),
+        "wilson_cg_solve_multi": (I, [VP, VP, VP, I, P(wilson_lattice), D, P(wilson_solver_params),
+                                      P(wilson_solve_stats), VP]),
         "wilson_solver_defaults": (wilson_solver_params, [I]),
         "wilson_gauge_create": (I, [P(VP), VP, P(wilson_lattice), I, I, VP]),
         "wilson_gauge_destroy": (I, [VP]),
@@ -163,6 +165,20 @@ def wilson_cg_solve(x, gauge, b, L: wilson_lattice, kappa: float, params: wilson
     if check:
         _check(rc)
     return out
+
+
+def wilson_cg_solve_multi(x, gauge, b, nrhs: int, L: wilson_lattice, kappa: float,
+                          params: wilson_solver_params | None = None, stream=None, check: bool = True):
+    """nrhs independent solves sharing one gauge field; x, b: [nrhs, V, 4, 3].
+    Returns (rc, [per-rhs stats dicts])."""
+    p = params if params is not None else solver_defaults(WILSON_F16)
+    st = (wilson_solve_stats * int(nrhs))()
+    rc = lib().wilson_cg_solve_multi(_ptr(x), _ptr(gauge), _ptr(b), int(nrhs), ctypes.byref(L), float(kappa),
+                                     ctypes.byref(p), st, _stream(stream))
+    out = [{f: getattr(st[k], f) for f, _ in wilson_solve_stats._fields_} for k in range(int(nrhs))]
+    if check:
+        _check(rc)
+    return rc, out
 
 
 class Gauge:

@@ -155,3 +155,17 @@ def test_zero_field_f16_scale(w):
     src = np.zeros((inputs.volume(dims) // 2, 4, 3), dtype=np.complex128)
     got = handle_hop(w, U, src, dims, inputs.DEFAULT_PHASES, w.WILSON_F16, 12, 0, 1, w.WILSON_OP_HOP)
     assert np.all(got == 0)
+
+
+@pytest.mark.parametrize("prec,recon", [("f64", 18), ("f32", 12), ("f16", 12)])
+@pytest.mark.parametrize("dag", [False, True])
+def test_handle_schur(w, oracle_mod, prec, recon, dag):
+    dims = (6, 4, 6, 10)
+    U = inputs.gauge_field(dims, "weak", eps=0.3, seed=116)
+    src = inputs.gaussian_spinor(inputs.volume(dims) // 2, seed=117, nrhs=2)
+    kappa = 0.1350
+    got = handle_hop(w, U, src, dims, CPLX_PHASES, w.PREC[prec], recon, 0, 0,
+                     w.WILSON_OP_SCHUR_DAG if dag else w.WILSON_OP_SCHUR, kappa, nrhs=2)
+    for k in range(2):
+        want = oracle_mod.schur(U, src[k], dims, kappa, 0, dag, CPLX_PHASES)
+        assert rel_l2(got[k], want) <= TOL[prec]

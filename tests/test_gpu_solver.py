@@ -101,3 +101,43 @@ def test_zero_source(w):
     b = np.zeros((inputs.volume(dims), 4, 3), dtype=np.complex128)
     x, st = solve(w, U, b, dims, 0.13, w.WILSON_F16)
     assert st["rc"] == 0 and np.all(x == 0)
+
+
+@pytest.mark.parametrize("inner", ["f64", "f16", "f32"])
+def test_multi_rhs_solve(w, oracle_mod, inner):
+    """12 right-hand sides (point sources and Gaussian noise) sharing one gauge
+    field, solved together; each reaches the target against the oracle's M."""
+    dims = (4, 4, 4, 8)
+    kappa = 0.1350
+    U = inputs.gauge_field(dims, "weak", eps=0.3, seed=212)
+    V = inputs.volume(dims)
+    b = np.concatenate([inputs.point_sources(dims, site=5)[:8],
+                        inputs.gaussian_spinor(dims, seed=213, nrhs=4)], axis=0)
+    L = w.lattice(dims)
+    x = dev(np.zeros_like(b))
+    rc, st = w.wilson_cg_solve_multi(x, dev(U), dev(b), 12, L, kappa, w.solver_defaults(w.PREC[inner]))
+    xs = host(x)
+    assert rc == 0
+    for k in range(12):
+        assert st[k]["true_rel_resid"] <= 1e-10
+        assert true_resid(oracle_mod, U, xs[k], b[k], dims, kappa) <= 1.1e-10
+    # the lockstep solve gives the single-rhs solution
+    x1, _ = solve(w, U, b[9], dims, kappa, w.PREC[inner])
+    assert rel_l2(xs[9], x1) <= 1e-8
+
+
+def test_multi_rhs_with_zero_and_easy_rhs(w, oracle_mod):
+    """Right-hand sides that finish at different times (a zero source finishes
+    at once) are skipped while the others continue."""
+    dims = (4, 4, 4, 4)
+    kappa = 0.13
+    U = inputs.gauge_field(dims, "weak", eps=0.3, seed=214)
+    b = inputs.gaussian_spinor(dims, seed=215, nrhs=3)
+    b[1] = 0
+    L = w.lattice(dims)
+    x = dev(np.zeros_like(b))
+    rc, st = w.wilson_cg_solve_multi(x, dev(U), dev(b), 3, L, kappa, w.solver_defaults(w.WILSON_F16))
+    xs = host(x)
+    assert rc == 0 and np.all(xs[1] == 0)
+    for k in (0, 2):
+        assert true_resid(oracle_mod, U, xs[k], b[k], dims, kappa) <= 1.1e-10
