@@ -141,6 +141,37 @@ int wilson_cg_solve(double* x, const double* gauge, const double* b, const wilso
 int wilson_cg_solve_multi(double* x, const double* gauge, const double* b, int nrhs, const wilson_lattice* L,
                           double kappa, const wilson_solver_params* p, wilson_solve_stats* st, void* stream);
 
+/* Many independent solves on lattices of different sizes, each with its
+ * own links, kappa and source, in ONE CUDA graph launch: a device-side loop
+ * (conditional graph node) runs every problem's CGNR + FP64-correction state
+ * machine over a tile table that covers all problems, FP64 corrections and
+ * reduced-precision CG iterations of different problems running as parallel
+ * graph branches.  Inner precision F32, F16 or BF16 (links with 12 reals).
+ * st[i].seconds is problem i's completion time measured on the device from
+ * the start of the batch; the loop stops after an iteration cap or a
+ * wall-clock budget even if some problem is unfinished (WILSON_ERR_TIMEOUT
+ * for those). */
+typedef struct {
+    wilson_lattice L;
+    double kappa;
+    const double* gauge;  /* 4V links, canonical, device                                  */
+    const double* b;      /* V spinors, canonical, device                                 */
+    double* x;            /* V spinors, canonical, device: solution (initial guess if set) */
+} wilson_problem;
+
+typedef struct {
+    double seconds;         /* host wall time of the call (set-up, solve, read-back)      */
+    double device_seconds;  /* device time from the batch's start to its end               */
+    int iterations;         /* loop iterations: one CG step or FP64 correction per problem */
+    int graph_launches;     /* 1 when the loop runs on the device                          */
+    int device_loop;        /* 1: conditional-node loop; 0: host-replayed graph chunks     */
+    int timed_out;          /* 1: the iteration cap or wall-clock budget ended the loop    */
+    int tiles;              /* 256-site tiles over all problems                            */
+} wilson_batch_info;
+
+int wilson_batch_solve(int n, const wilson_problem* probs, const wilson_solver_params* p, wilson_solve_stats* st,
+                       wilson_batch_info* info, void* stream);
+
 /* ---------------------------------------------------------------------- */
 /* Handles: prepared fields for repeated (timed) applications.             */
 /* A gauge handle holds the links in the site-vectorised structure-of-     */

@@ -350,6 +350,46 @@ int wilson_cg_solve_multi(double* x, const double* gauge, const double* b, int n
     return rc;
 }
 
+int wilson_batch_solve(int n, const wilson_problem* probs, const wilson_solver_params* p, wilson_solve_stats* st_out,
+                       wilson_batch_info* info, void* stream) {
+    return guarded([&] {
+        WL_REQUIRE(n >= 1 && n <= 4096, "n must be in 1..4096");
+        WL_REQUIRE(probs != nullptr && st_out != nullptr, "problems or stats array is NULL");
+        SolveParams prm = checked_params(p, 0.0);
+        WL_REQUIRE(prm.inner == P_F32 || prm.inner == P_F16 || prm.inner == P_BF16,
+                   "batched solves run an F32, F16 or BF16 inner CG");
+        WL_REQUIRE(p->recon == 12, "batched solves store the inner links with 12 reals");
+        long long sites = 0;
+        for (int i = 0; i < n; i++) {
+            const wilson_problem& q = probs[i];
+            const Geom g = checked_geom(&q.L);
+            sites += 2LL * g.Vh;
+            check_ptr(q.gauge, "problem gauge");
+            check_ptr(q.b, "problem b");
+            check_ptr(q.x, "problem x");
+            WL_REQUIRE(std::isfinite(q.kappa), "kappa must be finite");
+            WL_REQUIRE((const void*)q.x != (const void*)q.b, "x must not alias b");
+        }
+        WL_REQUIRE(sites < (1LL << 31), "total sites must be below 2^31");
+        check_device();
+        for (int i = 0; i < n; i++)
+            WL_REQUIRE(is_device_ptr(probs[i].x) && is_device_ptr(probs[i].b) && is_device_ptr(probs[i].gauge),
+                       "wilson_batch_solve takes device pointers");
+        cudaStream_t caller = static_cast<cudaStream_t>(stream);
+        SolveStream& ss = solve_stream();
+        WL_CUDA(cudaEventRecord(ss.e0, caller));
+        WL_CUDA(cudaStreamWaitEvent(ss.s, ss.e0, 0));
+        batch_solve(n, probs, prm, st_out, info, ss.s);
+        WL_CUDA(cudaEventRecord(ss.e1, ss.s));
+        WL_CUDA(cudaStreamWaitEvent(caller, ss.e1, 0));
+        WL_CUDA(cudaStreamSynchronize(caller));
+        int worst = 0;
+        for (int i = 0; i < n; i++)
+            if (st_out[i].status != 0 && (worst == 0 || st_out[i].status == WILSON_ERR_NUMERIC)) worst = st_out[i].status;
+        if (worst) throw Error(worst, "a problem of the batch did not converge");
+    });
+}
+
 // ---------------------------------------------------------------------------
 // handles
 // ---------------------------------------------------------------------------

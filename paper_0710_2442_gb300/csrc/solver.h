@@ -3,6 +3,7 @@
 
 #include <vector>
 
+#include "../../include/wilson.h"
 #include "blas.h"
 #include "internal.h"
 
@@ -47,5 +48,9 @@ std::vector<SolveStats> cg_solve_prepared(SpinorField& x, const SpinorField& b, 
 // The same on canonical complex128 device fields (nrhs fields back to back).
 std::vector<SolveStats> cg_solve(double* x, const double* gauge_canon, const double* b, int nrhs, const Geom& g,
                                  double kappa, const SolveParams& prm, cudaStream_t st);
+
+// Many independent solves in one graph launch (batch.cu).
+void batch_solve(int n, const wilson_problem* probs, const SolveParams& prm, wilson_solve_stats* stats,
+                 wilson_batch_info* info, cudaStream_t st);
 
 }  // namespace wl

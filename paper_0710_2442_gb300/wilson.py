@@ -46,6 +46,17 @@ class wilson_solve_stats(ctypes.Structure):
                 ("seconds", ctypes.c_double)]
 
 
+class wilson_problem(ctypes.Structure):
+    _fields_ = [("L", wilson_lattice), ("kappa", ctypes.c_double), ("gauge", ctypes.c_void_p),
+                ("b", ctypes.c_void_p), ("x", ctypes.c_void_p)]
+
+
+class wilson_batch_info(ctypes.Structure):
+    _fields_ = [("seconds", ctypes.c_double), ("device_seconds", ctypes.c_double), ("iterations", ctypes.c_int),
+                ("graph_launches", ctypes.c_int), ("device_loop", ctypes.c_int), ("timed_out", ctypes.c_int),
+                ("tiles", ctypes.c_int)]
+
+
 _lib = None
 VP = ctypes.c_void_p
 I = ctypes.c_int
@@ -62,6 +73,8 @@ def _declare(lib):
                                 P(wilson_solve_stats), VP]),
         "wilson_cg_solve_multi": (I, [VP, VP, VP, I, P(wilson_lattice), D, P(wilson_solver_params),
                                       P(wilson_solve_stats), VP]),
+        "wilson_batch_solve": (I, [I, P(wilson_problem), P(wilson_solver_params), P(wilson_solve_stats),
+                                   P(wilson_batch_info), VP]),
         "wilson_solver_defaults": (wilson_solver_params, [I]),
         "wilson_gauge_create": (I, [P(VP), VP, P(wilson_lattice), I, I, VP]),
         "wilson_gauge_destroy": (I, [VP]),
@@ -179,6 +192,31 @@ def wilson_cg_solve_multi(x, gauge, b, nrhs: int, L: wilson_lattice, kappa: floa
     if check:
         _check(rc)
     return rc, out
+
+
+def wilson_batch_solve(problems, params: wilson_solver_params | None = None, stream=None, check: bool = True):
+    """Independent solves of different lattices in one graph launch.
+
+    problems: list of dicts with keys L (wilson_lattice), kappa, gauge, b, x
+    (device tensors in the canonical layout).  Returns (rc, [per-problem
+    stats dicts], batch info dict)."""
+    n = len(problems)
+    arr = (wilson_problem * n)()
+    for i, q in enumerate(problems):
+        arr[i].L = q["L"]
+        arr[i].kappa = float(q["kappa"])
+        arr[i].gauge = _ptr(q["gauge"])
+        arr[i].b = _ptr(q["b"])
+        arr[i].x = _ptr(q["x"])
+    p = params if params is not None else solver_defaults(WILSON_F16)
+    st = (wilson_solve_stats * n)()
+    info = wilson_batch_info()
+    rc = lib().wilson_batch_solve(n, arr, ctypes.byref(p), st, ctypes.byref(info), _stream(stream))
+    out = [{f: getattr(st[k], f) for f, _ in wilson_solve_stats._fields_} for k in range(n)]
+    inf = {f: getattr(info, f) for f, _ in wilson_batch_info._fields_}
+    if check:
+        _check(rc)
+    return rc, out, inf
 
 
 class Gauge:
