@@ -43,10 +43,11 @@ L2_NOTE = ("inputs larger than L2: each application streams 403 MB of links plus
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--no-solver", action="store_true", help="skip the CG comparison block")
+    ap.add_argument("--no-solver", action="store_true",
+                    help="skip the solver, multi-RHS and batch blocks (CG time-to-solution comparisons)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--apps", type=int, default=None, help="applications per step (default 100)")
     ap.add_argument("--prec", choices=["f32", "f16", "bf16"], default="f32",
@@ -251,6 +252,8 @@ def run_ours(args, ws, rank, local, fields):
     }
     if rank == 0 and not args.no_solver:
         line["cg"] = run_solver_block(w, torch, dev, stream)
+        line["multirhs"] = run_multirhs_block(w, torch, dev, stream, fields)
+        line["batch"] = run_batch_block(w, torch, dev, stream)
     return line
 
 
@@ -277,6 +280,106 @@ def run_solver_block(w, torch, dev, stream):
     if res["f64"]["rc"] == 0 and res["f16"]["rc"] == 0:
         res["speedup_f16_vs_f64"] = round(res["f64"]["seconds"] / res["f16"]["seconds"], 3)
     return res
+
+
+def run_multirhs_block(w, torch, dev, stream, fields, nrhs=12):
+    """12 right-hand sides sharing the 32^3 x 64 F32 12-real links: the
+    multi-RHS hop against the single-RHS one, and the lockstep 12-RHS CG
+    (point sources, F16 inner) against 12 sequential solves."""
+    cfg, dims, U, src = fields
+    Vh = inputs.volume(dims) // 2
+    L = w.lattice(dims)
+    kappa = inputs.WORKLOADS["multirhs12_32^3x64"]["kappa"]
+    out = {"workload": "multirhs12_32^3x64", "links": "the headline workload's field, f32 12-real"}
+    g = w.Gauge(U, L, w.WILSON_F32, 12, stream)
+    for n in (1, nrhs):
+        a = w.Spinor(L, w.WILSON_EVEN, w.WILSON_F32, n)
+        b = w.Spinor(L, w.WILSON_ODD, w.WILSON_F32, n)
+        a.load(torch.from_numpy(inputs.gaussian_spinor(Vh, seed=31, nrhs=n)).to(dev), stream)
+        for _ in range(3):
+            w.wilson_dslash_h(b, g, a, 0.0, w.WILSON_OP_HOP, stream)
+            w.wilson_dslash_h(a, g, b, 0.0, w.WILSON_OP_HOP, stream)
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        reps = 20
+        e0.record(stream)
+        for _ in range(reps // 2):
+            w.wilson_dslash_h(b, g, a, 0.0, w.WILSON_OP_HOP, stream)
+            w.wilson_dslash_h(a, g, b, 0.0, w.WILSON_OP_HOP, stream)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        t = e0.elapsed_time(e1) / 1e3 / reps
+        byts = model.compulsory_bytes_per_site("f32", 12, eo=True, nrhs=n) * Vh
+        out[f"hop_nrhs{n}"] = {"us_per_application": round(t * 1e6, 2), "us_per_rhs": round(t * 1e6 / n, 2),
+                               "GBs_compulsory": round(byts / t / 1e9, 1),
+                               "TFlops": round(model.FLOPS_PER_SITE * Vh * n / t / 1e12, 3)}
+        a.close()
+        b.close()
+    g.close()
+    out["rhs_speedup_per_rhs"] = round(out["hop_nrhs1"]["us_per_rhs"] / out[f"hop_nrhs{nrhs}"]["us_per_rhs"], 3)
+    # lockstep 12-RHS CG vs 12 sequential solves (F16 inner, point sources at the origin)
+    Ud = torch.from_numpy(U).to(dev)
+    bsrc = torch.from_numpy(inputs.point_sources(dims, site=0)).to(dev)
+    p = w.solver_defaults(w.WILSON_F16)
+    x = torch.zeros_like(bsrc)
+    w.wilson_cg_solve_multi(x, Ud, bsrc, nrhs, L, kappa, p, stream, check=False)  # tunes
+    x.zero_()
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    rc, st = w.wilson_cg_solve_multi(x, Ud, bsrc, nrhs, L, kappa, p, stream, check=False)
+    torch.cuda.synchronize(dev)
+    t_multi = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    seq = []
+    for k in range(nrhs):
+        xk = torch.zeros_like(bsrc[k])
+        seq.append(w.wilson_cg_solve(xk, Ud, bsrc[k], L, kappa, p, stream, check=False))
+    torch.cuda.synchronize(dev)
+    t_seq = time.perf_counter() - t0
+    out["cg"] = {"kappa": kappa, "inner": "f16", "rc": rc, "seconds_lockstep": round(t_multi, 4),
+                 "seconds_sequential": round(t_seq, 4), "speedup": round(t_seq / t_multi, 3),
+                 "max_true_rel_resid": max(s["true_rel_resid"] for s in st),
+                 "inner_iters": [s["inner_iters"] for s in st]}
+    del Ud, bsrc, x
+    torch.cuda.empty_cache()
+    return out
+
+
+def run_batch_block(w, torch, dev, stream):
+    """64 uneven solves in one graph launch against the same 64 solved one by one."""
+    probs = inputs.batch_problems()
+    fields = []
+    for p in probs:
+        U = inputs.gauge_field(p["dims"], "weak", eps=p["eps"], seed=p["gauge_seed"])
+        b = inputs.gaussian_spinor(p["dims"], seed=p["spinor_seed"])
+        fields.append(dict(L=w.lattice(p["dims"]), kappa=p["kappa"], gauge=torch.from_numpy(U).to(dev),
+                           b=torch.from_numpy(b).to(dev), x=torch.zeros(b.shape, dtype=torch.complex128, device=dev)))
+    prm = w.solver_defaults(w.WILSON_F16)
+    w.wilson_batch_solve(fields, prm, stream, check=False)  # tunes the batched kernels
+    for f in fields:
+        f["x"].zero_()
+    torch.cuda.synchronize(dev)
+    rc, st, info = w.wilson_batch_solve(fields, prm, stream, check=False)
+    lat = sorted(s["seconds"] for s in st)
+    sites = sum(inputs.volume(p["dims"]) for p in probs)
+    t0 = time.perf_counter()
+    for f in fields:
+        f["x"].zero_()
+        w.wilson_cg_solve(f["x"], f["gauge"], f["b"], f["L"], f["kappa"], prm, stream, check=False)
+    torch.cuda.synchronize(dev)
+    t_seq = time.perf_counter() - t0
+    q = lambda a, f: a[min(len(a) - 1, int(round(f * (len(a) - 1))))]
+    out = {"workload": "batch64_uneven", "problems": len(probs), "sites": sites, "inner": "f16", "rc": rc,
+           "device_seconds": round(info["device_seconds"], 4), "call_seconds": round(info["seconds"], 4),
+           "solves_per_s": round(len(probs) / info["device_seconds"], 1),
+           "latency_p50_s": round(q(lat, 0.5), 4), "latency_p99_s": round(q(lat, 0.99), 4),
+           "loop_iterations": info["iterations"], "graph_launches": info["graph_launches"],
+           "device_loop": info["device_loop"], "timed_out": info["timed_out"],
+           "max_true_rel_resid": max(s["true_rel_resid"] for s in st),
+           "sequential_seconds": round(t_seq, 4), "speedup_vs_sequential": round(t_seq / info["device_seconds"], 3)}
+    del fields
+    torch.cuda.empty_cache()
+    return out
 
 
 # ---------------------------------------------------------------------------
