@@ -651,12 +651,13 @@ void batch_solve(int n, const wilson_problem* probs, const SolveParams& prm, wil
         char key[96];
         snprintf(key, sizeof(key), "bhop:lo%d:n%d:t%d", (int)B.ip, n, B.ntiles);
         const BOp o = B.op(BF_Q, BF_T, BF_P, 0, 0, 2, -1, 0, BF_NONE, 0);
-        B.hop_lo = tune_launch(key, hop_candidates(), LaunchConfig{128, 1}, st, [&](const LaunchConfig& c) {
+        const std::vector<LaunchConfig>& cands = hop_candidates();
+        B.hop_lo = tune_launch(key, cands, LaunchConfig{128, 1}, st, [&](const LaunchConfig& c) {
             dispatch_low(B.ip, [&](auto I) { B.hop_t<decltype(I)::value, decltype(I)::value>(o, 0, c, st); });
         });
         snprintf(key, sizeof(key), "bhop:f64:n%d:t%d", n, B.ntiles);
         const BOp o64 = B.op(BF_Q64, BF_T64, BF_X, 0, 1, 2, -1, 0, BF_NONE, 0);
-        B.hop_64 = tune_launch(key, hop_candidates(), LaunchConfig{128, 0}, st, [&](const LaunchConfig& c) {
+        B.hop_64 = tune_launch(key, cands, LaunchConfig{128, 0}, st, [&](const LaunchConfig& c) {
             B.hop_t<P_F64, P_F64>(o64, 0, c, st);
         });
     }
