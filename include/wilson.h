@@ -176,7 +176,8 @@ int wilson_batch_solve(int n, const wilson_problem* probs, const wilson_solver_p
 /* Handles: prepared fields for repeated (timed) applications.             */
 /* A gauge handle holds the links in the site-vectorised structure-of-     */
 /* arrays layout of one precision with 12 (two rows; the third rebuilt as  */
-/* the conjugate cross product, SU(3) only) or 18 reals per link.  A spinor */
+/* the conjugate cross product, SU(3) only) or 18 reals per link (every    */
+/* precision supports both).  A spinor                                      */
 /* handle holds one subset (even, odd or full) of nrhs fields in one       */
 /* precision; F16/BF16 spinors carry one FP32 scale per site and rhs.      */
 /* ---------------------------------------------------------------------- */

@@ -267,7 +267,6 @@ static SolveParams checked_params(const wilson_solver_params* p, double kappa) {
     WL_REQUIRE(p->recon == 12 || p->recon == 18, "recon must be 12 or 18");
     SolveParams prm;
     prm.inner = to_prec(p->inner);
-    WL_REQUIRE(prm.inner == P_F64 || p->recon == 12 || prm.inner == P_F32, "F16/BF16 links are stored with 12 reals");
     prm.recon = p->recon;
     prm.tol = p->tol;
     prm.maxiter = p->maxiter;
@@ -402,7 +401,6 @@ int wilson_gauge_create(wilson_gauge** out, const double* canon, const wilson_la
         check_ptr(canon, "gauge");
         const Prec p = to_prec(prec);
         WL_REQUIRE(recon == 12 || recon == 18, "recon must be 12 or 18");
-        WL_REQUIRE(recon == 12 || p == P_F64 || p == P_F32, "F16/BF16 links are stored with 12 reals");
         check_device();
         cudaStream_t st = static_cast<cudaStream_t>(stream);
         std::unique_ptr<wilson_gauge_s> h(new wilson_gauge_s);

@@ -77,19 +77,35 @@ struct Geom {
     int Vh;            // sites per parity
     int stride;        // SoA row length (chunks) of a parity-field row, >= Vh
     double ph[4][2];   // boundary phases (re, im)
+    unsigned int dm[3];  // division by Lx, Ly, Lz: n / L = umulhi(n, dm) >> ds, exact for n < 2^31
+    int ds[3];
 };
 
 __host__ __device__ inline int round_up(int a, int b) { return (a + b - 1) / b * b; }
+
+// Round-up division by an invariant integer (Granlund & Montgomery 1994,
+// Thm. 4.2, N = 31): with l = ceil(log2 d) and m = floor(2^(31+l) / d) + 1,
+// floor(n / d) = (n * m) >> (31 + l) for 0 <= n < 2^31 (d >= 2, so l >= 1).
+inline void div_magic(int d, unsigned int& m, int& shift) {
+    int l = 0;
+    while ((1LL << l) < d) l++;
+    m = (unsigned int)((1ULL << (31 + l)) / (unsigned long long)d + 1ULL);
+    shift = l - 1;
+}
+
+__device__ __forceinline__ int div_by(int n, const Geom& g, int k) {
+    return (int)(__umulhi((unsigned int)n, g.dm[k]) >> g.ds[k]);
+}
 
 // Coordinates and canonical index of the site with half index h and parity p.
 // The canonical index is s = 2h + ((y+z+t+p) & 1) because Lx is even.
 __device__ __forceinline__ void site_of_half(int h, int p, const Geom& g, int c[4], int& s) {
     int s0 = 2 * h;
-    int r = s0 / g.L[0];
+    int r = div_by(s0, g, 0);
     int x0 = s0 - r * g.L[0];
-    int r2 = r / g.L[1];
+    int r2 = div_by(r, g, 1);
     c[1] = r - r2 * g.L[1];
-    c[3] = r2 / g.L[2];
+    c[3] = div_by(r2, g, 2);
     c[2] = r2 - c[3] * g.L[2];
     int odd = (c[1] + c[2] + c[3] + p) & 1;
     c[0] = x0 + odd;
@@ -360,5 +376,31 @@ template <>
 struct GaugeFmt<P_F16, 12> : GaugeLow12<P_F16> {};
 template <>
 struct GaugeFmt<P_BF16, 12> : GaugeLow12<P_BF16> {};
+
+// 18 low-precision reals (no reconstruction arithmetic): two rows of 16 B
+// (8 reals each) and one row of 4 B per link, 36 B in all.
+template <int P>
+struct GaugeLow18 {
+    using real = float;
+    using LT = LowT<P>;
+    static constexpr int nchunk = 3;
+    static constexpr int chunk_bytes = 12;  // mean bytes per row (36 B per link)
+    __device__ static __forceinline__ void load(const void* base, int stride, int blk, int i, cpx<float> U[3][3]) {
+        const char* b = static_cast<const char*>(base) + (size_t)blk * 36 * stride;
+        const uint4 d0 = __ldcs(reinterpret_cast<const uint4*>(b) + i);
+        const uint4 d1 = __ldcs(reinterpret_cast<const uint4*>(b + 16LL * stride) + i);
+        const unsigned int d2 = __ldcs(reinterpret_cast<const unsigned int*>(b + 32LL * stride) + i);
+        const unsigned int w[9] = {d0.x, d0.y, d0.z, d0.w, d1.x, d1.y, d1.z, d1.w, d2};
+#pragma unroll
+        for (int k = 0; k < 9; k++) {
+            const float2 f = LT::to_f2(w[k]);
+            U[k / 3][k % 3] = {f.x, f.y};
+        }
+    }
+};
+template <>
+struct GaugeFmt<P_F16, 18> : GaugeLow18<P_F16> {};
+template <>
+struct GaugeFmt<P_BF16, 18> : GaugeLow18<P_BF16> {};
 
 }  // namespace wl

@@ -35,6 +35,8 @@ static void dispatch(const HopParams& P, Prec sp, Prec gp, int R, int block, int
     else if (sp == P_F32 && gp == P_F32 && R == 18) launch_hop_prec<P_F32, P_F32, 18>(P, block, blocks, ny, dag, variant, st);
     else if (sp == P_F16 && gp == P_F16 && R == 12) launch_hop_prec<P_F16, P_F16, 12>(P, block, blocks, ny, dag, variant, st);
     else if (sp == P_BF16 && gp == P_BF16 && R == 12) launch_hop_prec<P_BF16, P_BF16, 12>(P, block, blocks, ny, dag, variant, st);
+    else if (sp == P_F16 && gp == P_F16 && R == 18) launch_hop_prec<P_F16, P_F16, 18>(P, block, blocks, ny, dag, variant, st);
+    else if (sp == P_BF16 && gp == P_BF16 && R == 18) launch_hop_prec<P_BF16, P_BF16, 18>(P, block, blocks, ny, dag, variant, st);
     else throw Error(7, "unsupported spinor/gauge precision and link-storage combination");
 }
 

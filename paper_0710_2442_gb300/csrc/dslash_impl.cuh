@@ -268,5 +268,7 @@ extern template void launch_hop_prec<P_F32, P_F32, 12>(const HopParams&, int, in
 extern template void launch_hop_prec<P_F32, P_F32, 18>(const HopParams&, int, int, int, bool, int, cudaStream_t);
 extern template void launch_hop_prec<P_F16, P_F16, 12>(const HopParams&, int, int, int, bool, int, cudaStream_t);
 extern template void launch_hop_prec<P_BF16, P_BF16, 12>(const HopParams&, int, int, int, bool, int, cudaStream_t);
+extern template void launch_hop_prec<P_F16, P_F16, 18>(const HopParams&, int, int, int, bool, int, cudaStream_t);
+extern template void launch_hop_prec<P_BF16, P_BF16, 18>(const HopParams&, int, int, int, bool, int, cudaStream_t);
 
 }  // namespace wl

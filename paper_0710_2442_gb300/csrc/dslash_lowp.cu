@@ -6,4 +6,6 @@
 namespace wl {
 template void launch_hop_prec<P_F16, P_F16, 12>(const HopParams&, int, int, int, bool, int, cudaStream_t);
 template void launch_hop_prec<P_BF16, P_BF16, 12>(const HopParams&, int, int, int, bool, int, cudaStream_t);
+template void launch_hop_prec<P_F16, P_F16, 18>(const HopParams&, int, int, int, bool, int, cudaStream_t);
+template void launch_hop_prec<P_BF16, P_BF16, 18>(const HopParams&, int, int, int, bool, int, cudaStream_t);
 }  // namespace wl

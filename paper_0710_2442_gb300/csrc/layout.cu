@@ -24,6 +24,7 @@ Geom make_geom(const int dims[4], const double ph[4][2]) {
     }
     g.Vh = (int)(V / 2);
     g.stride = round_up(g.Vh, 64);
+    for (int k = 0; k < 3; k++) div_magic(dims[k], g.dm[k], g.ds[k]);
     return g;
 }
 
@@ -165,6 +166,15 @@ __device__ __forceinline__ void store_link(char* base, int stride, int blk, int 
         for (int c = 0; c < 3; c++)
             b[(size_t)c * stride] = make_float4((float)u[2 * c].x, (float)u[2 * c].y, (float)u[2 * c + 1].x,
                                                 (float)u[2 * c + 1].y);
+    } else if (R == 18) {  // F16 / BF16, 18 reals: rows of 16, 16 and 4 bytes
+        using LT = LowT<GP == P_F16 ? P_F16 : P_BF16>;
+        char* b = base + (size_t)blk * 36 * stride;
+        unsigned int w[9];
+#pragma unroll
+        for (int k = 0; k < 9; k++) w[k] = LT::from_f2((float)u[k].x, (float)u[k].y);
+        reinterpret_cast<uint4*>(b)[i] = make_uint4(w[0], w[1], w[2], w[3]);
+        reinterpret_cast<uint4*>(b + 16LL * stride)[i] = make_uint4(w[4], w[5], w[6], w[7]);
+        reinterpret_cast<unsigned int*>(b + 32LL * stride)[i] = w[8];
     } else {  // F16 / BF16, 12 reals
         using LT = LowT<GP == P_F16 ? P_F16 : P_BF16>;
         uint2* b = reinterpret_cast<uint2*>(base) + (size_t)blk * 3 * stride + i;
@@ -210,6 +220,8 @@ void pack_gauge(GaugeField& gf, const double* canon, cudaStream_t st) {
     else if (p == P_F32 && R == 12) pack_gauge_kernel<P_F32, 12><<<grid, block, 0, st>>>(src, base, gf.g);
     else if (p == P_F16 && R == 12) pack_gauge_kernel<P_F16, 12><<<grid, block, 0, st>>>(src, base, gf.g);
     else if (p == P_BF16 && R == 12) pack_gauge_kernel<P_BF16, 12><<<grid, block, 0, st>>>(src, base, gf.g);
+    else if (p == P_F16 && R == 18) pack_gauge_kernel<P_F16, 18><<<grid, block, 0, st>>>(src, base, gf.g);
+    else if (p == P_BF16 && R == 18) pack_gauge_kernel<P_BF16, 18><<<grid, block, 0, st>>>(src, base, gf.g);
     else throw Error(7, "unsupported link precision / storage");
     WL_LAUNCH_CHECK();
 }

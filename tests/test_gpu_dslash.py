@@ -84,7 +84,7 @@ def test_f64_schur(w, oracle_mod, dims, parity, dag):
     assert rel_l2(host(out), want) <= TOL["f64"]
 
 
-LOWP = [("f64", 18), ("f64", 12), ("f32", 12), ("f32", 18), ("f16", 12), ("bf16", 12)]
+LOWP = [("f64", 18), ("f64", 12), ("f32", 12), ("f32", 18), ("f16", 12), ("bf16", 12), ("f16", 18), ("bf16", 18)]
 
 
 @pytest.mark.parametrize("prec,recon", LOWP)
