@@ -29,6 +29,7 @@
 #include <algorithm>
 #include <chrono>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <memory>
 #include <vector>
@@ -546,7 +547,8 @@ struct BatchRun {
                  <<<blocks, c.block, 0, st>>>(A, o);                                                \
     else bhop_kernel<SP, GP, (SP == P_F64 ? 18 : 12), false, hop_variant_minb(V, SP)>              \
              <<<blocks, c.block, 0, st>>>(A, o);
-        if (v == 1) { WL_BHOP(1) } else if (v == 2) { WL_BHOP(2) } else { WL_BHOP(0) }
+        // the batch walker uses the scalar stencil: register variants only
+        if (v % 3 == 1) { WL_BHOP(1) } else if (v % 3 == 2) { WL_BHOP(2) } else { WL_BHOP(0) }
 #undef WL_BHOP
     }
     void hop(const BOp& o, int dag, cudaStream_t st) const {
@@ -651,7 +653,9 @@ void batch_solve(int n, const wilson_problem* probs, const SolveParams& prm, wil
         char key[96];
         snprintf(key, sizeof(key), "bhop:lo%d:n%d:t%d", (int)B.ip, n, B.ntiles);
         const BOp o = B.op(BF_Q, BF_T, BF_P, 0, 0, 2, -1, 0, BF_NONE, 0);
-        const std::vector<LaunchConfig>& cands = hop_candidates();
+        std::vector<LaunchConfig> cands;
+        for (const LaunchConfig& c : hop_candidates())
+            if (c.variant < 3) cands.push_back(c);
         B.hop_lo = tune_launch(key, cands, LaunchConfig{128, 1}, st, [&](const LaunchConfig& c) {
             dispatch_low(B.ip, [&](auto I) { B.hop_t<decltype(I)::value, decltype(I)::value>(o, 0, c, st); });
         });
@@ -687,8 +691,15 @@ void batch_solve(int n, const wilson_problem* probs, const SolveParams& prm, wil
     cudaGraphExec_t exec = nullptr;
     cudaGraphConditionalHandle handle{};
     int use_cond = 1;
-    const int max_iter = std::min(2 * prm.maxiter + 4 * prm.max_restarts + 16, 4000000);
-    const unsigned long long budget_ns = 60ULL * 1000000000ULL;
+    // Loop limits: an iteration cap every problem's own caps fit into, and a
+    // wall-clock budget.  WILSON_BATCH_MAX_LOOP / WILSON_BATCH_BUDGET_MS lower
+    // them (used by the tests that make the limit run out).
+    int max_iter = std::min(2 * prm.maxiter + 4 * prm.max_restarts + 16, 4000000);
+    unsigned long long budget_ns = 60ULL * 1000000000ULL;
+    if (const char* e = std::getenv("WILSON_BATCH_MAX_LOOP"))
+        if (std::atoi(e) > 0) max_iter = std::min(max_iter, std::atoi(e));
+    if (const char* e = std::getenv("WILSON_BATCH_BUDGET_MS"))
+        if (std::atoll(e) > 0) budget_ns = std::min(budget_ns, (unsigned long long)std::atoll(e) * 1000000ULL);
     WL_CUDA(cudaGraphCreate(&graph, 0));
     if (cudaGraphConditionalHandleCreate(&handle, graph, 1, cudaGraphCondAssignDefault) != cudaSuccess) {
         cudaGetLastError();

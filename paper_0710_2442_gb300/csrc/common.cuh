@@ -178,6 +178,39 @@ struct SpinorFmt<P_F64> {
     }
 };
 
+// Spinors in single and reduced precision are stored spin-paired: for each
+// colour c the components of spins (0, 1) and (2, 3) are interleaved as
+// (s0.re, s1.re, s0.im, s1.im) and (s2.re, s3.re, s2.im, s3.im), so one
+// 8-byte pair is the same real part of two spins.  The paired FP32
+// instructions of sm_100+ (FFMA2 etc.) then work on loaded data directly.
+//
+// PSpinor holds one site that way: re01[c] = (s0c.re, s1c.re), im01[c] =
+// (s0c.im, s1c.im), re23[c], im23[c] likewise for spins 2 and 3.
+struct PSpinor {
+    float2 re01[3], im01[3], re23[3], im23[3];
+};
+
+__device__ __forceinline__ void unpack_pairs(const PSpinor& q, cpx<float> v[12]) {
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+        v[0 * 3 + c] = {q.re01[c].x, q.im01[c].x};
+        v[1 * 3 + c] = {q.re01[c].y, q.im01[c].y};
+        v[2 * 3 + c] = {q.re23[c].x, q.im23[c].x};
+        v[3 * 3 + c] = {q.re23[c].y, q.im23[c].y};
+    }
+}
+
+__device__ __forceinline__ void pack_pairs(const cpx<float> v[12], PSpinor& q) {
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+        q.re01[c] = make_float2(v[c].re, v[3 + c].re);
+        q.im01[c] = make_float2(v[c].im, v[3 + c].im);
+        q.re23[c] = make_float2(v[6 + c].re, v[9 + c].re);
+        q.im23[c] = make_float2(v[6 + c].im, v[9 + c].im);
+    }
+}
+
+// F32: chunk 2c holds colour c, spins 0/1; chunk 2c+1 colour c, spins 2/3.
 template <>
 struct SpinorFmt<P_F32> {
     using real = float;
@@ -185,14 +218,32 @@ struct SpinorFmt<P_F32> {
     static constexpr int chunk_bytes = 16;
     static constexpr bool scaled = false;
     static __host__ __device__ long long field_bytes(int stride) { return 16LL * 6 * stride; }
-    __device__ static __forceinline__ void load(const void* base, int stride, int i, cpx<float> v[12]) {
+    __device__ static __forceinline__ void load_packed(const void* base, int stride, int i, PSpinor& q, float& s) {
         const float4* b = static_cast<const float4*>(base) + i;
 #pragma unroll
-        for (int c = 0; c < 6; c++) {
-            float4 d = __ldg(b + (size_t)c * stride);
-            v[2 * c] = {d.x, d.y};
-            v[2 * c + 1] = {d.z, d.w};
+        for (int c = 0; c < 3; c++) {
+            const float4 lo = __ldg(b + (size_t)(2 * c) * stride);
+            const float4 hi = __ldg(b + (size_t)(2 * c + 1) * stride);
+            q.re01[c] = make_float2(lo.x, lo.y);
+            q.im01[c] = make_float2(lo.z, lo.w);
+            q.re23[c] = make_float2(hi.x, hi.y);
+            q.im23[c] = make_float2(hi.z, hi.w);
         }
+        s = 1.0f;
+    }
+    __device__ static __forceinline__ void store_packed(void* base, int stride, int i, const PSpinor& q) {
+        float4* b = static_cast<float4*>(base) + i;
+#pragma unroll
+        for (int c = 0; c < 3; c++) {
+            b[(size_t)(2 * c) * stride] = make_float4(q.re01[c].x, q.re01[c].y, q.im01[c].x, q.im01[c].y);
+            b[(size_t)(2 * c + 1) * stride] = make_float4(q.re23[c].x, q.re23[c].y, q.im23[c].x, q.im23[c].y);
+        }
+    }
+    __device__ static __forceinline__ void load(const void* base, int stride, int i, cpx<float> v[12]) {
+        PSpinor q;
+        float s;
+        load_packed(base, stride, i, q, s);
+        unpack_pairs(q, v);
     }
     __device__ static __forceinline__ void load_raw(const void* base, int stride, int i, cpx<float> v[12],
                                                     float& s) {
@@ -200,16 +251,17 @@ struct SpinorFmt<P_F32> {
         s = 1.0f;
     }
     __device__ static __forceinline__ void store(void* base, int stride, int i, const cpx<float> v[12]) {
-        float4* b = static_cast<float4*>(base) + i;
-#pragma unroll
-        for (int c = 0; c < 6; c++)
-            b[(size_t)c * stride] = make_float4(v[2 * c].re, v[2 * c].im, v[2 * c + 1].re, v[2 * c + 1].im);
+        PSpinor q;
+        pack_pairs(v, q);
+        store_packed(base, stride, i, q);
     }
 };
 
-// 24 low-precision reals in 3 x 16 B chunks, then one FP32 scale per site
-// (row of stride floats after the 3 chunk rows).  value = q * scale, with
-// scale = max |component| of the site, so |q| <= 1.
+// 24 low-precision reals in 3 x 16 B chunks (chunk c = colour c: the
+// half2 words (s0.re, s1.re), (s0.im, s1.im), (s2.re, s3.re), (s2.im, s3.im)),
+// then one FP32 scale per site (a row of stride floats after the 3 chunk
+// rows).  value = q * scale, with scale = max |component| of the site, so
+// |q| <= 1.
 template <int P>
 struct SpinorLowFmt {
     using real = float;
@@ -222,52 +274,57 @@ struct SpinorLowFmt {
         const float* sc = reinterpret_cast<const float*>(static_cast<const char*>(base) + 48LL * stride);
         return __ldg(sc + i);
     }
-    __device__ static __forceinline__ void load(const void* base, int stride, int i, cpx<float> v[12]) {
-        const uint4* b = static_cast<const uint4*>(base) + i;
-        float s = load_scale(base, stride, i);
-#pragma unroll
-        for (int c = 0; c < 3; c++) {
-            uint4 d = __ldg(b + (size_t)c * stride);
-            float2 f0 = LT::to_f2(d.x), f1 = LT::to_f2(d.y), f2 = LT::to_f2(d.z), f3 = LT::to_f2(d.w);
-            v[4 * c + 0] = {f0.x * s, f0.y * s};
-            v[4 * c + 1] = {f1.x * s, f1.y * s};
-            v[4 * c + 2] = {f2.x * s, f2.y * s};
-            v[4 * c + 3] = {f3.x * s, f3.y * s};
-        }
-    }
     // The stored values q (|q| <= 1) and the site's scale separately: the
-    // hopping kernel applies the scale in its accumulation FMA for free.
-    __device__ static __forceinline__ void load_raw(const void* base, int stride, int i, cpx<float> v[12],
-                                                    float& s) {
+    // hopping kernels apply the scale in their accumulation FMA for free.
+    __device__ static __forceinline__ void load_packed(const void* base, int stride, int i, PSpinor& q, float& s) {
         const uint4* b = static_cast<const uint4*>(base) + i;
         s = load_scale(base, stride, i);
 #pragma unroll
         for (int c = 0; c < 3; c++) {
-            uint4 d = __ldg(b + (size_t)c * stride);
-            float2 f0 = LT::to_f2(d.x), f1 = LT::to_f2(d.y), f2 = LT::to_f2(d.z), f3 = LT::to_f2(d.w);
-            v[4 * c + 0] = {f0.x, f0.y};
-            v[4 * c + 1] = {f1.x, f1.y};
-            v[4 * c + 2] = {f2.x, f2.y};
-            v[4 * c + 3] = {f3.x, f3.y};
+            const uint4 d = __ldg(b + (size_t)c * stride);
+            q.re01[c] = LT::to_f2(d.x);
+            q.im01[c] = LT::to_f2(d.y);
+            q.re23[c] = LT::to_f2(d.z);
+            q.im23[c] = LT::to_f2(d.w);
         }
     }
-    __device__ static __forceinline__ void store(void* base, int stride, int i, const cpx<float> v[12]) {
+    __device__ static __forceinline__ void store_packed(void* base, int stride, int i, const PSpinor& q) {
         float m = 0.f;
 #pragma unroll
-        for (int k = 0; k < 12; k++) m = fmaxf(m, fmaxf(fabsf(v[k].re), fabsf(v[k].im)));
-        float inv = m > 0.f ? 1.0f / m : 0.f;
+        for (int c = 0; c < 3; c++) {
+            m = fmaxf(m, fmaxf(fmaxf(fabsf(q.re01[c].x), fabsf(q.re01[c].y)), fmaxf(fabsf(q.im01[c].x), fabsf(q.im01[c].y))));
+            m = fmaxf(m, fmaxf(fmaxf(fabsf(q.re23[c].x), fabsf(q.re23[c].y)), fmaxf(fabsf(q.im23[c].x), fabsf(q.im23[c].y))));
+        }
+        const float inv = m > 0.f ? 1.0f / m : 0.f;
         uint4* b = static_cast<uint4*>(base) + i;
 #pragma unroll
         for (int c = 0; c < 3; c++) {
             uint4 d;
-            d.x = LT::from_f2(v[4 * c + 0].re * inv, v[4 * c + 0].im * inv);
-            d.y = LT::from_f2(v[4 * c + 1].re * inv, v[4 * c + 1].im * inv);
-            d.z = LT::from_f2(v[4 * c + 2].re * inv, v[4 * c + 2].im * inv);
-            d.w = LT::from_f2(v[4 * c + 3].re * inv, v[4 * c + 3].im * inv);
+            d.x = LT::from_f2(q.re01[c].x * inv, q.re01[c].y * inv);
+            d.y = LT::from_f2(q.im01[c].x * inv, q.im01[c].y * inv);
+            d.z = LT::from_f2(q.re23[c].x * inv, q.re23[c].y * inv);
+            d.w = LT::from_f2(q.im23[c].x * inv, q.im23[c].y * inv);
             b[(size_t)c * stride] = d;
         }
         float* sc = reinterpret_cast<float*>(static_cast<char*>(base) + 48LL * stride);
         sc[i] = m;
+    }
+    __device__ static __forceinline__ void load_raw(const void* base, int stride, int i, cpx<float> v[12],
+                                                    float& s) {
+        PSpinor q;
+        load_packed(base, stride, i, q, s);
+        unpack_pairs(q, v);
+    }
+    __device__ static __forceinline__ void load(const void* base, int stride, int i, cpx<float> v[12]) {
+        float s;
+        load_raw(base, stride, i, v, s);
+#pragma unroll
+        for (int k = 0; k < 12; k++) v[k] = {v[k].re * s, v[k].im * s};
+    }
+    __device__ static __forceinline__ void store(void* base, int stride, int i, const cpx<float> v[12]) {
+        PSpinor q;
+        pack_pairs(v, q);
+        store_packed(base, stride, i, q);
     }
 };
 template <>

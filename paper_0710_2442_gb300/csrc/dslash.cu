@@ -2,6 +2,7 @@
 // dslash_impl.cuh): picks the instantiation for the storage precisions and
 // link format, and the launch configuration from the autotuner.
 #include <cstdio>
+#include <cstdlib>
 #include <string>
 
 #include "dslash_impl.cuh"
@@ -70,9 +71,16 @@ void launch_hop(const HopLaunch& L, cudaStream_t st) {
     const int R = gf.recon;
 
     LaunchConfig cfg;
+    const char* forced = std::getenv("WILSON_HOP_VARIANT");  // pins the kernel (tests of each variant)
     if (L.block > 0) {
         cfg.block = L.block;
         cfg.variant = L.variant;
+    } else if (forced && *forced) {
+        cfg.variant = std::atoi(forced);
+        const char* fb = std::getenv("WILSON_HOP_BLOCK");
+        cfg.block = fb && std::atoi(fb) > 0 ? std::atoi(fb) : 128;
+        WL_REQUIRE(cfg.variant >= 0 && cfg.variant < kHopVariants, "WILSON_HOP_VARIANT out of range");
+        WL_REQUIRE(cfg.block == 64 || cfg.block == 128 || cfg.block == 256, "WILSON_HOP_BLOCK must be 64, 128 or 256");
     } else {
         char key[160];
         snprintf(key, sizeof(key), "hop:s%d:g%d:r%d:d%d:f%d:x%d:n%d:%dx%dx%dx%d", (int)sp, (int)gp, R, (int)dag,

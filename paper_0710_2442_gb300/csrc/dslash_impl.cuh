@@ -241,24 +241,254 @@ __global__ void __launch_bounds__(256, MINB) hop_kernel(const HopParams P) {
     if (P.reduce) grid_reduce(nrm, P.red, k, nb * gridDim.y, sb + nb * blockIdx.y);
 }
 
-// Kernel variants: blocks of 256 threads guaranteed resident per SM, i.e. a
-// register budget of 128 / 85 / 64 per thread (FP64: 255 / 128 / 85, since
-// its operands take two registers each).
-constexpr int kHopVariants = 3;
-constexpr int hop_variant_minb(int v, int sp) { return (sp == P_F64 ? 1 : 2) + v; }
+// ---------------------------------------------------------------------------
+// The same stencil on paired FP32 instructions (sm_100+: FFMA2 / FMUL2 work
+// on two floats at once).  Spinors arrive spin-paired (PSpinor); the half
+// spinor pairs the two half-spin rows, hr[c] = (h0c.re, h1c.re), so the link
+// multiplies both rows in one paired FMA per real term, and the result
+// accumulates into the spin-paired accumulator.  Operations and rounding per
+// real number are those of the scalar kernel (each paired FMA is two FP32
+// FMAs); only the instruction count changes.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float2 bc2(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 sw2(float2 a) { return make_float2(a.y, a.x); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+
+struct PHalf {
+    float2 re[3], im[3];
+};
+
+// (1 - S g_mu) psi in paired form (same equations as project()).
+template <int MU, int S>
+__device__ __forceinline__ void project_p(const PSpinor& q, PHalf& h) {
+    constexpr float s = (float)S;
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+        if (MU == 0) {  // h0 = p0 - S i p3, h1 = p1 - S i p2
+            h.re[c] = fma2(bc2(s), sw2(q.im23[c]), q.re01[c]);
+            h.im[c] = fma2(bc2(-s), sw2(q.re23[c]), q.im01[c]);
+        } else if (MU == 1) {  // h0 = p0 + S p3, h1 = p1 - S p2
+            h.re[c] = fma2(make_float2(s, -s), sw2(q.re23[c]), q.re01[c]);
+            h.im[c] = fma2(make_float2(s, -s), sw2(q.im23[c]), q.im01[c]);
+        } else if (MU == 2) {  // h0 = p0 - S i p2, h1 = p1 + S i p3
+            h.re[c] = fma2(make_float2(s, -s), q.im23[c], q.re01[c]);
+            h.im[c] = fma2(make_float2(-s, s), q.re23[c], q.im01[c]);
+        } else {  // h0 = p0 - S p2, h1 = p1 - S p3
+            h.re[c] = fma2(bc2(-s), q.re23[c], q.re01[c]);
+            h.im[c] = fma2(bc2(-s), q.im23[c], q.im01[c]);
+        }
+    }
+}
+
+// w = U h (ADJ = false) or U^dag h (ADJ = true), both half-spin rows at once.
+template <bool ADJ>
+__device__ __forceinline__ void su3_mul_p(const cpx<float> U[3][3], const PHalf& h, PHalf& w) {
+#pragma unroll
+    for (int i = 0; i < 3; i++) {
+        float2 wr, wi;
+#pragma unroll
+        for (int k = 0; k < 3; k++) {
+            const cpx<float> u = ADJ ? U[k][i] : U[i][k];
+            const float ui = ADJ ? -u.im : u.im;  // the adjoint takes conj(U_ki)
+            if (k == 0) {
+                wr = mul2(bc2(u.re), h.re[0]);
+                wi = mul2(bc2(u.re), h.im[0]);
+            } else {
+                wr = fma2(bc2(u.re), h.re[k], wr);
+                wi = fma2(bc2(u.re), h.im[k], wi);
+            }
+            wr = fma2(bc2(-ui), h.im[k], wr);
+            wi = fma2(bc2(ui), h.re[k], wi);
+        }
+        w.re[i] = wr;
+        w.im[i] = wi;
+    }
+}
+
+// acc (+)= sc * (1 - S g_mu)-image of w (same equations as expand()).
+template <int MU, int S, bool FIRST>
+__device__ __forceinline__ void expand_p(PSpinor& a, const PHalf& w, float sc) {
+    const float t = (float)S * sc;
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+        float2 kr, ki, xr, xi;  // lower pair += kr * xr (re parts), ki * xi (im parts)
+        if (MU == 0) {  // (S i w1, S i w0)
+            kr = bc2(-t), xr = sw2(w.im[c]);
+            ki = bc2(t), xi = sw2(w.re[c]);
+        } else if (MU == 1) {  // (-S w1, S w0)
+            kr = make_float2(-t, t), xr = sw2(w.re[c]);
+            ki = make_float2(-t, t), xi = sw2(w.im[c]);
+        } else if (MU == 2) {  // (S i w0, -S i w1)
+            kr = make_float2(-t, t), xr = w.im[c];
+            ki = make_float2(t, -t), xi = w.re[c];
+        } else {  // (-S w0, -S w1)
+            kr = bc2(-t), xr = w.re[c];
+            ki = bc2(-t), xi = w.im[c];
+        }
+        if (FIRST) {
+            a.re01[c] = mul2(bc2(sc), w.re[c]);
+            a.im01[c] = mul2(bc2(sc), w.im[c]);
+            a.re23[c] = mul2(kr, xr);
+            a.im23[c] = mul2(ki, xi);
+        } else {
+            a.re01[c] = fma2(bc2(sc), w.re[c], a.re01[c]);
+            a.im01[c] = fma2(bc2(sc), w.im[c], a.im01[c]);
+            a.re23[c] = fma2(kr, xr, a.re23[c]);
+            a.im23[c] = fma2(ki, xi, a.im23[c]);
+        }
+    }
+}
+
+template <int SP, int GP, int R, bool DAG, int MU, bool FIRST>
+__device__ __forceinline__ void hop_dir_p(PSpinor& acc, const HopParams& P, const char* in, int p, int h,
+                                          const int c[4], int s) {
+    using SF = SpinorFmt<SP>;
+    using GF = GaugeFmt<GP, R>;
+    const Geom& g = P.g;
+    const int L = g.L[MU];
+    const int smu = MU == 0 ? 1 : MU == 1 ? g.L[0] : MU == 2 ? g.L[0] * g.L[1] : g.L[0] * g.L[1] * g.L[2];
+    constexpr int SF_ = DAG ? -1 : 1;
+    {
+        const bool wrap = c[MU] == L - 1;
+        const int sn = wrap ? s - (L - 1) * smu : s + smu;
+        PSpinor q;
+        PHalf hh, w;
+        cpx<float> U[3][3];
+        float sc;
+        SF::load_packed(in, g.stride, sn >> 1, q, sc);
+        GF::load(P.gauge, g.stride, p * 4 + MU, h, U);
+        project_p<MU, SF_>(q, hh);
+        if (wrap) {
+            const float er = (float)g.ph[MU][0], ei = (float)g.ph[MU][1];
+#pragma unroll
+            for (int k = 0; k < 3; k++) {
+                const float2 r = hh.re[k], m = hh.im[k];
+                hh.re[k] = fma2(bc2(-ei), m, mul2(bc2(er), r));
+                hh.im[k] = fma2(bc2(ei), r, mul2(bc2(er), m));
+            }
+        }
+        su3_mul_p<false>(U, hh, w);
+        expand_p<MU, SF_, FIRST>(acc, w, sc);
+    }
+    {
+        const bool wrap = c[MU] == 0;
+        const int sn = wrap ? s + (L - 1) * smu : s - smu;
+        const int hn = sn >> 1;
+        PSpinor q;
+        PHalf hh, w;
+        cpx<float> U[3][3];
+        float sc;
+        SF::load_packed(in, g.stride, hn, q, sc);
+        GF::load(P.gauge, g.stride, (1 - p) * 4 + MU, hn, U);
+        project_p<MU, -SF_>(q, hh);
+        if (wrap) {
+            const float er = (float)g.ph[MU][0], ei = -(float)g.ph[MU][1];
+#pragma unroll
+            for (int k = 0; k < 3; k++) {
+                const float2 r = hh.re[k], m = hh.im[k];
+                hh.re[k] = fma2(bc2(-ei), m, mul2(bc2(er), r));
+                hh.im[k] = fma2(bc2(ei), r, mul2(bc2(er), m));
+            }
+        }
+        su3_mul_p<true>(U, hh, w);
+        expand_p<MU, -SF_, false>(acc, w, sc);
+    }
+}
+
+template <int SP, int GP, int R, bool DAG, int MINB>
+__global__ void __launch_bounds__(256, MINB) hop_kernel_p(const HopParams P) {
+    using SF = SpinorFmt<SP>;
+    const int k = blockIdx.x % P.nrhs;
+    const int sb = blockIdx.x / P.nrhs;
+    const int nb = gridDim.x / P.nrhs;
+    if (P.skip && __ldcg(P.skip + (size_t)k * P.skip_stride)) return;
+    const int p = P.full ? (int)blockIdx.y : P.out_parity;
+    const int pin = 1 - p;
+    char* out = P.out + (P.full ? p * P.out_pstep : 0) + k * P.out_rstep;
+    const char* in = P.in + (P.full ? pin * P.in_pstep : 0) + k * P.in_rstep;
+    const char* x = P.x ? P.x + (P.full ? p * P.x_pstep : 0) + k * P.x_rstep : nullptr;
+    const Geom& g = P.g;
+    const float a = (float)P.a;
+    double nrm = 0.0;
+    for (int h = sb * blockDim.x + threadIdx.x; h - (int)threadIdx.x < g.Vh; h += nb * blockDim.x) {
+        if (h >= g.Vh) continue;
+        int c[4], s;
+        site_of_half(h, p, g, c, s);
+        PSpinor acc;
+        hop_dir_p<SP, GP, R, DAG, 0, true>(acc, P, in, p, h, c, s);
+        hop_dir_p<SP, GP, R, DAG, 1, false>(acc, P, in, p, h, c, s);
+        hop_dir_p<SP, GP, R, DAG, 2, false>(acc, P, in, p, h, c, s);
+        hop_dir_p<SP, GP, R, DAG, 3, false>(acc, P, in, p, h, c, s);
+        if (P.xpay) {
+            PSpinor xq;
+            float xs;
+            SF::load_packed(x, g.stride, h, xq, xs);
+            const float2 A = bc2(a), X = bc2(xs);
+#pragma unroll
+            for (int cc = 0; cc < 3; cc++) {
+                acc.re01[cc] = fma2(A, acc.re01[cc], mul2(X, xq.re01[cc]));
+                acc.im01[cc] = fma2(A, acc.im01[cc], mul2(X, xq.im01[cc]));
+                acc.re23[cc] = fma2(A, acc.re23[cc], mul2(X, xq.re23[cc]));
+                acc.im23[cc] = fma2(A, acc.im23[cc], mul2(X, xq.im23[cc]));
+            }
+        } else if (P.a != 1.0) {
+            const float2 A = bc2(a);
+#pragma unroll
+            for (int cc = 0; cc < 3; cc++) {
+                acc.re01[cc] = mul2(A, acc.re01[cc]);
+                acc.im01[cc] = mul2(A, acc.im01[cc]);
+                acc.re23[cc] = mul2(A, acc.re23[cc]);
+                acc.im23[cc] = mul2(A, acc.im23[cc]);
+            }
+        }
+        if (P.reduce) {
+            float2 n2 = make_float2(0.f, 0.f);
+#pragma unroll
+            for (int cc = 0; cc < 3; cc++) {
+                n2 = fma2(acc.re01[cc], acc.re01[cc], n2);
+                n2 = fma2(acc.im01[cc], acc.im01[cc], n2);
+                n2 = fma2(acc.re23[cc], acc.re23[cc], n2);
+                n2 = fma2(acc.im23[cc], acc.im23[cc], n2);
+            }
+            nrm += (double)n2.x + (double)n2.y;
+        }
+        SF::store_packed(out, g.stride, h, acc);
+    }
+    if (P.reduce) grid_reduce(nrm, P.red, k, nb * gridDim.y, sb + nb * blockIdx.y);
+}
+
+// Kernel variants v = 0..5: v % 3 is the register budget (blocks of 256
+// threads guaranteed resident per SM: 128 / 85 / 64 registers per thread;
+// FP64: 255 / 128 / 85, its operands take two registers each); v >= 3 is the
+// paired-FP32 kernel (single and reduced precision only).
+constexpr int kHopVariants = 6;
+constexpr int hop_variant_minb(int v, int sp) { return (sp == P_F64 ? 1 : 2) + v % 3; }
+
+template <int SP, int GP, int R, int V>
+void launch_hop_v(const HopParams& P, dim3 grid, int block, bool dag, cudaStream_t st) {
+    constexpr int MINB = hop_variant_minb(V, SP);
+    if constexpr (V >= 3 && SP != P_F64) {
+        if (dag) hop_kernel_p<SP, GP, R, true, MINB><<<grid, block, 0, st>>>(P);
+        else hop_kernel_p<SP, GP, R, false, MINB><<<grid, block, 0, st>>>(P);
+    } else {
+        if (dag) hop_kernel<SP, GP, R, true, MINB><<<grid, block, 0, st>>>(P);
+        else hop_kernel<SP, GP, R, false, MINB><<<grid, block, 0, st>>>(P);
+    }
+}
 
 template <int SP, int GP, int R>
 void launch_hop_prec(const HopParams& P, int block, int blocks, int ny, bool dag, int variant, cudaStream_t st) {
     const dim3 grid(blocks, ny);
-#define WL_LAUNCH(V)                                                                           \
-    if (dag) hop_kernel<SP, GP, R, true, hop_variant_minb(V, SP)><<<grid, block, 0, st>>>(P);  \
-    else hop_kernel<SP, GP, R, false, hop_variant_minb(V, SP)><<<grid, block, 0, st>>>(P);
+    if (SP == P_F64) variant %= 3;
     switch (variant) {
-        case 1: WL_LAUNCH(1) break;
-        case 2: WL_LAUNCH(2) break;
-        default: WL_LAUNCH(0) break;
+        case 1: launch_hop_v<SP, GP, R, 1>(P, grid, block, dag, st); break;
+        case 2: launch_hop_v<SP, GP, R, 2>(P, grid, block, dag, st); break;
+        case 3: launch_hop_v<SP, GP, R, 3>(P, grid, block, dag, st); break;
+        case 4: launch_hop_v<SP, GP, R, 4>(P, grid, block, dag, st); break;
+        case 5: launch_hop_v<SP, GP, R, 5>(P, grid, block, dag, st); break;
+        default: launch_hop_v<SP, GP, R, 0>(P, grid, block, dag, st); break;
     }
-#undef WL_LAUNCH
 }
 
 // Instantiated in the per-precision translation units.

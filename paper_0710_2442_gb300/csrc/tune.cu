@@ -80,7 +80,7 @@ const std::vector<LaunchConfig>& hop_candidates() {
     static const std::vector<LaunchConfig> c = [] {
         std::vector<LaunchConfig> v;
         for (int block : {64, 128, 256})
-            for (int var = 0; var < 3; var++) v.push_back(LaunchConfig{block, var});
+            for (int var = 0; var < 6; var++) v.push_back(LaunchConfig{block, var});
         return v;
     }();
     return c;

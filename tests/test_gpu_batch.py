@@ -85,3 +85,21 @@ def test_batch_noconv_and_numeric_are_per_problem(w, oracle_mod):
     probs, hf = make_batch(w, MIX[:2], seed0=470)
     rc, st, info = w.wilson_batch_solve(probs, p, check=False)
     assert rc == w.WILSON_ERR_NOCONV and all(s["status"] == w.WILSON_ERR_NOCONV for s in st)
+
+
+def test_loop_limit_runs_out_and_context_stays_usable(w, oracle_mod, monkeypatch):
+    """The device-side loop has a hard iteration cap; when it runs out the
+    unfinished problems report WILSON_ERR_TIMEOUT and the next call works."""
+    probs, hf = make_batch(w, MIX[:3], seed0=480)
+    monkeypatch.setenv("WILSON_BATCH_MAX_LOOP", "6")
+    rc, st, info = w.wilson_batch_solve(probs, w.solver_defaults(w.WILSON_F16), check=False)
+    assert info["timed_out"] == 1 and info["iterations"] == 6
+    assert rc == w.WILSON_ERR_TIMEOUT
+    assert all(s["status"] == w.WILSON_ERR_TIMEOUT for s in st)
+    monkeypatch.delenv("WILSON_BATCH_MAX_LOOP")
+    for q in probs:
+        q["x"].zero_()
+    rc, st, info = w.wilson_batch_solve(probs, w.solver_defaults(w.WILSON_F16))
+    assert rc == 0 and info["timed_out"] == 0
+    for q, (dims, U, b, kappa) in zip(probs, hf):
+        assert true_resid(oracle_mod, U, host(q["x"]), b, dims, kappa) <= 1.1e-10

@@ -169,3 +169,40 @@ def test_handle_schur(w, oracle_mod, prec, recon, dag):
     for k in range(2):
         want = oracle_mod.schur(U, src[k], dims, kappa, 0, dag, CPLX_PHASES)
         assert rel_l2(got[k], want) <= TOL[prec]
+
+
+# Every kernel variant (register budgets 0-2 of the scalar stencil, 3-5 of the
+# paired-FP32 stencil) against the oracle, pinned through WILSON_HOP_VARIANT so
+# that the autotuner's choice does not decide which code is tested.
+@pytest.mark.parametrize("variant", range(6))
+@pytest.mark.parametrize("prec,recon", [("f32", 12), ("f16", 12), ("bf16", 12), ("f32", 18), ("f16", 18)])
+def test_every_variant_eo_and_schur(w, oracle_mod, monkeypatch, variant, prec, recon):
+    monkeypatch.setenv("WILSON_HOP_VARIANT", str(variant))
+    monkeypatch.setenv("WILSON_HOP_BLOCK", str((64, 128, 256)[variant % 3]))
+    dims = (6, 4, 6, 10)
+    U = inputs.gauge_field(dims, "weak", eps=0.3, seed=118)
+    src = inputs.gaussian_spinor(inputs.volume(dims) // 2, seed=119, nrhs=2)
+    got = handle_hop(w, U, src, dims, CPLX_PHASES, w.PREC[prec], recon, 1, 0, w.WILSON_OP_HOP, nrhs=2)
+    for k in range(2):
+        assert rel_l2(got[k], oracle_mod.dslash_eo(U, src[k], dims, 0, CPLX_PHASES)) <= TOL[prec]
+    got = handle_hop(w, U, src, dims, CPLX_PHASES, w.PREC[prec], recon, 1, 1, w.WILSON_OP_SCHUR_DAG, 0.1350,
+                     nrhs=2)
+    for k in range(2):
+        assert rel_l2(got[k], oracle_mod.schur(U, src[k], dims, 0.1350, 1, True, CPLX_PHASES)) <= TOL[prec]
+    psi = inputs.gaussian_spinor(dims, seed=120)
+    got = handle_hop(w, U, psi, dims, CPLX_PHASES, w.PREC[prec], recon, w.WILSON_FULL, w.WILSON_FULL,
+                     w.WILSON_OP_M, 0.1350)
+    assert rel_l2(got, oracle_mod.wilson_m(U, psi, dims, 0.1350, CPLX_PHASES)) <= TOL[prec]
+
+
+@pytest.mark.parametrize("variant", [0, 3])
+def test_variant_solver(w, oracle_mod, monkeypatch, variant):
+    """The mixed-precision solve on each stencil family."""
+    monkeypatch.setenv("WILSON_HOP_VARIANT", str(variant))
+    dims = (4, 4, 4, 8)
+    U = inputs.gauge_field(dims, "weak", eps=0.3, seed=121)
+    b = inputs.gaussian_spinor(dims, seed=122)
+    x = dev(np.zeros_like(b))
+    st = w.wilson_cg_solve(x, dev(U), dev(b), w.lattice(dims), 0.135, w.solver_defaults(w.WILSON_F16))
+    r = b - oracle_mod.wilson_m(U, host(x), dims, 0.135)
+    assert np.linalg.norm(r) / np.linalg.norm(b) <= 1.1e-10
