@@ -35,6 +35,9 @@ sys.path.insert(0, ROOT)
 from paper_0710_2442_gb300 import inputs, model  # noqa: E402
 
 METRIC = "Dslash GFlop/s & HBM GB/s (% roofline); CG time-to-1e-10 mixed vs FP64"
+# DRAM bytes (read + write) per launch of the tuned kernel, from the ncu capture summarised in
+# profiles/hop_eo_32x32x32x64_f32_f16_f64.md (keyed by storage precision and link reals).
+NCU_TRAFFIC = {("f32", 12): 576.6e6, ("f16", 12): 280.0e6, ("f64", 18): 1620.2e6}
 WORKLOAD = "dslash_eo_f32_32^3x64"
 L2_NOTE = ("inputs larger than L2: each application streams 403 MB of links plus 2 x 101 MB of spinors "
            "through the 126 MB L2")
@@ -50,8 +53,10 @@ def parse():
                     help="skip the solver, multi-RHS and batch blocks (CG time-to-solution comparisons)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--apps", type=int, default=None, help="applications per step (default 100)")
-    ap.add_argument("--prec", choices=["f32", "f16", "bf16"], default="f32",
+    ap.add_argument("--prec", choices=["f32", "f16", "bf16", "f64"], default="f32",
                     help="storage precision of spinors and links (the workload is f32)")
+    ap.add_argument("--recon", type=int, choices=[12, 18], default=12,
+                    help="reals stored per link (the workload is 12)")
     return ap.parse_args()
 
 
@@ -173,7 +178,7 @@ def run_ours(args, ws, rank, local, fields):
     L = w.lattice(dims)
     stream = torch.cuda.current_stream(dev)
     P = w.PREC[args.prec]
-    g = w.Gauge(U, L, P, 12, stream)
+    g = w.Gauge(U, L, P, args.recon, stream)
     even = w.Spinor(L, w.WILSON_EVEN, P)
     odd = w.Spinor(L, w.WILSON_ODD, P)
     src_dev = torch.from_numpy(src).to(dev)
@@ -206,7 +211,7 @@ def run_ours(args, ws, rank, local, fields):
     launches = args.steps * apps
     t_launch = ms / 1e3 / launches
     flops = model.FLOPS_PER_SITE * Vh
-    comp_bytes = model.compulsory_bytes_per_site(args.prec, 12, eo=True) * Vh
+    comp_bytes = model.compulsory_bytes_per_site(args.prec, args.recon, eo=True) * Vh
     gflops = flops * launches * ws / (ms / 1e3) / 1e9
     peak, peak_kind = measured_peaks()
     achieved = comp_bytes / t_launch / 1e9
@@ -240,13 +245,15 @@ def run_ours(args, ws, rank, local, fields):
         "metric": METRIC, "value": round(gflops, 2), "unit": "GFlop/s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(ms / args.steps, 4), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": args.prec, "data": "synthetic",
-        "config": {"workload": WORKLOAD if args.prec == "f32" else WORKLOAD.replace("f32", args.prec),
-                   "dims": list(dims), "links": f"{args.prec} 12-real", "spinor": args.prec,
+        "config": {"workload": WORKLOAD if (args.prec, args.recon) == ("f32", 12)
+                   else WORKLOAD.replace("f32", f"{args.prec}-{args.recon}"),
+                   "dims": list(dims), "links": f"{args.prec} {args.recon}-real", "spinor": args.prec,
                    "kappa": cfg["kappa"], "applications_per_step": apps, "sites_per_application": Vh,
                    "l2": L2_NOTE, "parallelism": "replicas" if ws > 1 else "single"},
         "hbm_gbs": round(achieved * ws, 1),
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                     "frac": round(achieved / peak, 4), "traffic": None, "peak_kind": peak_kind,
+                     "frac": round(achieved / peak, 4), "traffic": NCU_TRAFFIC.get((args.prec, args.recon)),
+                     "peak_kind": peak_kind,
                      "algorithmic_bytes_per_launch": comp_bytes, "launch_us": round(t_launch * 1e6, 2)},
         "clocks": clocks, "e2e": e2e, "gpu_launches": launches,
     }
