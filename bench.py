@@ -38,6 +38,7 @@ METRIC = "Dslash GFlop/s & HBM GB/s (% roofline); CG time-to-1e-10 mixed vs FP64
 # DRAM bytes (read + write) per launch of the tuned kernel, from the ncu capture summarised in
 # profiles/hop_eo_32x32x32x64_f32_f16_f64.md (keyed by storage precision and link reals).
 NCU_TRAFFIC = {("f32", 12): 576.6e6, ("f16", 12): 280.0e6, ("f64", 18): 1620.2e6}
+FP64_PEAK_GFLOPS = 1250.0  # nominal GB300 FP64 rate
 WORKLOAD = "dslash_eo_f32_32^3x64"
 L2_NOTE = ("inputs larger than L2: each application streams 403 MB of links plus 2 x 101 MB of spinors "
            "through the 126 MB L2")
@@ -255,8 +256,16 @@ def run_ours(args, ws, rank, local, fields):
                      "frac": round(achieved / peak, 4), "traffic": NCU_TRAFFIC.get((args.prec, args.recon)),
                      "peak_kind": peak_kind,
                      "algorithmic_bytes_per_launch": comp_bytes, "launch_us": round(t_launch * 1e6, 2)},
-        "clocks": clocks, "e2e": e2e, "gpu_launches": launches,
     }
+    if args.prec == "f64":
+        # FP64 is bound by GB300's FP64 rate (FP64 pipe 91 % busy at 12 % DRAM
+        # throughput): roofline against the nominal 1.25 TFLOP/s FP64 peak.
+        gf_launch = flops / t_launch / 1e9
+        line["roofline"] = {"bound": "alu", "achieved": round(gf_launch, 1), "peak": FP64_PEAK_GFLOPS,
+                            "unit": "GFLOP/s", "frac": round(gf_launch / FP64_PEAK_GFLOPS, 4),
+                            "traffic": NCU_TRAFFIC.get((args.prec, args.recon)), "peak_kind": "nominal",
+                            "launch_us": round(t_launch * 1e6, 2)}
+    line.update({"clocks": clocks, "e2e": e2e, "gpu_launches": launches})
     if rank == 0 and not args.no_solver:
         line["cg"] = run_solver_block(w, torch, dev, stream)
         line["multirhs"] = run_multirhs_block(w, torch, dev, stream, fields)
