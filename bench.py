@@ -167,6 +167,14 @@ def make_c2_fields():
     return cfg, dims, U, src
 
 
+def workload_config(args, cfg, dims, apps, ws):
+    return {"workload": WORKLOAD if (args.prec, args.recon) == ("f32", 12)
+            else WORKLOAD.replace("f32", f"{args.prec}-{args.recon}"),
+            "dims": list(dims), "links": f"{args.prec} {args.recon}-real", "spinor": args.prec,
+            "kappa": cfg["kappa"], "applications_per_step": apps, "sites_per_application": inputs.volume(dims) // 2,
+            "l2": L2_NOTE, "parallelism": "replicas" if ws > 1 else "single"}
+
+
 def run_ours(args, ws, rank, local, fields):
     import torch
     from paper_0710_2442_gb300 import build, wilson as w
@@ -246,11 +254,7 @@ def run_ours(args, ws, rank, local, fields):
         "metric": METRIC, "value": round(gflops, 2), "unit": "GFlop/s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(ms / args.steps, 4), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": args.prec, "data": "synthetic",
-        "config": {"workload": WORKLOAD if (args.prec, args.recon) == ("f32", 12)
-                   else WORKLOAD.replace("f32", f"{args.prec}-{args.recon}"),
-                   "dims": list(dims), "links": f"{args.prec} {args.recon}-real", "spinor": args.prec,
-                   "kappa": cfg["kappa"], "applications_per_step": apps, "sites_per_application": Vh,
-                   "l2": L2_NOTE, "parallelism": "replicas" if ws > 1 else "single"},
+        "config": workload_config(args, cfg, dims, apps, ws),
         "hbm_gbs": round(achieved * ws, 1),
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                      "frac": round(achieved / peak, 4), "traffic": NCU_TRAFFIC.get((args.prec, args.recon)),
@@ -433,7 +437,7 @@ def run_reference(args, ws, rank):
     return {"metric": METRIC, "value": round(value, 4), "unit": "GFlop/s", "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": round(t_all / args.steps * 1e3, 2), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
-            "config": {"workload": WORKLOAD, "dims": list(dims), "kappa": cfg["kappa"]},
+            "config": workload_config(args, cfg, dims, args.apps or cfg["applications"], ws),
             "cpu_baseline": {"value": round(value, 4), "unit": "GFlop/s", "cores": cores, "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": round(value, 4), "unit": "GFlop/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
