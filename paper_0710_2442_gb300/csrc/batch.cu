@@ -598,6 +598,7 @@ void build_problem(HostProb& P, const wilson_problem& in, Prec ip, const SolvePa
 // Build, run and tear down one batch; fills stats[n] and info.
 void batch_solve(int n, const wilson_problem* probs, const SolveParams& prm, wilson_solve_stats* stats,
                  wilson_batch_info* info, cudaStream_t st) {
+    NvtxRange nvtx_batch("wilson batch solve");
     auto t0 = std::chrono::steady_clock::now();
     BatchRun B;
     B.nprob = n;

@@ -7,6 +7,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "common.cuh"
 #include "reduce.cuh"
 
@@ -172,6 +174,12 @@ void unpack_spinor(const SpinorField& f, int rhs, double* canon, cudaStream_t st
 void pack_gauge(GaugeField& gf, const double* canon, cudaStream_t st);
 
 int device_sm_count();
+
+// NVTX range for profilers (nsys/ncu timelines); no cost without a tool.
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+};
 
 // Set the calling thread's message returned by wilson_last_error().
 void record_error(const std::string& msg);

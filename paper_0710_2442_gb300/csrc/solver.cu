@@ -116,6 +116,7 @@ constexpr int kSkipStride = sizeof(CGScalars) / sizeof(int);
 std::vector<SolveStats> cg_solve_prepared(SpinorField& x, const SpinorField& b, const GaugeField& g64,
                                           const GaugeField& glo, double kappa, const SolveParams& prm,
                                           cudaStream_t st) {
+    NvtxRange nvtx_solve("wilson cg solve");
     auto t0 = std::chrono::steady_clock::now();
     const int nr = b.nrhs;
     std::vector<SolveStats> stats(nr);
@@ -220,6 +221,7 @@ std::vector<SolveStats> cg_solve_prepared(SpinorField& x, const SpinorField& b, 
     try {
         while (true) {
             // r64 = bhat - Mhat x_e (FP64)
+            NvtxRange nvtx_outer("fp64 correction");
             schur_apply(g64, P_F64, vec(q64, 0), vec(x, 0), vec(t64, 1), nr, kappa, 0, nullptr, nullptr, 0, 0, st);
             hops += 2;
             xmy_norm64(vec(r64, 0), vec(bhat, 0), vec(q64, 0), g, nr,

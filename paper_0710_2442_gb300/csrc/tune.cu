@@ -102,6 +102,7 @@ LaunchConfig tune_launch(const std::string& key0, const std::vector<LaunchConfig
     WL_CUDA(cudaStreamIsCapturing(st, &cs));
     if (cs != cudaStreamCaptureStatusNone) return fallback;
 
+    NvtxRange nvtx_tune("wilson autotune");
     cudaEvent_t e0, e1;
     WL_CUDA(cudaEventCreate(&e0));
     WL_CUDA(cudaEventCreate(&e1));
