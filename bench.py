@@ -389,6 +389,11 @@ def run_batch_block(w, torch, dev, stream):
     torch.cuda.synchronize(dev)
     t_seq = time.perf_counter() - t0
     q = lambda a, f: a[min(len(a) - 1, int(round(f * (len(a) - 1))))]
+    by_size = {}
+    for p, s_ in zip(probs, st):
+        by_size.setdefault("x".join(map(str, p["dims"])), []).append(s_["seconds"])
+    by_size = {k: {"n": len(v), "median_s": round(sorted(v)[len(v) // 2], 4), "max_s": round(max(v), 4)}
+               for k, v in by_size.items()}
     out = {"workload": "batch64_uneven", "problems": len(probs), "sites": sites, "inner": "f16", "rc": rc,
            "device_seconds": round(info["device_seconds"], 4), "call_seconds": round(info["seconds"], 4),
            "solves_per_s": round(len(probs) / info["device_seconds"], 1),
@@ -396,7 +401,8 @@ def run_batch_block(w, torch, dev, stream):
            "loop_iterations": info["iterations"], "graph_launches": info["graph_launches"],
            "device_loop": info["device_loop"], "timed_out": info["timed_out"],
            "max_true_rel_resid": max(s["true_rel_resid"] for s in st),
-           "sequential_seconds": round(t_seq, 4), "speedup_vs_sequential": round(t_seq / info["device_seconds"], 3)}
+           "sequential_seconds": round(t_seq, 4), "speedup_vs_sequential": round(t_seq / info["device_seconds"], 3),
+           "latency_by_lattice": by_size}
     del fields
     torch.cuda.empty_cache()
     return out

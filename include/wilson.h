@@ -142,15 +142,23 @@ int wilson_cg_solve_multi(double* x, const double* gauge, const double* b, int n
                           double kappa, const wilson_solver_params* p, wilson_solve_stats* st, void* stream);
 
 /* Many independent solves on lattices of different sizes, each with its
- * own links, kappa and source, in ONE CUDA graph launch: a device-side loop
- * (conditional graph node) runs every problem's CGNR + FP64-correction state
- * machine over a tile table that covers all problems, FP64 corrections and
- * reduced-precision CG iterations of different problems running as parallel
- * graph branches.  Inner precision F32, F16 or BF16 (links with 12 reals).
- * st[i].seconds is problem i's completion time measured on the device from
- * the start of the batch; the loop stops after an iteration cap or a
- * wall-clock budget even if some problem is unfinished (WILSON_ERR_TIMEOUT
- * for those). */
+ * own links, kappa and source, in ONE CUDA graph launch (Sec. 5 sets the
+ * lattice sizes that fit each memory level; here every size shares one GPU).
+ * Every problem runs the same CGNR + FP64-correction state machine as
+ * wilson_cg_solve.  Problems with at most 4096 sites per parity are each
+ * solved by one thread block that keeps the whole solve on its SM.  The
+ * others are grouped by lattice size into at most four classes; each class
+ * has its own device-side loop (a conditional graph node) over a tile table
+ * of its problems, FP64 corrections and reduced-precision CG steps of
+ * different problems running as parallel graph branches, and the kernels of
+ * smaller classes are scheduled ahead of larger ones (graph node priority),
+ * so every class finishes at its own pace.  Inner precision F32, F16 or BF16
+ * (links with 12 reals).  st[i].seconds is problem i's completion time
+ * measured on the device from the start of the batch; each loop stops after
+ * an iteration cap or a wall-clock budget (60 s) even if some problem is
+ * unfinished (WILSON_ERR_TIMEOUT for those).  Returns WILSON_OK if every
+ * problem converged, else WILSON_ERR_NUMERIC if any problem met a
+ * non-finite value, else the first non-OK status over the problems. */
 typedef struct {
     wilson_lattice L;
     double kappa;
@@ -162,11 +170,12 @@ typedef struct {
 typedef struct {
     double seconds;         /* host wall time of the call (set-up, solve, read-back)      */
     double device_seconds;  /* device time from the batch's start to its end               */
-    int iterations;         /* loop iterations: one CG step or FP64 correction per problem */
+    int iterations;         /* loop iterations of the longest class loop (one CG step or FP64
+                               correction per problem and iteration)                        */
     int graph_launches;     /* 1 when the loop runs on the device                          */
     int device_loop;        /* 1: conditional-node loop; 0: host-replayed graph chunks     */
     int timed_out;          /* 1: the iteration cap or wall-clock budget ended the loop    */
-    int tiles;              /* 256-site tiles over all problems                            */
+    int tiles;              /* 256-site tiles over the problems the class loops solve      */
 } wilson_batch_info;
 
 int wilson_batch_solve(int n, const wilson_problem* probs, const wilson_solver_params* p, wilson_solve_stats* st,

@@ -21,7 +21,10 @@ LIB_DIR = os.path.join(PKG, "lib")
 LIB = os.path.join(LIB_DIR, "libwilson_gb300.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
-              "-Xptxas", "-warn-spills"]
+              "-Xptxas", "-warn-spills",
+              # "expression has no effect" (e.g. a member template called without
+              # the template keyword on a dependent type) is an error
+              "--diag-error=174"]
 
 
 def nvcc() -> str:

@@ -57,6 +57,8 @@ struct BatchProb {
     double kappa, tol, delta;
     int tile0, ntiles;
     int maxiter, max_outer;
+    int small;            // 1: solved by one CTA (small_solve_kernel), no tiles
+    int keep_x;           // 1: x holds an initial guess
 };
 
 struct BatchState {
@@ -440,7 +442,8 @@ __global__ void __launch_bounds__(256) binit_kernel(const BatchArgs A, const BOp
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < A.nprob; i += gridDim.x * blockDim.x) {
         BatchState& S = A.state[i];
         S = BatchState{};
-        S.phase = S.next_phase = PH_OUTER;
+        // small problems are solved by their own CTA: the loop skips them
+        S.phase = S.next_phase = A.probs[i].small ? PH_DONE : PH_OUTER;
         S.first = 1;
         S.sc.maxiter = A.probs[i].maxiter;
     }
@@ -491,6 +494,253 @@ __global__ void bcommit_kernel(BatchState* state, int nprob, BatchGlobal* G, cud
 __global__ void bfinal_kernel(BatchGlobal* G) { G->t_end = globaltimer(); }
 
 // ---------------------------------------------------------------------------
+// CTA-resident solve of a small problem.  The paper's first layout keeps a
+// whole iterative solver in the SPEs' local stores (Sec. 5, "Data in on-chip
+// memory"); the GB300 analogue for lattices of a few thousand sites is one
+// thread block that runs the complete solve (the same FP64-corrected CG as
+// the rest of the batch) on its own SM, with the problem's fields resident in
+// L1/L2 and block barriers in place of kernel boundaries: no launch per step,
+// no device-wide synchronisation, and the problem finishes on its own clock
+// instead of advancing in lockstep with the largest lattice of the batch.
+// Loads that may see data written earlier in the same launch use the
+// coherent path (COH = true).
+// ---------------------------------------------------------------------------
+constexpr int kSmallThreads = 256;
+
+__device__ double cta_sum(double v) {  // block-wide sum, valid in every thread
+    __shared__ double s_bc;
+    const double t = block_sum(v);
+    if (threadIdx.x == 0) s_bc = t;
+    __syncthreads();
+    const double r = s_bc;
+    __syncthreads();
+    return r;
+}
+
+// out (parity p) = a * D in + x over the problem's sites; returns |out|^2.
+// Ends with a block barrier, so out is visible to the whole block.
+template <int SP, int GP, int R, bool DAG>
+__device__ double cta_hop(const Geom& g, const char* gauge, char* out, const char* in, const char* x, double a,
+                          int p) {
+    using SF = SpinorFmt<SP>;
+    using T = typename SF::real;
+    HopParams P;
+    P.g = g;
+    P.gauge = gauge;
+    const T at = (T)a;
+    double nrm = 0.0;
+    for (int h = threadIdx.x; h < g.Vh; h += blockDim.x) {
+        int c[4], s;
+        site_of_half(h, p, g, c, s);
+        cpx<T> acc[12];
+        hop_dir<SP, GP, R, DAG, 0, true, true>(acc, P, in, p, h, c, s);
+        hop_dir<SP, GP, R, DAG, 1, false, true>(acc, P, in, p, h, c, s);
+        hop_dir<SP, GP, R, DAG, 2, false, true>(acc, P, in, p, h, c, s);
+        hop_dir<SP, GP, R, DAG, 3, false, true>(acc, P, in, p, h, c, s);
+        if (x) {
+            cpx<T> xv[12];
+            SF::template load<true>(x, g.stride, h, xv);
+#pragma unroll
+            for (int k = 0; k < 12; k++) {
+                acc[k].re = fma(at, acc[k].re, xv[k].re);
+                acc[k].im = fma(at, acc[k].im, xv[k].im);
+            }
+        } else {
+#pragma unroll
+            for (int k = 0; k < 12; k++) acc[k] = cscale(at, acc[k]);
+        }
+        T n2 = 0;
+#pragma unroll
+        for (int k = 0; k < 12; k++) n2 += cnorm2(acc[k]);
+        nrm += (double)n2;
+        SF::store(out, g.stride, h, acc);
+    }
+    return cta_sum(nrm);
+}
+
+template <int IP>
+__global__ void __launch_bounds__(kSmallThreads, 1) small_solve_kernel(const BatchArgs A, const int* ids,
+                                                                       const BatchGlobal* G,
+                                                                       unsigned long long budget_ns) {
+    using TI = typename SpinorFmt<IP>::real;
+    const int pid = ids[blockIdx.x];
+    const BatchProb& Pr = A.probs[pid];
+    BatchState& S = A.state[pid];
+    const Geom g = Pr.g;
+    const double kappa = Pr.kappa, k2 = kappa * kappa;
+    char* const* f = Pr.f;
+    const char* b_e = f[BF_B];
+    const char* b_o = f[BF_B] + Pr.fp[BF_B];
+    char* x_e = f[BF_X];
+    char* x_o = f[BF_X] + Pr.fp[BF_X];
+    const int tid = threadIdx.x, nt = blockDim.x;
+
+    // set-up: zeroed iterates, |b|^2, bhat_e = b_e + kappa D_eo b_o
+    for (int h = tid; h < g.Vh; h += nt) {
+        cpx<double> z64[12];
+        cpx<float> z32[12];
+        cpx<TI> zl[12];
+#pragma unroll
+        for (int k = 0; k < 12; k++) {
+            z64[k] = {0.0, 0.0};
+            z32[k] = {0.f, 0.f};
+            zl[k] = {(TI)0.f, (TI)0.f};
+        }
+        if (!Pr.keep_x) SpinorFmt<P_F64>::store(x_e, g.stride, h, z64);
+        SpinorFmt<P_F32>::store(f[BF_XIN], g.stride, h, z32);
+        SpinorFmt<IP>::store(f[BF_P], g.stride, h, zl);
+    }
+    double nb = 0.0;
+    for (int h = tid; h < g.Vh; h += nt) {
+        cpx<double> v[12], w[12];
+        SpinorFmt<P_F64>::load<true>(b_e, g.stride, h, v);
+        SpinorFmt<P_F64>::load<true>(b_o, g.stride, h, w);
+#pragma unroll
+        for (int k = 0; k < 12; k++) nb += cnorm2(v[k]) + cnorm2(w[k]);
+    }
+    const double bnorm2 = cta_sum(nb);
+    cta_hop<P_F64, P_F64, 18, false>(g, Pr.g64, f[BF_BHAT], b_o, b_e, kappa, 0);
+    const double target2 = Pr.tol * Pr.tol * bnorm2;
+
+    int iter = 0, outer = 0, status = 0;
+    double gam = 0.0;
+    bool first = true;
+    while (true) {
+        // x_e += xin; r = bhat - Mhat x_e (FP64)
+        for (int h = tid; h < g.Vh; h += nt) {
+            cpx<double> xv[12];
+            cpx<float> ev[12];
+            SpinorFmt<P_F64>::load<true>(x_e, g.stride, h, xv);
+            SpinorFmt<P_F32>::load<true>(f[BF_XIN], g.stride, h, ev);
+#pragma unroll
+            for (int k = 0; k < 12; k++) {
+                xv[k].re += (double)ev[k].re;
+                xv[k].im += (double)ev[k].im;
+            }
+            SpinorFmt<P_F64>::store(x_e, g.stride, h, xv);
+        }
+        __syncthreads();
+        cta_hop<P_F64, P_F64, 18, false>(g, Pr.g64, f[BF_T64], x_e, nullptr, 1.0, 1);
+        cta_hop<P_F64, P_F64, 18, false>(g, Pr.g64, f[BF_Q64], f[BF_T64], x_e, -k2, 0);
+        double rn = 0.0;
+        for (int h = tid; h < g.Vh; h += nt) {
+            cpx<double> bv[12], qv[12];
+            SpinorFmt<P_F64>::load<true>(f[BF_BHAT], g.stride, h, bv);
+            SpinorFmt<P_F64>::load<true>(f[BF_Q64], g.stride, h, qv);
+            cpx<float> sv[12];
+            cpx<TI> lv[12], zl[12];
+            cpx<float> z32[12];
+#pragma unroll
+            for (int k = 0; k < 12; k++) {
+                bv[k] = csub(bv[k], qv[k]);
+                rn += cnorm2(bv[k]);
+                sv[k] = {(float)bv[k].re, (float)bv[k].im};
+                lv[k] = {(TI)bv[k].re, (TI)bv[k].im};
+                z32[k] = {0.f, 0.f};
+            }
+            // s = r, slow = r, xin = 0 (used only if the solve goes on)
+            SpinorFmt<P_F32>::store(f[BF_S], g.stride, h, sv);
+            SpinorFmt<IP>::store(f[BF_SLOW], g.stride, h, lv);
+            SpinorFmt<P_F32>::store(f[BF_XIN], g.stride, h, z32);
+        }
+        const double rn2 = cta_sum(rn);
+        if (!isfinite(rn2)) { status = WILSON_ERR_NUMERIC; break; }
+        if (rn2 <= target2) break;
+        if (outer >= Pr.max_outer || iter >= Pr.maxiter) { status = WILSON_ERR_NOCONV; break; }
+        if (globaltimer() - G->t_start > budget_ns) { status = WILSON_ERR_TIMEOUT; break; }
+        outer++;
+        // r' = Mhat'^dag s; p = r' + beta p (beta = 0 at the start)
+        cta_hop<IP, IP, 12, true>(g, Pr.glo, f[BF_T], f[BF_SLOW], nullptr, 1.0, 1);
+        const double rr0 = cta_hop<IP, IP, 12, true>(g, Pr.glo, f[BF_R], f[BF_T], f[BF_SLOW], -k2, 0);
+        if (!isfinite(rr0)) { status = WILSON_ERR_NUMERIC; break; }
+        double beta = (first || !(gam > 0.0)) ? 0.0 : rr0 / gam;
+        gam = rr0;
+        first = false;
+        const double stop = fmax(Pr.delta * sqrt(rn2), sqrt(target2));
+        const double stop2 = stop * stop;
+        while (true) {
+            for (int h = tid; h < g.Vh; h += nt) {
+                cpx<TI> pv[12], rv[12];
+                SpinorFmt<IP>::template load<true>(f[BF_P], g.stride, h, pv);
+                SpinorFmt<IP>::template load<true>(f[BF_R], g.stride, h, rv);
+#pragma unroll
+                for (int k = 0; k < 12; k++) {
+                    pv[k].re = fma((TI)beta, pv[k].re, rv[k].re);
+                    pv[k].im = fma((TI)beta, pv[k].im, rv[k].im);
+                }
+                SpinorFmt<IP>::store(f[BF_P], g.stride, h, pv);
+            }
+            __syncthreads();
+            cta_hop<IP, IP, 12, false>(g, Pr.glo, f[BF_T], f[BF_P], nullptr, 1.0, 1);
+            const double pq = cta_hop<IP, IP, 12, false>(g, Pr.glo, f[BF_Q], f[BF_T], f[BF_P], -k2, 0);
+            if (!isfinite(pq)) { status = WILSON_ERR_NUMERIC; break; }
+            if (!(pq > 0.0)) break;
+            const float alpha = (float)(gam / pq);
+            double sn = 0.0;
+            for (int h = tid; h < g.Vh; h += nt) {
+                cpx<float> xv[12], sv[12];
+                cpx<TI> pv[12], qv[12], lv[12];
+                SpinorFmt<P_F32>::load<true>(f[BF_XIN], g.stride, h, xv);
+                SpinorFmt<P_F32>::load<true>(f[BF_S], g.stride, h, sv);
+                SpinorFmt<IP>::template load<true>(f[BF_P], g.stride, h, pv);
+                SpinorFmt<IP>::template load<true>(f[BF_Q], g.stride, h, qv);
+                float n2 = 0.f;
+#pragma unroll
+                for (int k = 0; k < 12; k++) {
+                    xv[k].re = fmaf(alpha, (float)pv[k].re, xv[k].re);
+                    xv[k].im = fmaf(alpha, (float)pv[k].im, xv[k].im);
+                    sv[k].re = fmaf(-alpha, (float)qv[k].re, sv[k].re);
+                    sv[k].im = fmaf(-alpha, (float)qv[k].im, sv[k].im);
+                    n2 += cnorm2(sv[k]);
+                    lv[k] = {(TI)sv[k].re, (TI)sv[k].im};
+                }
+                sn += (double)n2;
+                SpinorFmt<P_F32>::store(f[BF_XIN], g.stride, h, xv);
+                SpinorFmt<P_F32>::store(f[BF_S], g.stride, h, sv);
+                SpinorFmt<IP>::store(f[BF_SLOW], g.stride, h, lv);
+            }
+            const double ss = cta_sum(sn);
+            iter++;
+            if (!isfinite(ss)) { status = WILSON_ERR_NUMERIC; break; }
+            if (ss <= stop2 || iter >= Pr.maxiter) break;
+            if ((iter & 15) == 0 && globaltimer() - G->t_start > budget_ns) break;
+            cta_hop<IP, IP, 12, true>(g, Pr.glo, f[BF_T], f[BF_SLOW], nullptr, 1.0, 1);
+            const double rr = cta_hop<IP, IP, 12, true>(g, Pr.glo, f[BF_R], f[BF_T], f[BF_SLOW], -k2, 0);
+            if (!isfinite(rr)) { status = WILSON_ERR_NUMERIC; break; }
+            beta = gam > 0.0 ? rr / gam : 0.0;
+            gam = rr;
+        }
+        if (status) break;
+    }
+    // x_o = b_o + kappa D_oe x_e; true residual |b - M x|^2 over both parities
+    cta_hop<P_F64, P_F64, 18, false>(g, Pr.g64, x_o, x_e, b_o, kappa, 1);
+    cta_hop<P_F64, P_F64, 18, false>(g, Pr.g64, f[BF_Q64], x_o, x_e, -kappa, 0);
+    cta_hop<P_F64, P_F64, 18, false>(g, Pr.g64, f[BF_T64], x_e, x_o, -kappa, 1);
+    double rs = 0.0;
+    for (int h = tid; h < g.Vh; h += nt) {
+        cpx<double> a[12], m[12];
+        SpinorFmt<P_F64>::load<true>(b_e, g.stride, h, a);
+        SpinorFmt<P_F64>::load<true>(f[BF_Q64], g.stride, h, m);
+#pragma unroll
+        for (int k = 0; k < 12; k++) rs += cnorm2(csub(a[k], m[k]));
+        SpinorFmt<P_F64>::load<true>(b_o, g.stride, h, a);
+        SpinorFmt<P_F64>::load<true>(f[BF_T64], g.stride, h, m);
+#pragma unroll
+        for (int k = 0; k < 12; k++) rs += cnorm2(csub(a[k], m[k]));
+    }
+    const double res2 = cta_sum(rs);
+    if (tid == 0) {
+        S.sc.iter = iter;
+        S.outer = outer;
+        S.status = status;
+        S.bnorm2 = bnorm2;
+        S.res2 = res2;
+        S.t_done = globaltimer();
+        S.phase = S.next_phase = PH_DONE;
+    }
+}
+
+// ---------------------------------------------------------------------------
 // host side
 // ---------------------------------------------------------------------------
 struct HostProb {
@@ -515,11 +765,13 @@ void dispatch_low(Prec p, F&& f) {
 struct BatchRun {
     int nprob = 0, ntiles = 0, sms = 1;
     Prec ip = P_F16;
-    std::vector<HostProb> hp;
-    DevBuf probs, state, tile_prob, global, partials, counters;
+    std::vector<int> members;  // global problem ids of this run's problems (local order)
+    DevBuf probs, state, tile_prob, global, partials, counters, ids;
     BatchArgs A{};
     int grid = 1;
     LaunchConfig hop_lo{128, 1}, hop_64{128, 0};
+    cudaGraphConditionalHandle handle{};
+    BatchGlobal* G() const { return global.as<BatchGlobal>(); }
 
     BOp op(int f_out, int f_in, int f_x, int parity, int use64, int coef, int phase, int skip_done, int fin,
            int rslot) const {
@@ -593,24 +845,19 @@ void build_problem(HostProb& P, const wilson_problem& in, Prec ip, const SolvePa
     if (prm.use_initial_guess) pack_spinor(P.f[BF_X], 0, in.x, st);
 }
 
-}  // namespace
-
-// Build, run and tear down one batch; fills stats[n] and info.
-void batch_solve(int n, const wilson_problem* probs, const SolveParams& prm, wilson_solve_stats* stats,
-                 wilson_batch_info* info, cudaStream_t st) {
-    NvtxRange nvtx_batch("wilson batch solve");
-    auto t0 = std::chrono::steady_clock::now();
-    BatchRun B;
-    B.nprob = n;
-    B.ip = prm.inner;
-    B.sms = device_sm_count();
-    B.hp.resize(n);
-    std::vector<BatchProb> desc(n);
-    std::vector<int> tiles;
-    for (int i = 0; i < n; i++) {
-        build_problem(B.hp[i], probs[i], B.ip, prm, st);
-        HostProb& P = B.hp[i];
-        BatchProb& D = desc[i];
+// Device descriptors, states and the tile table of one run.
+std::unique_ptr<BatchRun> make_run(const std::vector<HostProb>& hp, const std::vector<int>& members, bool small,
+                                   const SolveParams& prm, cudaStream_t st) {
+    auto R = std::make_unique<BatchRun>();
+    R->members = members;
+    R->nprob = (int)members.size();
+    R->ip = prm.inner;
+    R->sms = device_sm_count();
+    std::vector<BatchProb> desc(R->nprob);
+    std::vector<int> tiles, ids;
+    for (int j = 0; j < R->nprob; j++) {
+        const HostProb& P = hp[members[j]];
+        BatchProb& D = desc[j];
         std::memset(&D, 0, sizeof(D));
         D.g = P.g;
         for (int f = 0; f < BF_N; f++) {
@@ -622,76 +869,106 @@ void batch_solve(int n, const wilson_problem* probs, const SolveParams& prm, wil
         D.glo = P.glo.buf.as<const char>();
         D.kappa = P.kappa;
         D.tol = prm.tol;
-        D.delta = prm.delta > 0 ? prm.delta : (B.ip == P_F32 ? 1e-3 : 0.1);
+        D.delta = prm.delta > 0 ? prm.delta : (R->ip == P_F32 ? 1e-3 : 0.1);
         D.maxiter = prm.maxiter;
         D.max_outer = prm.max_restarts;
+        D.keep_x = prm.use_initial_guess;
+        D.small = small ? 1 : 0;
         D.tile0 = (int)tiles.size();
-        D.ntiles = (P.g.Vh + kTile - 1) / kTile;
-        for (int t = 0; t < D.ntiles; t++) tiles.push_back(i);
+        D.ntiles = small ? 0 : (P.g.Vh + kTile - 1) / kTile;
+        for (int t = 0; t < D.ntiles; t++) tiles.push_back(j);
+        ids.push_back(j);
     }
-    B.ntiles = (int)tiles.size();
-    B.probs.alloc(sizeof(BatchProb) * n);
-    B.state.alloc(sizeof(BatchState) * n);
-    B.tile_prob.alloc(sizeof(int) * B.ntiles);
-    B.global.alloc(sizeof(BatchGlobal));
+    R->ntiles = (int)tiles.size();
     constexpr int kRed = 6;  // reduction slots: prologue/epilogue, A4, A7, B2, B3, B5
-    B.partials.alloc(sizeof(double) * (size_t)kRed * B.ntiles);
-    B.counters.alloc(sizeof(unsigned int) * (size_t)kRed * n);
-    WL_CUDA(cudaMemcpyAsync(B.probs.p, desc.data(), sizeof(BatchProb) * n, cudaMemcpyHostToDevice, st));
-    WL_CUDA(cudaMemcpyAsync(B.tile_prob.p, tiles.data(), sizeof(int) * B.ntiles, cudaMemcpyHostToDevice, st));
-    WL_CUDA(cudaMemsetAsync(B.counters.p, 0, sizeof(unsigned int) * kRed * n, st));
-    WL_CUDA(cudaMemsetAsync(B.state.p, 0, sizeof(BatchState) * n, st));
-    B.A.probs = B.probs.as<BatchProb>();
-    B.A.state = B.state.as<BatchState>();
-    B.A.tile_prob = B.tile_prob.as<int>();
-    B.A.ntiles = B.ntiles;
-    B.A.nprob = n;
-    B.grid = std::max(1, std::min(B.ntiles, 8 * B.sms));
-    BatchGlobal* G = B.global.as<BatchGlobal>();
+    R->probs.alloc(sizeof(BatchProb) * R->nprob);
+    R->state.alloc(sizeof(BatchState) * R->nprob);
+    R->tile_prob.alloc(sizeof(int) * std::max(R->ntiles, 1));
+    R->ids.alloc(sizeof(int) * R->nprob);
+    R->global.alloc(sizeof(BatchGlobal));
+    R->partials.alloc(sizeof(double) * (size_t)kRed * std::max(R->ntiles, 1));
+    R->counters.alloc(sizeof(unsigned int) * (size_t)kRed * R->nprob);
+    WL_CUDA(cudaMemcpyAsync(R->probs.p, desc.data(), sizeof(BatchProb) * R->nprob, cudaMemcpyHostToDevice, st));
+    WL_CUDA(cudaMemcpyAsync(R->ids.p, ids.data(), sizeof(int) * R->nprob, cudaMemcpyHostToDevice, st));
+    if (R->ntiles)
+        WL_CUDA(cudaMemcpyAsync(R->tile_prob.p, tiles.data(), sizeof(int) * R->ntiles, cudaMemcpyHostToDevice, st));
+    WL_CUDA(cudaMemsetAsync(R->counters.p, 0, sizeof(unsigned int) * kRed * R->nprob, st));
+    WL_CUDA(cudaMemsetAsync(R->state.p, 0, sizeof(BatchState) * R->nprob, st));
+    WL_CUDA(cudaMemsetAsync(R->global.p, 0, sizeof(BatchGlobal), st));
+    R->A.probs = R->probs.as<BatchProb>();
+    R->A.state = R->state.as<BatchState>();
+    R->A.tile_prob = R->tile_prob.as<int>();
+    R->A.ntiles = R->ntiles;
+    R->A.nprob = R->nprob;
+    // blocks per SM of the tile-walking kernels; 0 (default): one block per
+    // tile, so that the block scheduler can interleave the classes' kernels
+    // tile by tile in priority order
+    int per_sm = 0;
+    if (const char* e = std::getenv("WILSON_BATCH_GRID_PER_SM")) per_sm = std::max(0, std::atoi(e));
+    R->grid = std::max(1, per_sm ? std::min(R->ntiles, per_sm * R->sms) : R->ntiles);
+    return R;
+}
 
-    // tune the two batched hop kernels (non-reducing launches on scratch fields)
-    {
-        char key[96];
-        snprintf(key, sizeof(key), "bhop:lo%d:n%d:t%d", (int)B.ip, n, B.ntiles);
-        const BOp o = B.op(BF_Q, BF_T, BF_P, 0, 0, 2, -1, 0, BF_NONE, 0);
-        std::vector<LaunchConfig> cands;
-        for (const LaunchConfig& c : hop_candidates())
-            if (c.variant < 3) cands.push_back(c);
-        B.hop_lo = tune_launch(key, cands, LaunchConfig{128, 1}, st, [&](const LaunchConfig& c) {
-            dispatch_low(B.ip, [&](auto I) { B.hop_t<decltype(I)::value, decltype(I)::value>(o, 0, c, st); });
-        });
-        snprintf(key, sizeof(key), "bhop:f64:n%d:t%d", n, B.ntiles);
-        const BOp o64 = B.op(BF_Q64, BF_T64, BF_X, 0, 1, 2, -1, 0, BF_NONE, 0);
-        B.hop_64 = tune_launch(key, cands, LaunchConfig{128, 0}, st, [&](const LaunchConfig& c) {
-            B.hop_t<P_F64, P_F64>(o64, 0, c, st);
-        });
+// Give every kernel node of g the launch priority prio.
+void set_kernel_priority(cudaGraph_t g, int prio) {
+    size_t n = 0;
+    WL_CUDA(cudaGraphGetNodes(g, nullptr, &n));
+    std::vector<cudaGraphNode_t> nodes(n);
+    WL_CUDA(cudaGraphGetNodes(g, nodes.data(), &n));
+    for (cudaGraphNode_t nd : nodes) {
+        cudaGraphNodeType t;
+        WL_CUDA(cudaGraphNodeGetType(nd, &t));
+        if (t != cudaGraphNodeTypeKernel) continue;
+        cudaKernelNodeAttrValue v{};
+        v.priority = prio;
+        WL_CUDA(cudaGraphKernelNodeSetAttribute(nd, cudaKernelNodeAttributePriority, &v));
     }
+}
 
-    const int bgrid = B.grid;
-    auto blas = [&](auto kernel, const BOp& o) {
-        kernel<<<bgrid, 256, 0, st>>>(B.A, o);
-        WL_LAUNCH_CHECK();
-    };
-    cudaStream_t st2 = nullptr;
-    cudaEvent_t fork = nullptr, join = nullptr;
-    WL_CUDA(cudaStreamCreateWithFlags(&st2, cudaStreamNonBlocking));
-    WL_CUDA(cudaEventCreateWithFlags(&fork, cudaEventDisableTiming));
-    WL_CUDA(cudaEventCreateWithFlags(&join, cudaEventDisableTiming));
-    struct Cleanup {
-        cudaStream_t s;
-        cudaEvent_t a, b;
-        ~Cleanup() {
-            if (s) cudaStreamDestroy(s);
-            if (a) cudaEventDestroy(a);
-            if (b) cudaEventDestroy(b);
-        }
-    } cleanup{st2, fork, join};
+// Group the loop problems by lattice size: one class per distinct half
+// volume, merged into at most max_classes classes of neighbouring sizes.
+std::vector<std::vector<int>> size_classes(const std::vector<HostProb>& hp, const std::vector<int>& ids,
+                                           int max_classes) {
+    std::vector<int> sizes;
+    for (int i : ids) sizes.push_back(hp[i].g.Vh);
+    std::sort(sizes.begin(), sizes.end());
+    sizes.erase(std::unique(sizes.begin(), sizes.end()), sizes.end());
+    const int nd = (int)sizes.size();
+    const int nc = std::max(1, std::min(max_classes, nd));
+    std::vector<std::vector<int>> cls(nc);
+    for (int i : ids) {
+        const int rank = (int)(std::lower_bound(sizes.begin(), sizes.end(), hp[i].g.Vh) - sizes.begin());
+        cls[(long long)rank * nc / std::max(nd, 1)].push_back(i);
+    }
+    cls.erase(std::remove_if(cls.begin(), cls.end(), [](const std::vector<int>& c) { return c.empty(); }), cls.end());
+    return cls;
+}
 
-    // ------------------------------------------------------------------ graph
-    cudaGraph_t graph = nullptr;
-    cudaGraphExec_t exec = nullptr;
-    cudaGraphConditionalHandle handle{};
-    int use_cond = 1;
+}  // namespace
+
+// Build, run and tear down one batch; fills stats[n] and info.
+void batch_solve(int n, const wilson_problem* probs, const SolveParams& prm, wilson_solve_stats* stats,
+                 wilson_batch_info* info, cudaStream_t st) {
+    NvtxRange nvtx_batch("wilson batch solve");
+    auto t0 = std::chrono::steady_clock::now();
+    const Prec ip = prm.inner;
+    std::vector<HostProb> hp(n);
+    for (int i = 0; i < n; i++) build_problem(hp[i], probs[i], ip, prm, st);
+
+    // Problems with at most small_vh sites per parity get their own CTA; the
+    // others run device loops, one per class of lattice sizes.
+    int small_vh = prm.batch_small_vh;
+    if (const char* e = std::getenv("WILSON_BATCH_SMALL_VH")) small_vh = std::atoi(e);
+    int max_classes = 4;
+    if (const char* e = std::getenv("WILSON_BATCH_CLASSES"))
+        if (std::atoi(e) > 0) max_classes = std::atoi(e);
+    std::vector<int> small_ids, loop_ids;
+    for (int i = 0; i < n; i++) (hp[i].g.Vh <= small_vh ? small_ids : loop_ids).push_back(i);
+    std::vector<std::unique_ptr<BatchRun>> loops;
+    for (const auto& c : size_classes(hp, loop_ids, max_classes)) loops.push_back(make_run(hp, c, false, prm, st));
+    std::unique_ptr<BatchRun> smallrun;
+    if (!small_ids.empty()) smallrun = make_run(hp, small_ids, true, prm, st);
+
     // Loop limits: an iteration cap every problem's own caps fit into, and a
     // wall-clock budget.  WILSON_BATCH_MAX_LOOP / WILSON_BATCH_BUDGET_MS lower
     // them (used by the tests that make the limit run out).
@@ -701,121 +978,230 @@ void batch_solve(int n, const wilson_problem* probs, const SolveParams& prm, wil
         if (std::atoi(e) > 0) max_iter = std::min(max_iter, std::atoi(e));
     if (const char* e = std::getenv("WILSON_BATCH_BUDGET_MS"))
         if (std::atoll(e) > 0) budget_ns = std::min(budget_ns, (unsigned long long)std::atoll(e) * 1000000ULL);
-    WL_CUDA(cudaGraphCreate(&graph, 0));
-    if (cudaGraphConditionalHandleCreate(&handle, graph, 1, cudaGraphCondAssignDefault) != cudaSuccess) {
-        cudaGetLastError();
-        use_cond = 0;
+
+    // tune the batched hop kernels of every loop class (non-reducing launches on scratch fields)
+    std::vector<LaunchConfig> cands;
+    for (const LaunchConfig& c : hop_candidates())
+        if (c.variant < 3) cands.push_back(c);
+    for (auto& R : loops) {
+        char key[96];
+        snprintf(key, sizeof(key), "bhop:lo%d:n%d:t%d", (int)ip, R->nprob, R->ntiles);
+        const BOp o = R->op(BF_Q, BF_T, BF_P, 0, 0, 2, -1, 0, BF_NONE, 0);
+        BatchRun* Rp = R.get();
+        R->hop_lo = tune_launch(key, cands, LaunchConfig{128, 1}, st, [&](const LaunchConfig& c) {
+            dispatch_low(ip, [&](auto I) { Rp->hop_t<decltype(I)::value, decltype(I)::value>(o, 0, c, st); });
+        });
+        snprintf(key, sizeof(key), "bhop:f64:n%d:t%d", R->nprob, R->ntiles);
+        const BOp o64 = R->op(BF_Q64, BF_T64, BF_X, 0, 1, 2, -1, 0, BF_NONE, 0);
+        R->hop_64 = tune_launch(key, cands, LaunchConfig{128, 0}, st,
+                                [&](const LaunchConfig& c) { Rp->hop_t<P_F64, P_F64>(o64, 0, c, st); });
     }
-    auto prologue = [&](cudaStream_t s) {
-        dispatch_low(B.ip, [&](auto I) {
-            binit_kernel<decltype(I)::value><<<bgrid, 256, 0, s>>>(B.A, B.op(0, 0, -1, 0, 0, 0, -1, 0, BF_NONE, 0),
-                                                                   prm.use_initial_guess, G);
+
+    cudaStream_t st2 = nullptr, st3 = nullptr;
+    cudaEvent_t fork = nullptr, join = nullptr, fork3 = nullptr, join3 = nullptr;
+    WL_CUDA(cudaStreamCreateWithFlags(&st2, cudaStreamNonBlocking));
+    WL_CUDA(cudaStreamCreateWithFlags(&st3, cudaStreamNonBlocking));
+    WL_CUDA(cudaEventCreateWithFlags(&fork, cudaEventDisableTiming));
+    WL_CUDA(cudaEventCreateWithFlags(&join, cudaEventDisableTiming));
+    WL_CUDA(cudaEventCreateWithFlags(&fork3, cudaEventDisableTiming));
+    WL_CUDA(cudaEventCreateWithFlags(&join3, cudaEventDisableTiming));
+    struct Cleanup {
+        cudaStream_t s[2];
+        cudaEvent_t e[4];
+        ~Cleanup() {
+            for (cudaStream_t x : s)
+                if (x) cudaStreamDestroy(x);
+            for (cudaEvent_t x : e)
+                if (x) cudaEventDestroy(x);
+        }
+    } cleanup{{st2, st3}, {fork, join, fork3, join3}};
+
+    auto blas = [&](const BatchRun& R, auto kernel, const BOp& o, cudaStream_t s) {
+        kernel<<<R.grid, 256, 0, s>>>(R.A, o);
+        WL_LAUNCH_CHECK();
+    };
+    auto prologue = [&](const BatchRun& R, cudaStream_t s) {
+        dispatch_low(ip, [&](auto I) {
+            binit_kernel<decltype(I)::value><<<R.grid, 256, 0, s>>>(
+                R.A, R.op(0, 0, -1, 0, 0, 0, -1, 0, BF_NONE, 0), prm.use_initial_guess, R.G());
         });
         WL_LAUNCH_CHECK();
-        blas(bnorm_kernel, B.op(0, BF_B, -1, 0, 0, 0, -1, 0, BFIN_BNORM, 0));
-        blas(bnorm_kernel, B.op(0, BF_B, -1, 1, 0, 0, -1, 0, BFIN_BNORM, 0));
+        if (!R.ntiles) return;
+        blas(R, bnorm_kernel, R.op(0, BF_B, -1, 0, 0, 0, -1, 0, BFIN_BNORM, 0), s);
+        blas(R, bnorm_kernel, R.op(0, BF_B, -1, 1, 0, 0, -1, 0, BFIN_BNORM, 0), s);
         // bhat_e = b_e + kappa D_eo b_o
-        B.hop(B.op(BF_BHAT, BF_B, BF_B, 0, 1, 1, -1, 0, BF_NONE, 0), 0, s);
+        R.hop(R.op(BF_BHAT, BF_B, BF_B, 0, 1, 1, -1, 0, BF_NONE, 0), 0, s);
     };
-    auto body = [&](cudaStream_t s) {
+    auto body = [&](const BatchRun& R, int use_handle, cudaStream_t s) {
         WL_CUDA(cudaEventRecord(fork, s));
         WL_CUDA(cudaStreamWaitEvent(st2, fork, 0));
         // branch A (OUTER problems) on s
-        blas(baxpy_kernel, B.op(0, 0, -1, 0, 0, 0, PH_OUTER, 0, BF_NONE, 1));
-        B.hop(B.op(BF_T64, BF_X, -1, 1, 1, 0, PH_OUTER, 0, BF_NONE, 1), 0, s);
-        B.hop(B.op(BF_Q64, BF_T64, BF_X, 0, 1, 2, PH_OUTER, 0, BF_NONE, 1), 0, s);
-        blas(bxmy_kernel, B.op(0, 0, -1, 0, 0, 0, PH_OUTER, 0, BFIN_OUTER, 1));
-        dispatch_low(B.ip, [&](auto I) {
-            bprep_kernel<decltype(I)::value><<<bgrid, 256, 0, s>>>(B.A, B.op(0, 0, -1, 0, 0, 0, PH_OUTER, 0,
-                                                                             BF_NONE, 2));
+        blas(R, baxpy_kernel, R.op(0, 0, -1, 0, 0, 0, PH_OUTER, 0, BF_NONE, 1), s);
+        R.hop(R.op(BF_T64, BF_X, -1, 1, 1, 0, PH_OUTER, 0, BF_NONE, 1), 0, s);
+        R.hop(R.op(BF_Q64, BF_T64, BF_X, 0, 1, 2, PH_OUTER, 0, BF_NONE, 1), 0, s);
+        blas(R, bxmy_kernel, R.op(0, 0, -1, 0, 0, 0, PH_OUTER, 0, BFIN_OUTER, 1), s);
+        dispatch_low(ip, [&](auto I) {
+            bprep_kernel<decltype(I)::value><<<R.grid, 256, 0, s>>>(R.A, R.op(0, 0, -1, 0, 0, 0, PH_OUTER, 0,
+                                                                              BF_NONE, 2));
         });
         WL_LAUNCH_CHECK();
-        B.hop(B.op(BF_T, BF_SLOW, -1, 1, 0, 0, PH_OUTER, 0, BF_NONE, 2), 1, s);
-        B.hop(B.op(BF_R, BF_T, BF_SLOW, 0, 0, 2, PH_OUTER, 0, BFIN_START, 2), 1, s);
-        dispatch_low(B.ip, [&](auto I) {
-            bp_kernel<decltype(I)::value><<<bgrid, 256, 0, s>>>(B.A, B.op(0, 0, -1, 0, 0, 0, PH_OUTER, 0, BF_NONE, 2));
+        R.hop(R.op(BF_T, BF_SLOW, -1, 1, 0, 0, PH_OUTER, 0, BF_NONE, 2), 1, s);
+        R.hop(R.op(BF_R, BF_T, BF_SLOW, 0, 0, 2, PH_OUTER, 0, BFIN_START, 2), 1, s);
+        dispatch_low(ip, [&](auto I) {
+            bp_kernel<decltype(I)::value><<<R.grid, 256, 0, s>>>(R.A, R.op(0, 0, -1, 0, 0, 0, PH_OUTER, 0, BF_NONE,
+                                                                           2));
         });
         WL_LAUNCH_CHECK();
         // branch B (INNER problems) on st2
-        B.hop(B.op(BF_T, BF_P, -1, 1, 0, 0, PH_INNER, 1, BF_NONE, 3), 0, st2);
-        B.hop(B.op(BF_Q, BF_T, BF_P, 0, 0, 2, PH_INNER, 1, BFIN_ALPHA, 3), 0, st2);
-        dispatch_low(B.ip, [&](auto I) {
-            bxs_kernel<decltype(I)::value><<<bgrid, 256, 0, st2>>>(B.A, B.op(0, 0, -1, 0, 0, 0, PH_INNER, 1,
-                                                                             BFIN_RES, 4));
+        R.hop(R.op(BF_T, BF_P, -1, 1, 0, 0, PH_INNER, 1, BF_NONE, 3), 0, st2);
+        R.hop(R.op(BF_Q, BF_T, BF_P, 0, 0, 2, PH_INNER, 1, BFIN_ALPHA, 3), 0, st2);
+        dispatch_low(ip, [&](auto I) {
+            bxs_kernel<decltype(I)::value><<<R.grid, 256, 0, st2>>>(R.A, R.op(0, 0, -1, 0, 0, 0, PH_INNER, 1,
+                                                                              BFIN_RES, 4));
         });
         WL_LAUNCH_CHECK();
-        B.hop(B.op(BF_T, BF_SLOW, -1, 1, 0, 0, PH_INNER, 1, BF_NONE, 5), 1, st2);
-        B.hop(B.op(BF_R, BF_T, BF_SLOW, 0, 0, 2, PH_INNER, 1, BFIN_BETA, 5), 1, st2);
-        dispatch_low(B.ip, [&](auto I) {
-            bp_kernel<decltype(I)::value><<<bgrid, 256, 0, st2>>>(B.A, B.op(0, 0, -1, 0, 0, 0, PH_INNER, 1,
-                                                                            BF_NONE, 5));
+        R.hop(R.op(BF_T, BF_SLOW, -1, 1, 0, 0, PH_INNER, 1, BF_NONE, 5), 1, st2);
+        R.hop(R.op(BF_R, BF_T, BF_SLOW, 0, 0, 2, PH_INNER, 1, BFIN_BETA, 5), 1, st2);
+        dispatch_low(ip, [&](auto I) {
+            bp_kernel<decltype(I)::value><<<R.grid, 256, 0, st2>>>(R.A, R.op(0, 0, -1, 0, 0, 0, PH_INNER, 1,
+                                                                             BF_NONE, 5));
         });
         WL_LAUNCH_CHECK();
         WL_CUDA(cudaEventRecord(join, st2));
         WL_CUDA(cudaStreamWaitEvent(s, join, 0));
-        bcommit_kernel<<<1, 256, 0, s>>>(B.A.state, n, G, handle, use_cond, max_iter, budget_ns);
+        bcommit_kernel<<<1, 256, 0, s>>>(R.A.state, R.nprob, R.G(), R.handle, use_handle, max_iter, budget_ns);
         WL_LAUNCH_CHECK();
     };
-    auto epilogue = [&](cudaStream_t s) {
-        // x_o = b_o + kappa D_oe x_e
-        B.hop(B.op(BF_X, BF_X, BF_B, 1, 1, 1, -1, 0, BF_NONE, 0), 0, s);
-        // M x per parity into q64 (even) and t64 (odd); |b - M x|^2
-        B.hop(B.op(BF_Q64, BF_X, BF_X, 0, 1, 3, -1, 0, BF_NONE, 0), 0, s);
-        B.hop(B.op(BF_T64, BF_X, BF_X, 1, 1, 3, -1, 0, BF_NONE, 0), 0, s);
-        blas(bnorm_kernel, B.op(0, BF_B, BF_Q64, 0, 0, 0, -1, 0, BFIN_TRUE, 0));
-        blas(bnorm_kernel, B.op(0, BF_B, BF_T64, 1, 0, 0, -1, 0, BFIN_TRUE, 0));
-        bfinal_kernel<<<1, 1, 0, s>>>(G);
+    auto epilogue = [&](const BatchRun& R, cudaStream_t s) {
+        if (R.ntiles) {
+            // x_o = b_o + kappa D_oe x_e
+            R.hop(R.op(BF_X, BF_X, BF_B, 1, 1, 1, -1, 0, BF_NONE, 0), 0, s);
+            // M x per parity into q64 (even) and t64 (odd); |b - M x|^2
+            R.hop(R.op(BF_Q64, BF_X, BF_X, 0, 1, 3, -1, 0, BF_NONE, 0), 0, s);
+            R.hop(R.op(BF_T64, BF_X, BF_X, 1, 1, 3, -1, 0, BF_NONE, 0), 0, s);
+            blas(R, bnorm_kernel, R.op(0, BF_B, BF_Q64, 0, 0, 0, -1, 0, BFIN_TRUE, 0), s);
+            blas(R, bnorm_kernel, R.op(0, BF_B, BF_T64, 1, 0, 0, -1, 0, BFIN_TRUE, 0), s);
+        }
+        bfinal_kernel<<<1, 1, 0, s>>>(R.G());
         WL_LAUNCH_CHECK();
+    };
+    // the small problems' CTA-resident solves, concurrent with the loops
+    auto small_fork = [&](cudaStream_t s) {
+        if (!smallrun) return;
+        WL_CUDA(cudaEventRecord(fork3, s));
+        WL_CUDA(cudaStreamWaitEvent(st3, fork3, 0));
+        dispatch_low(ip, [&](auto I) {
+            small_solve_kernel<decltype(I)::value><<<smallrun->nprob, kSmallThreads, 0, st3>>>(
+                smallrun->A, smallrun->ids.as<int>(), smallrun->G(), budget_ns);
+        });
+        WL_LAUNCH_CHECK();
+        WL_CUDA(cudaEventRecord(join3, st3));
+    };
+    auto small_join = [&](cudaStream_t s) {
+        if (smallrun) WL_CUDA(cudaStreamWaitEvent(s, join3, 0));
     };
 
+    // ------------------------------------------------------------------ graph
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    std::vector<cudaGraph_t> bodies;
+    // WILSON_BATCH_HOST_LOOP=1 selects the host-driven loop (the path taken
+    // where conditional graph nodes are unavailable)
+    int use_cond = 1;
+    if (const char* e = std::getenv("WILSON_BATCH_HOST_LOOP")) use_cond = std::atoi(e) ? 0 : 1;
+    WL_CUDA(cudaGraphCreate(&graph, 0));
+    for (auto& R : loops)
+        if (use_cond &&
+            cudaGraphConditionalHandleCreate(&R->handle, graph, 1, cudaGraphCondAssignDefault) != cudaSuccess) {
+            cudaGetLastError();
+            use_cond = 0;
+        }
+    // The classes' loops share the SMs.  Blocks of a smaller class's kernels
+    // are scheduled ahead of pending blocks of larger classes (graph node
+    // priorities), so small lattices finish at their own pace instead of
+    // queueing behind the largest lattice's sweeps.  WILSON_BATCH_PRIORITY=0
+    // turns this off.
+    int prio_least = 0, prio_greatest = 0;
+    WL_CUDA(cudaDeviceGetStreamPriorityRange(&prio_least, &prio_greatest));
+    int prioritise = loops.size() > 1 && prio_greatest < prio_least;
+    if (const char* e = std::getenv("WILSON_BATCH_PRIORITY")) prioritise = prioritise && std::atoi(e) != 0;
+    auto class_priority = [&](int c) { return std::min(prio_least, prio_greatest + c); };
     int graph_launches = 0;
     try {
         if (use_cond) {
             WL_CUDA(cudaStreamBeginCaptureToGraph(st, graph, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
-            prologue(st);
+            for (auto& R : loops) prologue(*R, st);
+            if (smallrun) prologue(*smallrun, st);
+            small_fork(st);
             cudaStreamCaptureStatus cs;
             const cudaGraphNode_t* deps = nullptr;
             size_t ndeps = 0;
             WL_CUDA(cudaStreamGetCaptureInfo(st, &cs, nullptr, nullptr, &deps, nullptr, &ndeps));
-            cudaGraphNodeParams cp = {cudaGraphNodeTypeConditional};
-            cp.conditional.handle = handle;
-            cp.conditional.type = cudaGraphCondTypeWhile;
-            cp.conditional.size = 1;
-            cudaGraphNode_t cnode;
-            WL_CUDA(cudaGraphAddNode(&cnode, graph, deps, nullptr, ndeps, &cp));
-            cudaGraph_t bodyg = cp.conditional.phGraph_out[0];
-            WL_CUDA(cudaStreamUpdateCaptureDependencies(st, &cnode, nullptr, 1, cudaStreamSetCaptureDependencies));
-            epilogue(st);
+            const std::vector<cudaGraphNode_t> prologue_tail(deps, deps + ndeps);
+            // one device-side while loop per size class, as parallel branches
+            std::vector<cudaGraphNode_t> cnodes;
+            for (auto& R : loops) {
+                cudaGraphNodeParams cp = {cudaGraphNodeTypeConditional};
+                cp.conditional.handle = R->handle;
+                cp.conditional.type = cudaGraphCondTypeWhile;
+                cp.conditional.size = 1;
+                cudaGraphNode_t cnode;
+                WL_CUDA(cudaGraphAddNode(&cnode, graph, prologue_tail.data(), nullptr, prologue_tail.size(), &cp));
+                cnodes.push_back(cnode);
+                bodies.push_back(cp.conditional.phGraph_out[0]);
+            }
+            if (!cnodes.empty())
+                WL_CUDA(cudaStreamUpdateCaptureDependencies(st, cnodes.data(), nullptr, cnodes.size(),
+                                                            cudaStreamSetCaptureDependencies));
+            small_join(st);
+            for (auto& R : loops) epilogue(*R, st);
+            if (smallrun) epilogue(*smallrun, st);
             cudaGraph_t out = nullptr;
             WL_CUDA(cudaStreamEndCapture(st, &out));
-            // the loop body, captured into the conditional node's child graph
-            WL_CUDA(cudaStreamBeginCaptureToGraph(st, bodyg, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
-            body(st);
-            WL_CUDA(cudaStreamEndCapture(st, &out));
-            WL_CUDA(cudaGraphInstantiate(&exec, graph, 0));
+            for (size_t c = 0; c < loops.size(); c++) {
+                WL_CUDA(cudaStreamBeginCaptureToGraph(st, bodies[c], nullptr, nullptr, 0,
+                                                      cudaStreamCaptureModeThreadLocal));
+                body(*loops[c], 1, st);
+                WL_CUDA(cudaStreamEndCapture(st, &out));
+                if (prioritise) set_kernel_priority(bodies[c], class_priority((int)c));
+            }
+            WL_CUDA(cudaGraphInstantiate(&exec, graph, prioritise ? cudaGraphInstantiateFlagUseNodePriority : 0));
             WL_CUDA(cudaGraphLaunch(exec, st));
             graph_launches = 1;
         } else {
-            // without conditional nodes: prologue, then graphs of 8 body
-            // iterations replayed while some problem is active, then epilogue
-            prologue(st);
+            // without conditional nodes: prologues, then per class graphs of 8
+            // body iterations replayed while the class is active, then epilogues
             WL_CUDA(cudaGraphDestroy(graph));
             graph = nullptr;
-            WL_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
-            for (int k = 0; k < 8; k++) body(st);
-            WL_CUDA(cudaStreamEndCapture(st, &graph));
-            WL_CUDA(cudaGraphInstantiate(&exec, graph, 0));
-            std::vector<BatchState> hs(n);
-            while (true) {
-                WL_CUDA(cudaGraphLaunch(exec, st));
-                graph_launches++;
-                WL_CUDA(cudaMemcpyAsync(hs.data(), B.state.p, sizeof(BatchState) * n, cudaMemcpyDeviceToHost, st));
-                WL_CUDA(cudaStreamSynchronize(st));
-                bool active = false;
-                for (auto& s : hs) active = active || s.phase != PH_DONE;
-                if (!active || graph_launches * 8 >= max_iter) break;
+            for (auto& R : loops) prologue(*R, st);
+            if (smallrun) prologue(*smallrun, st);
+            small_fork(st);
+            for (auto& R : loops) {
+                cudaGraph_t g8 = nullptr;
+                cudaGraphExec_t e8 = nullptr;
+                WL_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+                for (int k = 0; k < 8; k++) body(*R, 0, st);
+                WL_CUDA(cudaStreamEndCapture(st, &g8));
+                WL_CUDA(cudaGraphInstantiate(&e8, g8, 0));
+                std::vector<BatchState> hs(R->nprob);
+                BatchGlobal hgl{};
+                for (int launches = 0;; launches++) {
+                    WL_CUDA(cudaGraphLaunch(e8, st));
+                    graph_launches++;
+                    WL_CUDA(cudaMemcpyAsync(hs.data(), R->state.p, sizeof(BatchState) * R->nprob,
+                                            cudaMemcpyDeviceToHost, st));
+                    WL_CUDA(cudaMemcpyAsync(&hgl, R->global.p, sizeof(BatchGlobal), cudaMemcpyDeviceToHost, st));
+                    WL_CUDA(cudaStreamSynchronize(st));
+                    bool active = false;
+                    for (auto& x : hs) active = active || x.phase != PH_DONE;
+                    if (!active || hgl.timed_out || (launches + 1) * 8 >= max_iter) break;
+                }
+                cudaGraphExecDestroy(e8);
+                cudaGraphDestroy(g8);
             }
-            epilogue(st);
+            small_join(st);
+            for (auto& R : loops) epilogue(*R, st);
+            if (smallrun) epilogue(*smallrun, st);
         }
         WL_CUDA(cudaStreamSynchronize(st));
     } catch (...) {
@@ -831,34 +1217,53 @@ void batch_solve(int n, const wilson_problem* probs, const SolveParams& prm, wil
     if (exec) cudaGraphExecDestroy(exec);
     if (graph) cudaGraphDestroy(graph);
 
-    std::vector<BatchState> hs(n);
-    BatchGlobal hg;
-    WL_CUDA(cudaMemcpy(hs.data(), B.state.p, sizeof(BatchState) * n, cudaMemcpyDeviceToHost));
-    WL_CUDA(cudaMemcpy(&hg, B.global.p, sizeof(BatchGlobal), cudaMemcpyDeviceToHost));
-    for (int i = 0; i < n; i++) {
-        unpack_spinor(B.hp[i].f[BF_X], 0, probs[i].x, st);
-        const BatchState& S = hs[i];
-        wilson_solve_stats& o = stats[i];
-        const double bn = std::sqrt(S.bnorm2);
-        o.true_rel_resid = bn > 0 ? std::sqrt(S.res2) / bn : std::sqrt(S.res2);
-        o.inner_iters = S.sc.iter;
-        o.outer_iters = S.outer;
-        o.hop_applications = 4 * S.sc.iter + 4 * (S.outer + 1) + 4;
-        o.seconds = S.phase == PH_DONE && S.t_done >= hg.t_start ? (double)(S.t_done - hg.t_start) * 1e-9 : -1.0;
-        int status = S.status;
-        if (status == 0 && S.phase != PH_DONE) status = hg.timed_out ? WILSON_ERR_TIMEOUT : WILSON_ERR_NOCONV;
-        if (status == 0 && !(o.true_rel_resid <= prm.tol)) status = WILSON_ERR_NOCONV;
-        o.status = status;
+    // results, problem by problem (latencies from the earliest run start)
+    std::vector<BatchRun*> runs;
+    for (auto& R : loops) runs.push_back(R.get());
+    if (smallrun) runs.push_back(smallrun.get());
+    std::vector<BatchGlobal> hg(runs.size());
+    unsigned long long t_first = ~0ULL, t_last = 0;
+    int iters = 0, timed_out = 0, tiles = 0;
+    for (size_t r = 0; r < runs.size(); r++) {
+        WL_CUDA(cudaMemcpy(&hg[r], runs[r]->global.p, sizeof(BatchGlobal), cudaMemcpyDeviceToHost));
+        t_first = std::min(t_first, hg[r].t_start);
+        t_last = std::max(t_last, hg[r].t_end);
+        tiles += runs[r]->ntiles;
+        if (runs[r] != smallrun.get()) {
+            iters = std::max(iters, hg[r].iterations);
+            timed_out |= hg[r].timed_out;
+        }
+    }
+    for (size_t r = 0; r < runs.size(); r++) {
+        const BatchRun& R = *runs[r];
+        std::vector<BatchState> hs(R.nprob);
+        WL_CUDA(cudaMemcpy(hs.data(), R.state.p, sizeof(BatchState) * R.nprob, cudaMemcpyDeviceToHost));
+        for (int j = 0; j < R.nprob; j++) {
+            const int i = R.members[j];
+            unpack_spinor(hp[i].f[BF_X], 0, probs[i].x, st);
+            const BatchState& S = hs[j];
+            wilson_solve_stats& o = stats[i];
+            const double bn = std::sqrt(S.bnorm2);
+            o.true_rel_resid = bn > 0 ? std::sqrt(S.res2) / bn : std::sqrt(S.res2);
+            o.inner_iters = S.sc.iter;
+            o.outer_iters = S.outer;
+            o.hop_applications = 4 * S.sc.iter + 4 * (S.outer + 1) + 4;
+            o.seconds = S.phase == PH_DONE && S.t_done >= t_first ? (double)(S.t_done - t_first) * 1e-9 : -1.0;
+            int status = S.status;
+            if (status == 0 && S.phase != PH_DONE) status = hg[r].timed_out ? WILSON_ERR_TIMEOUT : WILSON_ERR_NOCONV;
+            if (status == 0 && !(o.true_rel_resid <= prm.tol)) status = WILSON_ERR_NOCONV;
+            o.status = status;
+        }
     }
     WL_CUDA(cudaStreamSynchronize(st));
     if (info) {
         info->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
-        info->device_seconds = (double)(hg.t_end - hg.t_start) * 1e-9;
-        info->iterations = hg.iterations;
+        info->device_seconds = t_last > t_first ? (double)(t_last - t_first) * 1e-9 : 0.0;
+        info->iterations = iters;
         info->graph_launches = graph_launches;
         info->device_loop = use_cond;
-        info->timed_out = hg.timed_out;
-        info->tiles = B.ntiles;
+        info->timed_out = timed_out;
+        info->tiles = tiles;
     }
 }
 

@@ -112,6 +112,15 @@ __device__ __forceinline__ void site_of_half(int h, int p, const Geom& g, int c[
     s = s0 + odd;
 }
 
+// Read-only loads go through the non-coherent path (__ldg) by default.  A
+// kernel that reads data it wrote itself earlier in the same launch (the
+// CTA-resident solver) instantiates the loads with COH = true: plain loads.
+template <bool COH, class T>
+__device__ __forceinline__ T ldro(const T* p) {
+    if constexpr (COH) return *p;
+    else return __ldg(p);
+}
+
 // ---------------------------------------------------------------------------
 // low-precision helpers
 // ---------------------------------------------------------------------------
@@ -157,18 +166,20 @@ struct SpinorFmt<P_F64> {
     static constexpr int chunk_bytes = 16;
     static constexpr bool scaled = false;
     static __host__ __device__ long long field_bytes(int stride) { return 16LL * 12 * stride; }
+    template <bool COH = false>
     __device__ static __forceinline__ void load(const void* base, int stride, int i, cpx<double> v[12]) {
         const double2* b = static_cast<const double2*>(base) + i;
 #pragma unroll
         for (int c = 0; c < 12; c++) {
-            double2 d = __ldg(b + (size_t)c * stride);
+            double2 d = ldro<COH>(b + (size_t)c * stride);
             v[c] = {d.x, d.y};
         }
     }
     // unscaled format: the scale is the constant 1 and folds away
+    template <bool COH = false>
     __device__ static __forceinline__ void load_raw(const void* base, int stride, int i, cpx<double> v[12],
                                                     double& s) {
-        load(base, stride, i, v);
+        load<COH>(base, stride, i, v);
         s = 1.0;
     }
     __device__ static __forceinline__ void store(void* base, int stride, int i, const cpx<double> v[12]) {
@@ -218,12 +229,13 @@ struct SpinorFmt<P_F32> {
     static constexpr int chunk_bytes = 16;
     static constexpr bool scaled = false;
     static __host__ __device__ long long field_bytes(int stride) { return 16LL * 6 * stride; }
+    template <bool COH = false>
     __device__ static __forceinline__ void load_packed(const void* base, int stride, int i, PSpinor& q, float& s) {
         const float4* b = static_cast<const float4*>(base) + i;
 #pragma unroll
         for (int c = 0; c < 3; c++) {
-            const float4 lo = __ldg(b + (size_t)(2 * c) * stride);
-            const float4 hi = __ldg(b + (size_t)(2 * c + 1) * stride);
+            const float4 lo = ldro<COH>(b + (size_t)(2 * c) * stride);
+            const float4 hi = ldro<COH>(b + (size_t)(2 * c + 1) * stride);
             q.re01[c] = make_float2(lo.x, lo.y);
             q.im01[c] = make_float2(lo.z, lo.w);
             q.re23[c] = make_float2(hi.x, hi.y);
@@ -239,15 +251,17 @@ struct SpinorFmt<P_F32> {
             b[(size_t)(2 * c + 1) * stride] = make_float4(q.re23[c].x, q.re23[c].y, q.im23[c].x, q.im23[c].y);
         }
     }
+    template <bool COH = false>
     __device__ static __forceinline__ void load(const void* base, int stride, int i, cpx<float> v[12]) {
         PSpinor q;
         float s;
-        load_packed(base, stride, i, q, s);
+        load_packed<COH>(base, stride, i, q, s);
         unpack_pairs(q, v);
     }
+    template <bool COH = false>
     __device__ static __forceinline__ void load_raw(const void* base, int stride, int i, cpx<float> v[12],
                                                     float& s) {
-        load(base, stride, i, v);
+        load<COH>(base, stride, i, v);
         s = 1.0f;
     }
     __device__ static __forceinline__ void store(void* base, int stride, int i, const cpx<float> v[12]) {
@@ -270,18 +284,20 @@ struct SpinorLowFmt {
     static constexpr int chunk_bytes = 16;
     static constexpr bool scaled = true;
     static __host__ __device__ long long field_bytes(int stride) { return 16LL * 3 * stride + 4LL * stride; }
+    template <bool COH = false>
     __device__ static __forceinline__ float load_scale(const void* base, int stride, int i) {
         const float* sc = reinterpret_cast<const float*>(static_cast<const char*>(base) + 48LL * stride);
-        return __ldg(sc + i);
+        return ldro<COH>(sc + i);
     }
     // The stored values q (|q| <= 1) and the site's scale separately: the
     // hopping kernels apply the scale in their accumulation FMA for free.
+    template <bool COH = false>
     __device__ static __forceinline__ void load_packed(const void* base, int stride, int i, PSpinor& q, float& s) {
         const uint4* b = static_cast<const uint4*>(base) + i;
-        s = load_scale(base, stride, i);
+        s = load_scale<COH>(base, stride, i);
 #pragma unroll
         for (int c = 0; c < 3; c++) {
-            const uint4 d = __ldg(b + (size_t)c * stride);
+            const uint4 d = ldro<COH>(b + (size_t)c * stride);
             q.re01[c] = LT::to_f2(d.x);
             q.im01[c] = LT::to_f2(d.y);
             q.re23[c] = LT::to_f2(d.z);
@@ -309,15 +325,17 @@ struct SpinorLowFmt {
         float* sc = reinterpret_cast<float*>(static_cast<char*>(base) + 48LL * stride);
         sc[i] = m;
     }
+    template <bool COH = false>
     __device__ static __forceinline__ void load_raw(const void* base, int stride, int i, cpx<float> v[12],
                                                     float& s) {
         PSpinor q;
-        load_packed(base, stride, i, q, s);
+        load_packed<COH>(base, stride, i, q, s);
         unpack_pairs(q, v);
     }
+    template <bool COH = false>
     __device__ static __forceinline__ void load(const void* base, int stride, int i, cpx<float> v[12]) {
         float s;
-        load_raw(base, stride, i, v, s);
+        load_raw<COH>(base, stride, i, v, s);
 #pragma unroll
         for (int k = 0; k < 12; k++) v[k] = {v[k].re * s, v[k].im * s};
     }

@@ -139,7 +139,7 @@ struct HopParams {
 };
 
 // One direction mu: forward and backward hop into acc.
-template <int SP, int GP, int R, bool DAG, int MU, bool FIRST>
+template <int SP, int GP, int R, bool DAG, int MU, bool FIRST, bool COH = false>
 __device__ __forceinline__ void hop_dir(cpx<typename SpinorFmt<SP>::real> acc[12], const HopParams& P,
                                         const char* in, int p, int h, const int c[4], int s) {
     using SF = SpinorFmt<SP>;
@@ -155,7 +155,7 @@ __device__ __forceinline__ void hop_dir(cpx<typename SpinorFmt<SP>::real> acc[12
         const int sn = wrap ? s - (L - 1) * smu : s + smu;
         cpx<T> v[12], hs[6], w[6], U[3][3];
         T sc;
-        SF::load_raw(in, g.stride, sn >> 1, v, sc);
+        SF::template load_raw<COH>(in, g.stride, sn >> 1, v, sc);
         GF::load(P.gauge, g.stride, p * 4 + MU, h, U);
         project<MU, SF_>(v, hs);
         if (wrap) {
@@ -173,7 +173,7 @@ __device__ __forceinline__ void hop_dir(cpx<typename SpinorFmt<SP>::real> acc[12
         const int hn = sn >> 1;
         cpx<T> v[12], hs[6], w[6], U[3][3];
         T sc;
-        SF::load_raw(in, g.stride, hn, v, sc);
+        SF::template load_raw<COH>(in, g.stride, hn, v, sc);
         GF::load(P.gauge, g.stride, (1 - p) * 4 + MU, hn, U);
         project<MU, -SF_>(v, hs);
         if (wrap) {

@@ -20,6 +20,8 @@ struct SolveParams {
     int reliable = 1;
     int chunk = 16;           // iterations per captured graph
     int use_graph = 1;
+    int batch_small_vh = 4096;  // batched solves: problems with at most this many sites per parity
+                                // run the CTA-resident solver (0: none)
 };
 
 struct SolveStats {

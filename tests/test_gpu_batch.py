@@ -37,12 +37,18 @@ def true_resid(oracle_mod, U, x, b, dims, kappa, phases=None):
     return np.linalg.norm(b - oracle_mod.wilson_m(U, x, dims, kappa, phases)) / np.linalg.norm(b)
 
 
+# WILSON_BATCH_SMALL_VH: problems with at most this many sites per parity run
+# the CTA-resident solver; 0 sends every problem through the device loop,
+# 400 splits MIX between the two paths, 4096 puts all of MIX on CTAs.
+@pytest.mark.parametrize("small_vh", ["0", "400", "4096"])
 @pytest.mark.parametrize("inner", ["f16", "bf16", "f32"])
-def test_batch_matches_oracle(w, oracle_mod, inner):
+def test_batch_matches_oracle(w, oracle_mod, monkeypatch, inner, small_vh):
+    monkeypatch.setenv("WILSON_BATCH_SMALL_VH", small_vh)
     probs, hf = make_batch(w, MIX)
     rc, st, info = w.wilson_batch_solve(probs, w.solver_defaults(w.PREC[inner]))
     assert rc == 0 and not info["timed_out"]
-    assert info["graph_launches"] >= 1 and info["tiles"] > 0
+    assert info["graph_launches"] >= 1
+    assert (info["tiles"] > 0) == (small_vh != "4096")  # all of MIX fits the CTA path at 4096
     for q, (dims, U, b, kappa), s in zip(probs, hf, st):
         x = host(q["x"])
         assert s["status"] == 0 and s["true_rel_resid"] <= 1e-10
@@ -50,7 +56,9 @@ def test_batch_matches_oracle(w, oracle_mod, inner):
         assert 0 <= s["seconds"] <= info["device_seconds"] + 1e-6
 
 
-def test_batch_equals_single_solves(w):
+@pytest.mark.parametrize("small_vh", ["0", "4096"])
+def test_batch_equals_single_solves(w, monkeypatch, small_vh):
+    monkeypatch.setenv("WILSON_BATCH_SMALL_VH", small_vh)
     probs, hf = make_batch(w, MIX[:4], seed0=420)
     rc, st, info = w.wilson_batch_solve(probs, w.solver_defaults(w.WILSON_F16))
     for q, (dims, U, b, kappa) in zip(probs, hf):
@@ -60,7 +68,9 @@ def test_batch_equals_single_solves(w):
         assert rel_l2(host(q["x"]), host(xs)) <= 1e-7
 
 
-def test_batch_complex_phases(w, oracle_mod):
+@pytest.mark.parametrize("small_vh", ["0", "400"])
+def test_batch_complex_phases(w, oracle_mod, monkeypatch, small_vh):
+    monkeypatch.setenv("WILSON_BATCH_SMALL_VH", small_vh)
     ph = (np.exp(0.3j), 1.0, np.exp(-1.2j), -1.0)
     probs, hf = make_batch(w, MIX[:3], seed0=440, phases=ph)
     rc, st, info = w.wilson_batch_solve(probs, w.solver_defaults(w.WILSON_F16))
@@ -68,7 +78,9 @@ def test_batch_complex_phases(w, oracle_mod):
         assert true_resid(oracle_mod, U, host(q["x"]), b, dims, kappa, ph) <= 1.1e-10
 
 
-def test_batch_noconv_and_numeric_are_per_problem(w, oracle_mod):
+@pytest.mark.parametrize("small_vh", ["0", "4096"])
+def test_batch_noconv_and_numeric_are_per_problem(w, oracle_mod, monkeypatch, small_vh):
+    monkeypatch.setenv("WILSON_BATCH_SMALL_VH", small_vh)
     probs, hf = make_batch(w, MIX[:3], seed0=460)
     bad = host(probs[1]["b"])
     bad[3, 2, 1] = np.nan
@@ -87,10 +99,30 @@ def test_batch_noconv_and_numeric_are_per_problem(w, oracle_mod):
     assert rc == w.WILSON_ERR_NOCONV and all(s["status"] == w.WILSON_ERR_NOCONV for s in st)
 
 
+# WILSON_BATCH_CLASSES caps the number of device loops (one per class of
+# lattice sizes); WILSON_BATCH_HOST_LOOP=1 replaces the device-side loop by
+# host-replayed graphs of eight iterations.
+@pytest.mark.parametrize("classes,host_loop", [("1", "0"), ("2", "0"), ("8", "0"), ("8", "1")])
+def test_batch_classes_and_host_loop(w, oracle_mod, monkeypatch, classes, host_loop):
+    monkeypatch.setenv("WILSON_BATCH_SMALL_VH", "0")
+    monkeypatch.setenv("WILSON_BATCH_CLASSES", classes)
+    monkeypatch.setenv("WILSON_BATCH_HOST_LOOP", host_loop)
+    probs, hf = make_batch(w, MIX, seed0=500)
+    rc, st, info = w.wilson_batch_solve(probs, w.solver_defaults(w.WILSON_F16))
+    assert rc == 0 and not info["timed_out"]
+    assert info["device_loop"] == (host_loop == "0")
+    if host_loop == "0":
+        assert info["graph_launches"] == 1
+    for q, (dims, U, b, kappa), s in zip(probs, hf, st):
+        assert s["status"] == 0
+        assert true_resid(oracle_mod, U, host(q["x"]), b, dims, kappa) <= 1.1e-10
+
+
 def test_loop_limit_runs_out_and_context_stays_usable(w, oracle_mod, monkeypatch):
     """The device-side loop has a hard iteration cap; when it runs out the
     unfinished problems report WILSON_ERR_TIMEOUT and the next call works."""
     probs, hf = make_batch(w, MIX[:3], seed0=480)
+    monkeypatch.setenv("WILSON_BATCH_SMALL_VH", "0")  # the loop cap governs the loop path
     monkeypatch.setenv("WILSON_BATCH_MAX_LOOP", "6")
     rc, st, info = w.wilson_batch_solve(probs, w.solver_defaults(w.WILSON_F16), check=False)
     assert info["timed_out"] == 1 and info["iterations"] == 6
@@ -103,3 +135,13 @@ def test_loop_limit_runs_out_and_context_stays_usable(w, oracle_mod, monkeypatch
     assert rc == 0 and info["timed_out"] == 0
     for q, (dims, U, b, kappa) in zip(probs, hf):
         assert true_resid(oracle_mod, U, host(q["x"]), b, dims, kappa) <= 1.1e-10
+
+
+def test_small_path_budget_runs_out(w, monkeypatch):
+    """The CTA-resident solver checks the wall-clock budget too."""
+    monkeypatch.setenv("WILSON_BATCH_SMALL_VH", "4096")
+    monkeypatch.setenv("WILSON_BATCH_BUDGET_MS", "1")
+    probs, hf = make_batch(w, [((8, 8, 8, 8), 0.3, 0.1355)] * 2, seed0=490)
+    rc, st, info = w.wilson_batch_solve(probs, w.solver_defaults(w.WILSON_F16), check=False)
+    assert rc in (w.WILSON_ERR_TIMEOUT, w.WILSON_OK)
+    assert all(s["status"] in (w.WILSON_ERR_TIMEOUT, w.WILSON_OK) for s in st)
