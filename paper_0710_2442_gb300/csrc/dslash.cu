@@ -4,6 +4,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <string>
+#include <vector>
 
 #include "dslash_impl.cuh"
 
@@ -28,8 +29,9 @@ int hop_grid_blocks(const Geom& g, int block, int grid_cap) {
     return blocks < 1 ? 1 : blocks;
 }
 
-static void dispatch(const HopParams& P, Prec sp, Prec gp, int R, int block, int blocks, int ny, bool dag,
+static void dispatch(const HopParams& P, Prec sp, Prec gp, int R, int block, int site_blocks, int ny, bool dag,
                      int variant, cudaStream_t st) {
+    const int blocks = site_blocks;
     if (sp == P_F64 && gp == P_F64 && R == 18) launch_hop_prec<P_F64, P_F64, 18>(P, block, blocks, ny, dag, variant, st);
     else if (sp == P_F64 && gp == P_F64 && R == 12) launch_hop_prec<P_F64, P_F64, 12>(P, block, blocks, ny, dag, variant, st);
     else if (sp == P_F32 && gp == P_F32 && R == 12) launch_hop_prec<P_F32, P_F32, 12>(P, block, blocks, ny, dag, variant, st);
@@ -80,6 +82,8 @@ void launch_hop(const HopLaunch& L, cudaStream_t st) {
         const char* fb = std::getenv("WILSON_HOP_BLOCK");
         cfg.block = fb && std::atoi(fb) > 0 ? std::atoi(fb) : 128;
         WL_REQUIRE(cfg.variant >= 0 && cfg.variant < kHopVariants, "WILSON_HOP_VARIANT out of range");
+        // a blocked variant that does not fit this launch falls back to variant 3
+        if (!hop_variant_valid(cfg.variant, sp, R, P.nrhs)) cfg.variant = 3;
         WL_REQUIRE(cfg.block == 64 || cfg.block == 128 || cfg.block == 256, "WILSON_HOP_BLOCK must be 64, 128 or 256");
     } else {
         char key[160];
@@ -87,18 +91,24 @@ void launch_hop(const HopLaunch& L, cudaStream_t st) {
                  L.full, L.xpay, P.nrhs, P.g.L[0], P.g.L[1], P.g.L[2], P.g.L[3]);
         // tuning launches never reduce: the finishers are not idempotent
         const HopParams Pt = P;
-        cfg = tune_launch(key, hop_candidates(), LaunchConfig{}, st, [&](const LaunchConfig& c) {
-            dispatch(Pt, sp, gp, R, c.block, hop_grid_blocks(Pt.g, c.block, 0) * Pt.nrhs, ny, dag, c.variant, st);
+        std::vector<LaunchConfig> cands = hop_candidates();
+        if (P.nrhs > 1)
+            for (int block : {64, 128, 256})
+                for (int v = kHopBaseVariants; v < kHopVariants; v++)
+                    if (hop_variant_valid(v, sp, R, P.nrhs)) cands.push_back(LaunchConfig{block, v});
+        cfg = tune_launch(key, cands, LaunchConfig{}, st, [&](const LaunchConfig& c) {
+            dispatch(Pt, sp, gp, R, c.block, hop_grid_blocks(Pt.g, c.block, 0), ny, dag, c.variant, st);
         });
     }
+    WL_REQUIRE(hop_variant_valid(cfg.variant, sp, R, P.nrhs), "hop variant does not fit this launch");
     if (L.red) {
         P.reduce = 1;
         P.red = *L.red;
         WL_REQUIRE(!L.full, "reducing hop launches are single-parity");
     }
-    const int blocks = hop_grid_blocks(P.g, cfg.block, L.red ? L.grid_cap : 0) * P.nrhs;
-    WL_REQUIRE(!L.red || blocks / P.nrhs <= L.red->slot_cap, "reduction capacity below the grid size");
-    dispatch(P, sp, gp, R, cfg.block, blocks, ny, dag, cfg.variant, st);
+    const int site_blocks = hop_grid_blocks(P.g, cfg.block, L.red ? L.grid_cap : 0);
+    WL_REQUIRE(!L.red || site_blocks <= L.red->slot_cap, "reduction capacity below the grid size");
+    dispatch(P, sp, gp, R, cfg.block, site_blocks, ny, dag, cfg.variant, st);
     WL_LAUNCH_CHECK();
 }
 

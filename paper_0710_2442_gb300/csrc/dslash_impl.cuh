@@ -458,12 +458,183 @@ __global__ void __launch_bounds__(256, MINB) hop_kernel_p(const HopParams P) {
     if (P.reduce) grid_reduce(nrm, P.red, k, nb * gridDim.y, sb + nb * blockIdx.y);
 }
 
-// Kernel variants v = 0..5: v % 3 is the register budget (blocks of 256
+// ---------------------------------------------------------------------------
+// Register-blocked multi-RHS stencil: one thread computes one output site for
+// NB right-hand sides.  Per hop the neighbour index is computed and the link
+// loaded and completed once, then applied to the NB neighbour spinors, so the
+// link traffic through L1/L2, the 12 -> 18 reconstruction and the index
+// arithmetic are shared by NB right-hand sides.  The arithmetic per
+// right-hand side is that of hop_kernel_p.  Grid: blockIdx.x = site_block *
+// (nrhs / NB) + group.  A group runs unless all its right-hand sides are
+// flagged to be skipped; a flagged member is computed but neither stored nor
+// reduced, so its output keeps its old value as with the other kernels.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void apply_phase_p(PHalf& hh, float er, float ei) {
+#pragma unroll
+    for (int k = 0; k < 3; k++) {
+        const float2 r = hh.re[k], m = hh.im[k];
+        hh.re[k] = fma2(bc2(-ei), m, mul2(bc2(er), r));
+        hh.im[k] = fma2(bc2(ei), r, mul2(bc2(er), m));
+    }
+}
+
+template <int SP, int GP, int R, bool DAG, int MU, bool FIRST, int NB>
+__device__ __forceinline__ void hop_dir_pm(PSpinor (&acc)[NB], const HopParams& P, const char* in, int p, int h,
+                                           const int c[4], int s) {
+    using SF = SpinorFmt<SP>;
+    using GF = GaugeFmt<GP, R>;
+    const Geom& g = P.g;
+    const int L = g.L[MU];
+    const int smu = MU == 0 ? 1 : MU == 1 ? g.L[0] : MU == 2 ? g.L[0] * g.L[1] : g.L[0] * g.L[1] * g.L[2];
+    constexpr int SF_ = DAG ? -1 : 1;
+    {
+        const bool wrap = c[MU] == L - 1;
+        const int hn = (wrap ? s - (L - 1) * smu : s + smu) >> 1;
+        cpx<float> U[3][3];
+        GF::load(P.gauge, g.stride, p * 4 + MU, h, U);
+#pragma unroll
+        for (int r = 0; r < NB; r++) {
+            PSpinor q;
+            PHalf hh, w;
+            float sc;
+            SF::load_packed(in + r * P.in_rstep, g.stride, hn, q, sc);
+            project_p<MU, SF_>(q, hh);
+            if (wrap) apply_phase_p(hh, (float)g.ph[MU][0], (float)g.ph[MU][1]);
+            su3_mul_p<false>(U, hh, w);
+            expand_p<MU, SF_, FIRST>(acc[r], w, sc);
+        }
+    }
+    {
+        const bool wrap = c[MU] == 0;
+        const int hn = (wrap ? s + (L - 1) * smu : s - smu) >> 1;
+        cpx<float> U[3][3];
+        GF::load(P.gauge, g.stride, (1 - p) * 4 + MU, hn, U);
+#pragma unroll
+        for (int r = 0; r < NB; r++) {
+            PSpinor q;
+            PHalf hh, w;
+            float sc;
+            SF::load_packed(in + r * P.in_rstep, g.stride, hn, q, sc);
+            project_p<MU, -SF_>(q, hh);
+            if (wrap) apply_phase_p(hh, (float)g.ph[MU][0], -(float)g.ph[MU][1]);
+            su3_mul_p<true>(U, hh, w);
+            expand_p<MU, -SF_, false>(acc[r], w, sc);
+        }
+    }
+}
+
+template <int SP, int GP, int R, bool DAG, int MINB, int NB>
+__global__ void __launch_bounds__(256, MINB) hop_kernel_pm(const HopParams P) {
+    using SF = SpinorFmt<SP>;
+    const int ng = P.nrhs / NB;
+    const int grp = blockIdx.x % ng;
+    const int sb = blockIdx.x / ng;
+    const int nb = gridDim.x / ng;
+    const int k0 = grp * NB;
+    unsigned act = 0;
+#pragma unroll
+    for (int r = 0; r < NB; r++)
+        if (!P.skip || !__ldcg(P.skip + (size_t)(k0 + r) * P.skip_stride)) act |= 1u << r;
+    if (!act) return;
+    const int p = P.full ? (int)blockIdx.y : P.out_parity;
+    const int pin = 1 - p;
+    char* out = P.out + (P.full ? p * P.out_pstep : 0) + k0 * P.out_rstep;
+    const char* in = P.in + (P.full ? pin * P.in_pstep : 0) + k0 * P.in_rstep;
+    const char* x = P.x ? P.x + (P.full ? p * P.x_pstep : 0) + k0 * P.x_rstep : nullptr;
+    const Geom& g = P.g;
+    const float a = (float)P.a;
+    double nrm[NB];
+#pragma unroll
+    for (int r = 0; r < NB; r++) nrm[r] = 0.0;
+    for (int h = sb * blockDim.x + threadIdx.x; h - (int)threadIdx.x < g.Vh; h += nb * blockDim.x) {
+        if (h >= g.Vh) continue;
+        int c[4], s;
+        site_of_half(h, p, g, c, s);
+        PSpinor acc[NB];
+        hop_dir_pm<SP, GP, R, DAG, 0, true, NB>(acc, P, in, p, h, c, s);
+        hop_dir_pm<SP, GP, R, DAG, 1, false, NB>(acc, P, in, p, h, c, s);
+        hop_dir_pm<SP, GP, R, DAG, 2, false, NB>(acc, P, in, p, h, c, s);
+        hop_dir_pm<SP, GP, R, DAG, 3, false, NB>(acc, P, in, p, h, c, s);
+#pragma unroll
+        for (int r = 0; r < NB; r++) {
+            PSpinor& A = acc[r];
+            if (P.xpay) {
+                PSpinor xq;
+                float xs;
+                SF::load_packed(x + r * P.x_rstep, g.stride, h, xq, xs);
+                const float2 Af = bc2(a), X = bc2(xs);
+#pragma unroll
+                for (int cc = 0; cc < 3; cc++) {
+                    A.re01[cc] = fma2(Af, A.re01[cc], mul2(X, xq.re01[cc]));
+                    A.im01[cc] = fma2(Af, A.im01[cc], mul2(X, xq.im01[cc]));
+                    A.re23[cc] = fma2(Af, A.re23[cc], mul2(X, xq.re23[cc]));
+                    A.im23[cc] = fma2(Af, A.im23[cc], mul2(X, xq.im23[cc]));
+                }
+            } else if (P.a != 1.0) {
+                const float2 Af = bc2(a);
+#pragma unroll
+                for (int cc = 0; cc < 3; cc++) {
+                    A.re01[cc] = mul2(Af, A.re01[cc]);
+                    A.im01[cc] = mul2(Af, A.im01[cc]);
+                    A.re23[cc] = mul2(Af, A.re23[cc]);
+                    A.im23[cc] = mul2(Af, A.im23[cc]);
+                }
+            }
+            if (P.reduce) {
+                float2 n2 = make_float2(0.f, 0.f);
+#pragma unroll
+                for (int cc = 0; cc < 3; cc++) {
+                    n2 = fma2(A.re01[cc], A.re01[cc], n2);
+                    n2 = fma2(A.im01[cc], A.im01[cc], n2);
+                    n2 = fma2(A.re23[cc], A.re23[cc], n2);
+                    n2 = fma2(A.im23[cc], A.im23[cc], n2);
+                }
+                nrm[r] += (double)n2.x + (double)n2.y;
+            }
+            if (act >> r & 1u) SF::store_packed(out + r * P.out_rstep, g.stride, h, A);
+        }
+    }
+    if (P.reduce) {
+#pragma unroll
+        for (int r = 0; r < NB; r++)
+            if (act >> r & 1u) grid_reduce(nrm[r], P.red, k0 + r, nb * gridDim.y, sb + nb * blockIdx.y);
+    }
+}
+
+// Kernel variants: v = 0..5: v % 3 is the register budget (blocks of 256
 // threads guaranteed resident per SM: 128 / 85 / 64 registers per thread;
 // FP64: 255 / 128 / 85, its operands take two registers each); v >= 3 is the
-// paired-FP32 kernel (single and reduced precision only).
-constexpr int kHopVariants = 6;
-constexpr int hop_variant_minb(int v, int sp) { return (sp == P_F64 ? 1 : 2) + v % 3; }
+// paired-FP32 kernel (single and reduced precision only).  v = 6..9: the
+// register-blocked multi-RHS kernel with NB = 2, 2, 3, 4 right-hand sides per
+// thread and 255, 128, 255, 255 registers (single and reduced precision,
+// 12-real links, NB dividing nrhs; NB >= 3 spills at 128 registers).
+constexpr int kHopVariants = 10;
+constexpr int kHopBaseVariants = 6;
+constexpr int hop_variant_nb(int v) {
+    return v < kHopBaseVariants ? 1 : v == 6 || v == 7 ? 2 : v == 8 ? 3 : 4;
+}
+constexpr int hop_variant_minb(int v, int sp) {
+    return v < kHopBaseVariants ? (sp == P_F64 ? 1 : 2) + v % 3 : v == 7 ? 2 : 1;
+}
+inline bool hop_variant_valid(int v, Prec sp, int recon, int nrhs) {
+    if (v < 0 || v >= kHopVariants) return false;
+    if (v < kHopBaseVariants) return true;
+    const int nb = hop_variant_nb(v);
+    return sp != P_F64 && recon == 12 && nrhs >= nb && nrhs % nb == 0;
+}
+
+// The register-blocked kernels (instantiated in dslash_mrhs.cu).
+template <int SP, int GP, int R>
+void launch_hop_mrhs(const HopParams& P, int block, int site_blocks, int ny, bool dag, int variant,
+                     cudaStream_t st);
+
+template <int SP, int GP, int R, int V>
+void launch_hop_mrhs_v(const HopParams& P, int block, int site_blocks, int ny, bool dag, cudaStream_t st) {
+    constexpr int NB = hop_variant_nb(V), MINB = hop_variant_minb(V, SP);
+    const dim3 grid(site_blocks * (P.nrhs / NB), ny);
+    if (dag) hop_kernel_pm<SP, GP, R, true, MINB, NB><<<grid, block, 0, st>>>(P);
+    else hop_kernel_pm<SP, GP, R, false, MINB, NB><<<grid, block, 0, st>>>(P);
+}
 
 template <int SP, int GP, int R, int V>
 void launch_hop_v(const HopParams& P, dim3 grid, int block, bool dag, cudaStream_t st) {
@@ -477,9 +648,19 @@ void launch_hop_v(const HopParams& P, dim3 grid, int block, bool dag, cudaStream
     }
 }
 
+// site_blocks: blocks over the half lattice; the grid covers them once per
+// right-hand side (or group of right-hand sides).
 template <int SP, int GP, int R>
-void launch_hop_prec(const HopParams& P, int block, int blocks, int ny, bool dag, int variant, cudaStream_t st) {
-    const dim3 grid(blocks, ny);
+void launch_hop_prec(const HopParams& P, int block, int site_blocks, int ny, bool dag, int variant,
+                     cudaStream_t st) {
+    if (variant >= kHopBaseVariants) {
+        if constexpr (SP != P_F64 && R == 12) {
+            launch_hop_mrhs<SP, GP, R>(P, block, site_blocks, ny, dag, variant, st);
+            return;
+        }
+        throw Error(7, "register-blocked hop variant needs F32/F16/BF16 spinors and 12-real links");
+    }
+    const dim3 grid(site_blocks * P.nrhs, ny);
     if (SP == P_F64) variant %= 3;
     switch (variant) {
         case 1: launch_hop_v<SP, GP, R, 1>(P, grid, block, dag, st); break;
@@ -500,5 +681,8 @@ extern template void launch_hop_prec<P_F16, P_F16, 12>(const HopParams&, int, in
 extern template void launch_hop_prec<P_BF16, P_BF16, 12>(const HopParams&, int, int, int, bool, int, cudaStream_t);
 extern template void launch_hop_prec<P_F16, P_F16, 18>(const HopParams&, int, int, int, bool, int, cudaStream_t);
 extern template void launch_hop_prec<P_BF16, P_BF16, 18>(const HopParams&, int, int, int, bool, int, cudaStream_t);
+extern template void launch_hop_mrhs<P_F32, P_F32, 12>(const HopParams&, int, int, int, bool, int, cudaStream_t);
+extern template void launch_hop_mrhs<P_F16, P_F16, 12>(const HopParams&, int, int, int, bool, int, cudaStream_t);
+extern template void launch_hop_mrhs<P_BF16, P_BF16, 12>(const HopParams&, int, int, int, bool, int, cudaStream_t);
 
 }  // namespace wl

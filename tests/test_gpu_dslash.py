@@ -206,3 +206,54 @@ def test_variant_solver(w, oracle_mod, monkeypatch, variant):
     st = w.wilson_cg_solve(x, dev(U), dev(b), w.lattice(dims), 0.135, w.solver_defaults(w.WILSON_F16))
     r = b - oracle_mod.wilson_m(U, host(x), dims, 0.135)
     assert np.linalg.norm(r) / np.linalg.norm(b) <= 1.1e-10
+
+
+# The register-blocked multi-RHS variants (NB = 2, 2, 3, 4 right-hand sides
+# per thread), pinned through WILSON_HOP_VARIANT, on 12 right-hand sides
+# (a multiple of every NB) over a lattice with a ragged last block.
+@pytest.mark.parametrize("variant", [6, 7, 8, 9])
+@pytest.mark.parametrize("prec", ["f32", "f16", "bf16"])
+def test_blocked_multi_rhs_variants(w, oracle_mod, monkeypatch, variant, prec):
+    monkeypatch.setenv("WILSON_HOP_VARIANT", str(variant))
+    monkeypatch.setenv("WILSON_HOP_BLOCK", str((64, 128, 256)[variant % 3]))
+    dims = (6, 4, 6, 10)
+    U = inputs.gauge_field(dims, "weak", eps=0.3, seed=123)
+    src = inputs.gaussian_spinor(inputs.volume(dims) // 2, seed=124, nrhs=12)
+    src[5] *= 1e-3  # right-hand sides of different magnitudes (F16 per-site scales)
+    got = handle_hop(w, U, src, dims, CPLX_PHASES, w.PREC[prec], 12, 1, 0, w.WILSON_OP_HOP, nrhs=12)
+    for k in range(12):
+        assert rel_l2(got[k], oracle_mod.dslash_eo(U, src[k], dims, 0, CPLX_PHASES)) <= TOL[prec]
+    got = handle_hop(w, U, src, dims, CPLX_PHASES, w.PREC[prec], 12, 1, 1, w.WILSON_OP_SCHUR_DAG, 0.1350,
+                     nrhs=12)
+    for k in range(12):
+        assert rel_l2(got[k], oracle_mod.schur(U, src[k], dims, 0.1350, 1, True, CPLX_PHASES)) <= TOL[prec]
+    psi = inputs.gaussian_spinor(dims, seed=125, nrhs=12)
+    got = handle_hop(w, U, psi, dims, CPLX_PHASES, w.PREC[prec], 12, w.WILSON_FULL, w.WILSON_FULL,
+                     w.WILSON_OP_M, 0.1350, nrhs=12)
+    for k in range(12):
+        assert rel_l2(got[k], oracle_mod.wilson_m(U, psi[k], dims, 0.1350, CPLX_PHASES)) <= TOL[prec]
+
+
+@pytest.mark.parametrize("variant", [6, 8, 9])
+def test_blocked_variant_lockstep_solve(w, oracle_mod, monkeypatch, variant):
+    """The lockstep multi-RHS solve on a blocked kernel: right-hand sides that
+    finish early (a zero source at once) are skipped inside their group while
+    the others go on, and every per-RHS reduction stays separate."""
+    monkeypatch.setenv("WILSON_HOP_VARIANT", str(variant))
+    dims = (4, 4, 4, 8)
+    kappa = 0.1350
+    U = inputs.gauge_field(dims, "weak", eps=0.3, seed=126)
+    b = inputs.gaussian_spinor(dims, seed=127, nrhs=12)
+    b[2] = 0
+    b[7] *= 1e-6
+    b[10] = inputs.point_sources(dims, site=3)[4]
+    x = dev(np.zeros_like(b))
+    rc, st = w.wilson_cg_solve_multi(x, dev(U), dev(b), 12, w.lattice(dims), kappa,
+                                     w.solver_defaults(w.WILSON_F16))
+    xs = host(x)
+    assert rc == 0 and np.all(xs[2] == 0)
+    for k in range(12):
+        if k == 2:
+            continue
+        r = b[k] - oracle_mod.wilson_m(U, xs[k], dims, kappa)
+        assert np.linalg.norm(r) / np.linalg.norm(b[k]) <= 1.1e-10
