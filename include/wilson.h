@@ -114,6 +114,11 @@ typedef struct {
     double delta;           /* inner reduction per outer correction (0 = default per prec)  */
     int use_initial_guess;  /* 1: x holds the initial guess on entry                        */
     int reliable;           /* 1: reliable updates (keep the CG direction), 0: restart CG   */
+    int block_cg;           /* wilson_cg_solve_multi with 2..16 right-hand sides: 1 = one
+                               block CG over all of them (O'Leary 1980, in Dubrulle's 2001
+                               form with an orthonormal residual basis) inside the FP64
+                               correction, instead of independent CGs in lockstep; 0 (default)
+                               = independent CGs.  Ignored for a single right-hand side.    */
 } wilson_solver_params;
 
 typedef struct {

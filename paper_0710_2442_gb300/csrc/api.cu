@@ -147,6 +147,7 @@ wilson_solver_params wilson_solver_defaults(int inner) {
     p.delta = 0.0;
     p.use_initial_guess = 0;
     p.reliable = 1;
+    p.block_cg = 0;
     return p;
 }
 
@@ -274,6 +275,7 @@ static SolveParams checked_params(const wilson_solver_params* p, double kappa) {
     prm.delta = p->delta;
     prm.use_initial_guess = p->use_initial_guess;
     prm.reliable = p->reliable;
+    prm.block_cg = p->block_cg;
     return prm;
 }
 
@@ -326,6 +328,7 @@ int wilson_cg_solve_multi(double* x, const double* gauge, const double* b, int n
         WL_REQUIRE(nrhs >= 1 && nrhs <= 64, "nrhs must be in 1..64");
         WL_REQUIRE(x != b, "x must not alias b");
         const SolveParams prm = checked_params(p, kappa);
+        WL_REQUIRE(!prm.block_cg || nrhs <= 16, "block CG takes at most 16 right-hand sides");
         check_device();
         WL_REQUIRE(is_device_ptr(x) && is_device_ptr(b) && is_device_ptr(gauge),
                    "wilson_cg_solve_multi takes device pointers");

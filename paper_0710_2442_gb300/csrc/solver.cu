@@ -39,8 +39,10 @@
 #include <chrono>
 #include <cmath>
 #include <cstddef>
+#include <memory>
 #include <vector>
 
+#include "blockcg.h"
 #include "solver.h"
 
 namespace wl {
@@ -173,6 +175,8 @@ std::vector<SolveStats> cg_solve_prepared(SpinorField& x, const SpinorField& b, 
 
     Inner in;
     in.alloc(prm.inner, g, nr);
+    std::unique_ptr<BlockInner> blk;
+    if (prm.block_cg && nr > 1) blk = std::make_unique<BlockInner>(in.ip, in.xp, g, nr);
     double delta = prm.delta;
     if (!(delta > 0.0)) delta = prm.inner == P_F64 ? 0.0 : prm.inner == P_F32 ? 1e-3 : 0.1;
 
@@ -255,6 +259,32 @@ std::vector<SolveStats> cg_solve_prepared(SpinorField& x, const SpinorField& b, 
             convert(in.xp, vec(in.s, 0), P_F64, vec(r64, 0), g, nr, st);
             if (in.has_slow) convert(in.ip, vec(in.slow, 0), P_F64, vec(r64, 0), g, nr, st);
             for (int k = 0; k < nr; k++) WL_CUDA(cudaMemsetAsync(in.xin.block(0, k), 0, in.xin.pbytes, st));
+            if (blk) {
+                // block CG over the unfinished right-hand sides
+                // column k stops after its normal residual fell by max(delta, half the
+                // factor its Schur residual still has to fall to reach the target)
+                int left = prm.maxiter;
+                std::vector<double> dk(nr, 1.0);
+                for (int k = 0; k < nr; k++) {
+                    if (finished[k]) continue;
+                    left = std::min(left, prm.maxiter - total_inner[k]);
+                    dk[k] = std::max(delta, 0.5 * target[k] / rnorm[k]);
+                }
+                const BlockInner::Result br =
+                    blk->run(glo, kappa, in.s_in(), vec(in.p, 0), vec(in.q, 0), vec(in.r, 0), vec(in.t, 1),
+                             vec(in.xin, 0), finished, dk, left, chunk, prm.use_graph != 0, prm.reliable != 0,
+                             st);
+                hops += 2 + 4 * br.iterations;
+                for (int k = 0; k < nr; k++)
+                    if (!finished[k]) total_inner[k] += br.iterations;
+                // The block lost rank (3) or met NaN/Inf in its own arithmetic (4; the
+                // sources' NaNs were caught by the FP64 residual above): independent CGs
+                // from here on, from a fresh start.  A rank loss keeps the correction made
+                // so far; a NaN/Inf drops it.
+                if (br.status != 0) blk.reset();
+                if (br.status != 4) axpy(P_F64, vec(x, 0), in.xp, vec(in.xin, 0), 1.0, g, nr, st);
+                continue;
+            }
             const bool restart = first || !prm.reliable;
             for (int k = 0; k < nr; k++) {
                 h_sc[k] = CGScalars{};

@@ -18,6 +18,7 @@ struct SolveParams {
     double delta = 0.0;       // 0: default per precision
     int use_initial_guess = 0;
     int reliable = 1;
+    int block_cg = 0;           // several right-hand sides: one block CG instead of lockstep CGs
     int chunk = 16;           // iterations per captured graph
     int use_graph = 1;
     int batch_small_vh = 4096;  // batched solves: problems with at most this many sites per parity

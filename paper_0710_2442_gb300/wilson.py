@@ -37,7 +37,7 @@ class wilson_lattice(ctypes.Structure):
 class wilson_solver_params(ctypes.Structure):
     _fields_ = [("inner", ctypes.c_int), ("recon", ctypes.c_int), ("tol", ctypes.c_double),
                 ("maxiter", ctypes.c_int), ("max_restarts", ctypes.c_int), ("delta", ctypes.c_double),
-                ("use_initial_guess", ctypes.c_int), ("reliable", ctypes.c_int)]
+                ("use_initial_guess", ctypes.c_int), ("reliable", ctypes.c_int), ("block_cg", ctypes.c_int)]
 
 
 class wilson_solve_stats(ctypes.Structure):

@@ -92,5 +92,19 @@ def test_no_device_is_an_error_not_a_fallback(w):
 def test_solver_defaults(w):
     p = w.solver_defaults(w.WILSON_F16)
     assert p.inner == w.WILSON_F16 and p.recon == 12 and p.tol == 1e-10 and p.reliable == 1
+    assert p.block_cg == 0
     p = w.solver_defaults(w.WILSON_F64)
     assert p.recon == 18
+
+
+def test_block_cg_rhs_limit(w):
+    """Block CG carries at most 16 right-hand sides; more is an argument error
+    raised before any device call."""
+    buf = np.zeros(64, dtype=np.complex128)
+    L = w.lattice((2, 2, 2, 2))
+    p = w.solver_defaults(w.WILSON_F16)
+    p.block_cg = 1
+    call = lambda: w.wilson_cg_solve_multi(buf, buf.ctypes.data + 256, buf.ctypes.data + 512, 17, L, 0.1, p,
+                                           check=False)[0]
+    assert call() == w.WILSON_ERR_ARG
+    assert "16" in w.lib().wilson_last_error().decode()
