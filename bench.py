@@ -305,7 +305,8 @@ def run_solver_block(w, torch, dev, stream):
 def run_multirhs_block(w, torch, dev, stream, fields, nrhs=12):
     """12 right-hand sides sharing the 32^3 x 64 F32 12-real links: the
     multi-RHS hop against the single-RHS one, and the lockstep 12-RHS CG
-    (point sources, F16 inner) against 12 sequential solves."""
+    (point sources, F16 inner) against 12 sequential solves and against
+    one block CG over the 12 right-hand sides."""
     cfg, dims, U, src = fields
     Vh = inputs.volume(dims) // 2
     L = w.lattice(dims)
@@ -356,10 +357,24 @@ def run_multirhs_block(w, torch, dev, stream, fields, nrhs=12):
         seq.append(w.wilson_cg_solve(xk, Ud, bsrc[k], L, kappa, p, stream, check=False))
     torch.cuda.synchronize(dev)
     t_seq = time.perf_counter() - t0
+    # block CG over the 12 right-hand sides (same sources, inner precision and target)
+    pb = w.solver_defaults(w.WILSON_F16)
+    pb.block_cg = 1
+    x.zero_()
+    w.wilson_cg_solve_multi(x, Ud, bsrc, nrhs, L, kappa, pb, stream, check=False)
+    x.zero_()
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    rcb, stb = w.wilson_cg_solve_multi(x, Ud, bsrc, nrhs, L, kappa, pb, stream, check=False)
+    torch.cuda.synchronize(dev)
+    t_block = time.perf_counter() - t0
     out["cg"] = {"kappa": kappa, "inner": "f16", "rc": rc, "seconds_lockstep": round(t_multi, 4),
                  "seconds_sequential": round(t_seq, 4), "speedup": round(t_seq / t_multi, 3),
                  "max_true_rel_resid": max(s["true_rel_resid"] for s in st),
-                 "inner_iters": [s["inner_iters"] for s in st]}
+                 "inner_iters": [s["inner_iters"] for s in st],
+                 "block_cg": {"rc": rcb, "seconds": round(t_block, 4),
+                              "inner_iters": max(s["inner_iters"] for s in stb),
+                              "max_true_rel_resid": max(s["true_rel_resid"] for s in stb)}}
     del Ud, bsrc, x
     torch.cuda.empty_cache()
     return out
