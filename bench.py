@@ -52,6 +52,8 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-solver", action="store_true",
                     help="skip the solver, multi-RHS and batch blocks (CG time-to-solution comparisons)")
+    ap.add_argument("--blocks", default="cg,multirhs,batch",
+                    help="solver blocks to run after the headline (comma list of cg, multirhs, batch)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--apps", type=int, default=None, help="applications per step (default 100)")
     ap.add_argument("--prec", choices=["f32", "f16", "bf16", "f64"], default="f32",
@@ -271,9 +273,13 @@ def run_ours(args, ws, rank, local, fields):
                             "launch_us": round(t_launch * 1e6, 2)}
     line.update({"clocks": clocks, "e2e": e2e, "gpu_launches": launches})
     if rank == 0 and not args.no_solver:
-        line["cg"] = run_solver_block(w, torch, dev, stream)
-        line["multirhs"] = run_multirhs_block(w, torch, dev, stream, fields)
-        line["batch"] = run_batch_block(w, torch, dev, stream)
+        blocks = {b.strip() for b in args.blocks.split(",")}
+        if "cg" in blocks:
+            line["cg"] = run_solver_block(w, torch, dev, stream)
+        if "multirhs" in blocks:
+            line["multirhs"] = run_multirhs_block(w, torch, dev, stream, fields)
+        if "batch" in blocks:
+            line["batch"] = run_batch_block(w, torch, dev, stream)
     return line
 
 

@@ -269,6 +269,75 @@ __global__ void __launch_bounds__(256, MINB) bhop_kernel(const BatchArgs A, cons
     }
 }
 
+// The same on the paired-FP32 stencil (F32 / F16 / BF16 spinors; see
+// hop_kernel_p): fewer instructions per site for the same arithmetic.
+template <int SP, int GP, int R, bool DAG, int MINB>
+__global__ void __launch_bounds__(256, MINB) bhop_kernel_p(const BatchArgs A, const BOp op) {
+    using SF = SpinorFmt<SP>;
+    for (int t = blockIdx.x; t < A.ntiles; t += gridDim.x) {
+        const int pid = __ldg(A.tile_prob + t);
+        if (!tile_active(A, op, pid)) continue;
+        const BatchProb& Pr = A.probs[pid];
+        HopParams P;
+        P.g = Pr.g;
+        P.gauge = Pr.glo;
+        const int p = op.out_parity;
+        char* out = Pr.f[op.f_out] + p * Pr.fp[op.f_out];
+        const char* in = Pr.f[op.f_in] + (1 - p) * Pr.fp[op.f_in];
+        const char* x = op.f_x >= 0 ? Pr.f[op.f_x] + p * Pr.fp[op.f_x] : nullptr;
+        const float a = (float)coef_of(op.coef, Pr.kappa);
+        const Geom& g = P.g;
+        double nrm = 0.0;
+        const int h0 = (t - Pr.tile0) * kTile;
+        for (int j = threadIdx.x; j < kTile; j += blockDim.x) {
+            const int h = h0 + j;
+            if (h >= g.Vh) break;
+            int c[4], s;
+            site_of_half(h, p, g, c, s);
+            PSpinor acc;
+            hop_dir_p<SP, GP, R, DAG, 0, true>(acc, P, in, p, h, c, s);
+            hop_dir_p<SP, GP, R, DAG, 1, false>(acc, P, in, p, h, c, s);
+            hop_dir_p<SP, GP, R, DAG, 2, false>(acc, P, in, p, h, c, s);
+            hop_dir_p<SP, GP, R, DAG, 3, false>(acc, P, in, p, h, c, s);
+            const float2 Af = bc2(a);
+            if (x) {
+                PSpinor xq;
+                float xs;
+                SF::load_packed(x, g.stride, h, xq, xs);
+                const float2 X = bc2(xs);
+#pragma unroll
+                for (int cc = 0; cc < 3; cc++) {
+                    acc.re01[cc] = fma2(Af, acc.re01[cc], mul2(X, xq.re01[cc]));
+                    acc.im01[cc] = fma2(Af, acc.im01[cc], mul2(X, xq.im01[cc]));
+                    acc.re23[cc] = fma2(Af, acc.re23[cc], mul2(X, xq.re23[cc]));
+                    acc.im23[cc] = fma2(Af, acc.im23[cc], mul2(X, xq.im23[cc]));
+                }
+            } else {
+#pragma unroll
+                for (int cc = 0; cc < 3; cc++) {
+                    acc.re01[cc] = mul2(Af, acc.re01[cc]);
+                    acc.im01[cc] = mul2(Af, acc.im01[cc]);
+                    acc.re23[cc] = mul2(Af, acc.re23[cc]);
+                    acc.im23[cc] = mul2(Af, acc.im23[cc]);
+                }
+            }
+            if (op.fin != BF_NONE) {
+                float2 n2 = make_float2(0.f, 0.f);
+#pragma unroll
+                for (int cc = 0; cc < 3; cc++) {
+                    n2 = fma2(acc.re01[cc], acc.re01[cc], n2);
+                    n2 = fma2(acc.im01[cc], acc.im01[cc], n2);
+                    n2 = fma2(acc.re23[cc], acc.re23[cc], n2);
+                    n2 = fma2(acc.im23[cc], acc.im23[cc], n2);
+                }
+                nrm += (double)n2.x + (double)n2.y;
+            }
+            SF::store_packed(out, g.stride, h, acc);
+        }
+        if (op.fin != BF_NONE) tile_reduce(nrm, A, op, t, pid);
+    }
+}
+
 // ---------------------------------------------------------------------------
 // batched BLAS-1 kernels (all tile-walking, phase-filtered)
 // ---------------------------------------------------------------------------
@@ -799,9 +868,18 @@ struct BatchRun {
                  <<<blocks, c.block, 0, st>>>(A, o);                                                \
     else bhop_kernel<SP, GP, (SP == P_F64 ? 18 : 12), false, hop_variant_minb(V, SP)>              \
              <<<blocks, c.block, 0, st>>>(A, o);
-        // the batch walker uses the scalar stencil: register variants only
+#define WL_BHOP_P(V)                                                                                \
+    if (dag) bhop_kernel_p<SP, GP, 12, true, hop_variant_minb(V, SP)><<<blocks, c.block, 0, st>>>(A, o); \
+    else bhop_kernel_p<SP, GP, 12, false, hop_variant_minb(V, SP)><<<blocks, c.block, 0, st>>>(A, o);
+        // variants 0-2: scalar stencil, 3-5: paired-FP32 stencil (not for FP64)
+        if constexpr (SP != P_F64) {
+            if (v == 3) { WL_BHOP_P(3) return; }
+            if (v == 4) { WL_BHOP_P(4) return; }
+            if (v == 5) { WL_BHOP_P(5) return; }
+        }
         if (v % 3 == 1) { WL_BHOP(1) } else if (v % 3 == 2) { WL_BHOP(2) } else { WL_BHOP(0) }
 #undef WL_BHOP
+#undef WL_BHOP_P
     }
     void hop(const BOp& o, int dag, cudaStream_t st) const {
         if (o.use64) {
@@ -980,9 +1058,11 @@ void batch_solve(int n, const wilson_problem* probs, const SolveParams& prm, wil
         if (std::atoll(e) > 0) budget_ns = std::min(budget_ns, (unsigned long long)std::atoll(e) * 1000000ULL);
 
     // tune the batched hop kernels of every loop class (non-reducing launches on scratch fields)
-    std::vector<LaunchConfig> cands;
-    for (const LaunchConfig& c : hop_candidates())
-        if (c.variant < 3) cands.push_back(c);
+    std::vector<LaunchConfig> cands, cands64;
+    for (const LaunchConfig& c : hop_candidates()) {
+        cands.push_back(c);
+        if (c.variant < 3) cands64.push_back(c);
+    }
     for (auto& R : loops) {
         char key[96];
         snprintf(key, sizeof(key), "bhop:lo%d:n%d:t%d", (int)ip, R->nprob, R->ntiles);
@@ -993,7 +1073,7 @@ void batch_solve(int n, const wilson_problem* probs, const SolveParams& prm, wil
         });
         snprintf(key, sizeof(key), "bhop:f64:n%d:t%d", R->nprob, R->ntiles);
         const BOp o64 = R->op(BF_Q64, BF_T64, BF_X, 0, 1, 2, -1, 0, BF_NONE, 0);
-        R->hop_64 = tune_launch(key, cands, LaunchConfig{128, 0}, st,
+        R->hop_64 = tune_launch(key, cands64, LaunchConfig{128, 0}, st,
                                 [&](const LaunchConfig& c) { Rp->hop_t<P_F64, P_F64>(o64, 0, c, st); });
     }
 
