@@ -111,7 +111,10 @@ typedef struct {
     double tol;             /* target true relative residual, e.g. 1e-10                    */
     int maxiter;            /* cap on inner CG iterations over the whole solve              */
     int max_restarts;       /* cap on FP64 outer corrections                                */
-    double delta;           /* inner reduction per outer correction (0 = default per prec)  */
+    double delta;           /* inner reduction per outer correction; 0 = default per inner
+                               precision: F32 1e-4, F16 0.02, BF16 0.1 (FP64: none).  An
+                               inner solve also stops after 1000 iterations, and the next
+                               FP64 correction continues it.                                */
     int use_initial_guess;  /* 1: x holds the initial guess on entry                        */
     int reliable;           /* 1: reliable updates (keep the CG direction), 0: restart CG   */
     int block_cg;           /* wilson_cg_solve_multi with 2..16 right-hand sides: 1 = one
@@ -134,7 +137,9 @@ typedef struct {
 wilson_solver_params wilson_solver_defaults(int inner);
 
 /* x, b: V spinors (canonical, device); gauge: 4V links (canonical, device).
- * Returns WILSON_OK, or WILSON_ERR_NOCONV with x holding the last iterate. */
+ * Returns WILSON_OK, or WILSON_ERR_NOCONV with x holding the last iterate
+ * (maxiter or max_restarts spent, or an FP64 residual grown 1000-fold past
+ * the smallest one of the solve: a diverging inner solve). */
 int wilson_cg_solve(double* x, const double* gauge, const double* b, const wilson_lattice* L,
                     double kappa, const wilson_solver_params* p, wilson_solve_stats* st, void* stream);
 

@@ -70,6 +70,7 @@ struct BatchState {
     int pad;
     double bnorm2;
     double rnorm2;
+    double best2;  // smallest |r|^2 of the FP64 corrections so far
     double res2;
     unsigned long long t_done;
 };
@@ -147,13 +148,15 @@ __device__ void batch_finish(int op, const BatchProb& P, BatchState& S, double s
             break;
         case BFIN_OUTER: {
             S.rnorm2 = sum;
+            if (S.outer == 0 || sum < S.best2) S.best2 = sum;
             const double target2 = P.tol * P.tol * S.bnorm2;
             if (!isfinite(sum)) {
                 S.status = WILSON_ERR_NUMERIC;
                 S.next_phase = PH_DONE;
             } else if (sum <= target2) {
                 S.next_phase = PH_DONE;
-            } else if (S.outer >= P.max_outer || sc.iter >= P.maxiter) {
+            } else if (S.outer >= P.max_outer || sc.iter >= P.maxiter ||
+                       (S.outer > 0 && sum > kDivergence * kDivergence * S.best2)) {
                 S.status = WILSON_ERR_NOCONV;
                 S.next_phase = PH_DONE;
             } else {
@@ -163,7 +166,7 @@ __device__ void batch_finish(int op, const BatchProb& P, BatchState& S, double s
                 sc.stop2 = stop * stop;
                 sc.snorm2 = sum;
                 sc.done = 0;
-                sc.maxiter = P.maxiter;
+                sc.maxiter = min(P.maxiter, sc.iter + kInnerCap);  // iter counts the whole solve
             }
             if (S.next_phase == PH_DONE) S.t_done = globaltimer();
             break;
@@ -672,7 +675,7 @@ __global__ void __launch_bounds__(kSmallThreads, 1) small_solve_kernel(const Bat
     const double target2 = Pr.tol * Pr.tol * bnorm2;
 
     int iter = 0, outer = 0, status = 0;
-    double gam = 0.0;
+    double gam = 0.0, best2 = HUGE_VAL;  // best2: smallest |r|^2 of the FP64 corrections
     bool first = true;
     while (true) {
         // x_e += xin; r = bhat - Mhat x_e (FP64)
@@ -715,7 +718,11 @@ __global__ void __launch_bounds__(kSmallThreads, 1) small_solve_kernel(const Bat
         const double rn2 = cta_sum(rn);
         if (!isfinite(rn2)) { status = WILSON_ERR_NUMERIC; break; }
         if (rn2 <= target2) break;
-        if (outer >= Pr.max_outer || iter >= Pr.maxiter) { status = WILSON_ERR_NOCONV; break; }
+        if (outer >= Pr.max_outer || iter >= Pr.maxiter || rn2 > kDivergence * kDivergence * best2) {
+            status = WILSON_ERR_NOCONV;
+            break;
+        }
+        best2 = fmin(best2, rn2);
         if (globaltimer() - G->t_start > budget_ns) { status = WILSON_ERR_TIMEOUT; break; }
         outer++;
         // r' = Mhat'^dag s; p = r' + beta p (beta = 0 at the start)
@@ -727,6 +734,7 @@ __global__ void __launch_bounds__(kSmallThreads, 1) small_solve_kernel(const Bat
         first = false;
         const double stop = fmax(Pr.delta * sqrt(rn2), sqrt(target2));
         const double stop2 = stop * stop;
+        const int iter_cap = min(Pr.maxiter, iter + kInnerCap);
         while (true) {
             for (int h = tid; h < g.Vh; h += nt) {
                 cpx<TI> pv[12], rv[12];
@@ -771,7 +779,7 @@ __global__ void __launch_bounds__(kSmallThreads, 1) small_solve_kernel(const Bat
             const double ss = cta_sum(sn);
             iter++;
             if (!isfinite(ss)) { status = WILSON_ERR_NUMERIC; break; }
-            if (ss <= stop2 || iter >= Pr.maxiter) break;
+            if (ss <= stop2 || iter >= iter_cap) break;
             if ((iter & 15) == 0 && globaltimer() - G->t_start > budget_ns) break;
             cta_hop<IP, IP, 12, true>(g, Pr.glo, f[BF_T], f[BF_SLOW], nullptr, 1.0, 1);
             const double rr = cta_hop<IP, IP, 12, true>(g, Pr.glo, f[BF_R], f[BF_T], f[BF_SLOW], -k2, 0);
@@ -947,7 +955,7 @@ std::unique_ptr<BatchRun> make_run(const std::vector<HostProb>& hp, const std::v
         D.glo = P.glo.buf.as<const char>();
         D.kappa = P.kappa;
         D.tol = prm.tol;
-        D.delta = prm.delta > 0 ? prm.delta : (R->ip == P_F32 ? 1e-3 : 0.1);
+        D.delta = prm.delta > 0 ? prm.delta : default_delta(R->ip);
         D.maxiter = prm.maxiter;
         D.max_outer = prm.max_restarts;
         D.keep_x = prm.use_initial_guess;

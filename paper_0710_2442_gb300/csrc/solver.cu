@@ -178,7 +178,7 @@ std::vector<SolveStats> cg_solve_prepared(SpinorField& x, const SpinorField& b, 
     std::unique_ptr<BlockInner> blk;
     if (prm.block_cg && nr > 1) blk = std::make_unique<BlockInner>(in.ip, in.xp, g, nr);
     double delta = prm.delta;
-    if (!(delta > 0.0)) delta = prm.inner == P_F64 ? 0.0 : prm.inner == P_F32 ? 1e-3 : 0.1;
+    if (!(delta > 0.0)) delta = default_delta(prm.inner);
 
     // Tune the operator launches before capture (tuning cannot run inside a
     // captured stream).  The launches below only write scratch fields.
@@ -220,6 +220,7 @@ std::vector<SolveStats> cg_solve_prepared(SpinorField& x, const SpinorField& b, 
     }
 
     std::vector<int> total_inner(nr, 0), finished(nr, 0);
+    std::vector<double> best(nr, HUGE_VAL);  // smallest FP64 residual so far
     int outer = 0;
     bool first = true;
     try {
@@ -244,12 +245,13 @@ std::vector<SolveStats> cg_solve_prepared(SpinorField& x, const SpinorField& b, 
                     stats[k].status = 6;
                 } else if (rnorm[k] <= target[k]) {
                     finished[k] = 1;
-                } else if (total_inner[k] >= prm.maxiter || !budget) {
+                } else if (total_inner[k] >= prm.maxiter || !budget || rnorm[k] > kDivergence * best[k]) {
                     finished[k] = 1;
                     stats[k].status = 4;
                 } else {
                     all_done = false;
                 }
+                best[k] = std::min(best[k], rnorm[k]);
             }
             if (all_done) break;
             outer++;
@@ -263,7 +265,7 @@ std::vector<SolveStats> cg_solve_prepared(SpinorField& x, const SpinorField& b, 
                 // block CG over the unfinished right-hand sides
                 // column k stops after its normal residual fell by max(delta, half the
                 // factor its Schur residual still has to fall to reach the target)
-                int left = prm.maxiter;
+                int left = kInnerCap;
                 std::vector<double> dk(nr, 1.0);
                 for (int k = 0; k < nr; k++) {
                     if (finished[k]) continue;
@@ -295,7 +297,7 @@ std::vector<SolveStats> cg_solve_prepared(SpinorField& x, const SpinorField& b, 
                 const double stop = std::max(delta * rnorm[k], target[k]);
                 h_sc[k].stop2 = stop * stop;
                 h_sc[k].snorm2 = rnorm[k] * rnorm[k];
-                h_sc[k].maxiter = prm.maxiter - total_inner[k];
+                h_sc[k].maxiter = std::min(prm.maxiter - total_inner[k], kInnerCap);
             }
             if (restart) {
                 WL_CUDA(cudaMemcpyAsync(sc, h_sc, sizeof(CGScalars) * nr, cudaMemcpyHostToDevice, st));

@@ -25,6 +25,25 @@ struct SolveParams {
                                 // run the CTA-resident solver (0: none)
 };
 
+// Default inner reduction per FP64 correction (|s| <= delta |r|), by inner
+// precision: measured on the 24^3 x 48 solve, F16 is fastest near 0.02 and
+// stagnates below about 0.005 (its storage precision), BF16 is fastest at
+// 0.1, F32 at 1e-4 .. 1e-5.  FP64: the inner CG runs to the target.
+inline double default_delta(Prec ip) {
+    return ip == P_F64 ? 0.0 : ip == P_F32 ? 1e-4 : ip == P_F16 ? 0.02 : 0.1;
+}
+
+// Inner CG iterations between two FP64 corrections at most.  With reliable
+// updates a forced correction only replaces the residual (the direction
+// continues), so the cap costs one FP64 residual per 1000 iterations; it
+// bounds an inner solve whose delta is below what its precision can reach.
+constexpr int kInnerCap = 1000;
+
+// A right-hand side whose FP64 residual grows past this factor times the
+// smallest one it has had is diverging (an inner precision too coarse for its
+// delta): it stops with WILSON_ERR_NOCONV instead of spending maxiter.
+constexpr double kDivergence = 1e3;
+
 struct SolveStats {
     int status = 0;
     int outer_iters = 0;
