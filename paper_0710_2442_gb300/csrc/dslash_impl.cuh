@@ -613,14 +613,18 @@ constexpr int kHopBaseVariants = 6;
 constexpr int hop_variant_nb(int v) {
     return v < kHopBaseVariants ? 1 : v == 6 || v == 7 ? 2 : v == 8 ? 3 : 4;
 }
+// FP64 operands take two registers per real: their budgets start at 255
+// registers.
+constexpr bool wide_regs(int sp) { return sp == P_F64; }
+constexpr bool float_storage(int sp) { return sp == P_F32 || sp == P_F16 || sp == P_BF16; }
 constexpr int hop_variant_minb(int v, int sp) {
-    return v < kHopBaseVariants ? (sp == P_F64 ? 1 : 2) + v % 3 : v == 7 ? 2 : 1;
+    return v < kHopBaseVariants ? (wide_regs(sp) ? 1 : 2) + v % 3 : v == 7 ? 2 : 1;
 }
 inline bool hop_variant_valid(int v, Prec sp, int recon, int nrhs) {
     if (v < 0 || v >= kHopVariants) return false;
     if (v < kHopBaseVariants) return true;
     const int nb = hop_variant_nb(v);
-    return sp != P_F64 && recon == 12 && nrhs >= nb && nrhs % nb == 0;
+    return float_storage(sp) && recon == 12 && nrhs >= nb && nrhs % nb == 0;
 }
 
 // The register-blocked kernels (instantiated in dslash_mrhs.cu).
@@ -639,7 +643,7 @@ void launch_hop_mrhs_v(const HopParams& P, int block, int site_blocks, int ny, b
 template <int SP, int GP, int R, int V>
 void launch_hop_v(const HopParams& P, dim3 grid, int block, bool dag, cudaStream_t st) {
     constexpr int MINB = hop_variant_minb(V, SP);
-    if constexpr (V >= 3 && SP != P_F64) {
+    if constexpr (V >= 3 && float_storage(SP)) {
         if (dag) hop_kernel_p<SP, GP, R, true, MINB><<<grid, block, 0, st>>>(P);
         else hop_kernel_p<SP, GP, R, false, MINB><<<grid, block, 0, st>>>(P);
     } else {
@@ -654,14 +658,14 @@ template <int SP, int GP, int R>
 void launch_hop_prec(const HopParams& P, int block, int site_blocks, int ny, bool dag, int variant,
                      cudaStream_t st) {
     if (variant >= kHopBaseVariants) {
-        if constexpr (SP != P_F64 && R == 12) {
+        if constexpr (float_storage(SP) && R == 12) {
             launch_hop_mrhs<SP, GP, R>(P, block, site_blocks, ny, dag, variant, st);
             return;
         }
         throw Error(7, "register-blocked hop variant needs F32/F16/BF16 spinors and 12-real links");
     }
     const dim3 grid(site_blocks * P.nrhs, ny);
-    if (SP == P_F64) variant %= 3;
+    if (wide_regs(SP)) variant %= 3;
     switch (variant) {
         case 1: launch_hop_v<SP, GP, R, 1>(P, grid, block, dag, st); break;
         case 2: launch_hop_v<SP, GP, R, 2>(P, grid, block, dag, st); break;
