@@ -177,6 +177,11 @@ std::vector<SolveStats> cg_solve_prepared(SpinorField& x, const SpinorField& b, 
     in.alloc(prm.inner, g, nr);
     std::unique_ptr<BlockInner> blk;
     if (prm.block_cg && nr > 1) blk = std::make_unique<BlockInner>(in.ip, in.xp, g, nr);
+    // The block's own reduction per correction: the caller's delta, else a
+    // conservative default (longer block runs in reduced precision lose the
+    // orthogonality of their residual basis).
+    const double delta_block =
+        prm.delta > 0.0 ? prm.delta : prm.inner == P_F64 ? 0.0 : prm.inner == P_F32 ? 1e-3 : 0.1;
     double delta = prm.delta;
     if (!(delta > 0.0)) delta = default_delta(prm.inner);
 
@@ -270,7 +275,7 @@ std::vector<SolveStats> cg_solve_prepared(SpinorField& x, const SpinorField& b, 
                 for (int k = 0; k < nr; k++) {
                     if (finished[k]) continue;
                     left = std::min(left, prm.maxiter - total_inner[k]);
-                    dk[k] = std::max(delta, 0.5 * target[k] / rnorm[k]);
+                    dk[k] = std::max(delta_block, 0.5 * target[k] / rnorm[k]);
                 }
                 const BlockInner::Result br =
                     blk->run(glo, kappa, in.s_in(), vec(in.p, 0), vec(in.q, 0), vec(in.r, 0), vec(in.t, 1),
@@ -283,8 +288,19 @@ std::vector<SolveStats> cg_solve_prepared(SpinorField& x, const SpinorField& b, 
                 // sources' NaNs were caught by the FP64 residual above): independent CGs
                 // from here on, from a fresh start.  A rank loss keeps the correction made
                 // so far; a NaN/Inf drops it.
-                if (br.status != 0) blk.reset();
-                if (br.status != 4) axpy(P_F64, vec(x, 0), in.xp, vec(in.xin, 0), 1.0, g, nr, st);
+                // A correction that is not finite everywhere is dropped the same way.
+                bool finite = br.status != 4;
+                if (finite) {
+                    norm2(in.xp, vec(in.xin, 0), g, nr, red.args(slot(7), FIN_STORE, d_res + 5 * nr, nullptr),
+                          grid_cap, st);
+                    WL_CUDA(cudaMemcpyAsync(h_res + 5 * nr, d_res + 5 * nr, nr * sizeof(double),
+                                            cudaMemcpyDeviceToHost, st));
+                    WL_CUDA(cudaStreamSynchronize(st));
+                    for (int k = 0; k < nr; k++)
+                        if (!finished[k] && !std::isfinite(h_res[5 * nr + k])) finite = false;
+                }
+                if (br.status != 0 || !finite) blk.reset();
+                if (finite) axpy(P_F64, vec(x, 0), in.xp, vec(in.xin, 0), 1.0, g, nr, st);
                 continue;
             }
             const bool restart = first || !prm.reliable;
