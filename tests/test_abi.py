@@ -108,3 +108,30 @@ def test_block_cg_rhs_limit(w):
                                            check=False)[0]
     assert call() == w.WILSON_ERR_ARG
     assert "16" in w.lib().wilson_last_error().decode()
+
+
+def test_batch_and_multi_rhs_arguments_rejected(w):
+    """Batched and multi-RHS solves validate their arguments before any
+    device call: an empty batch, an FP64 or 18-real inner operator, an odd
+    extent, x aliasing b, and right-hand-side counts outside 1..64."""
+    buf = np.zeros(4096, dtype=np.complex128)
+    base = buf.ctypes.data
+    L = w.lattice((4, 4, 4, 4))
+
+    def prob(dims=(4, 4, 4, 4), b_off=512, x_off=1024):
+        return dict(L=w.lattice(dims), kappa=0.12, gauge=base, b=base + b_off, x=base + x_off)
+
+    def batch(probs, inner=w.WILSON_F16, recon=12):
+        p = w.solver_defaults(inner)
+        p.recon = recon
+        return w.wilson_batch_solve(probs, p, check=False)[0]
+
+    assert batch([]) == w.WILSON_ERR_ARG
+    assert batch([prob()], inner=w.WILSON_F64) == w.WILSON_ERR_ARG
+    assert batch([prob()], recon=18) == w.WILSON_ERR_ARG
+    assert batch([prob(), prob(dims=(4, 4, 3, 4))]) == w.WILSON_ERR_ARG
+    assert batch([prob(b_off=512, x_off=512)]) == w.WILSON_ERR_ARG
+    p = w.solver_defaults(w.WILSON_F16)
+    for nrhs in (0, 65):
+        rc, _ = w.wilson_cg_solve_multi(base + 1024, base, base + 512, nrhs, L, 0.12, p, check=False)
+        assert rc == w.WILSON_ERR_ARG

@@ -145,3 +145,24 @@ def test_small_path_budget_runs_out(w, monkeypatch):
     rc, st, info = w.wilson_batch_solve(probs, w.solver_defaults(w.WILSON_F16), check=False)
     assert rc in (w.WILSON_ERR_TIMEOUT, w.WILSON_OK)
     assert all(s["status"] in (w.WILSON_ERR_TIMEOUT, w.WILSON_OK) for s in st)
+
+
+@pytest.mark.parametrize("small_vh", ["0", "4096"])
+def test_batch_single_and_degenerate_problems(w, oracle_mod, monkeypatch, small_vh):
+    """A batch of one problem, and a batch holding a kappa = 0 problem (M = 1,
+    x = b) and a zero source (x stays 0) beside a regular one, on the loop
+    path and on the CTA-resident path."""
+    monkeypatch.setenv("WILSON_BATCH_SMALL_VH", small_vh)
+    probs, hf = make_batch(w, [((4, 4, 4, 8), 0.3, 0.13)], seed0=510)
+    rc, st, info = w.wilson_batch_solve(probs, w.solver_defaults(w.WILSON_F16))
+    dims, U, b, kappa = hf[0]
+    assert rc == 0 and true_resid(oracle_mod, U, host(probs[0]["x"]), b, dims, kappa) <= 1.1e-10
+    probs, hf = make_batch(w, [((4, 4, 4, 4), 0.3, 0.0), ((6, 4, 6, 10), 0.3, 0.13), ((4, 4, 4, 8), 0.3, 0.125)],
+                           seed0=520)
+    probs[2]["b"].zero_()
+    rc, st, info = w.wilson_batch_solve(probs, w.solver_defaults(w.WILSON_F16))
+    assert rc == 0 and all(s["status"] == 0 for s in st)
+    assert rel_l2(host(probs[0]["x"]), hf[0][2]) <= 1e-10
+    dims, U, b, kappa = hf[1]
+    assert true_resid(oracle_mod, U, host(probs[1]["x"]), b, dims, kappa) <= 1.1e-10
+    assert np.all(host(probs[2]["x"]) == 0)

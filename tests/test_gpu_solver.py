@@ -216,3 +216,14 @@ def test_block_cg_nan_source_is_per_column(w, oracle_mod):
     for k in (0, 1, 3):
         assert st[k]["status"] == 0
         assert true_resid(oracle_mod, U, x[k], b[k], dims, kappa) <= 1.1e-10
+
+
+@pytest.mark.parametrize("inner", ["f64", "f16"])
+def test_kappa_zero_is_identity(w, inner):
+    """kappa = 0 makes M the identity: the solve returns x = b."""
+    dims = (4, 4, 4, 6)
+    U = inputs.gauge_field(dims, "weak", eps=0.3, seed=240)
+    b = inputs.gaussian_spinor(dims, seed=241)
+    x, st = solve(w, U, b, dims, 0.0, w.PREC[inner])
+    assert st["rc"] == 0 and st["true_rel_resid"] <= 1e-10
+    assert rel_l2(x, b) <= 1e-10
