@@ -1,13 +1,17 @@
 // batch.cu -- many independent solves on lattices of different sizes in one
-// CUDA graph launch (wilson_batch_solve).
+// CUDA graph launch (wilson_batch_solve): host orchestration and the batched
+// BLAS-1 kernels.  The problem states, finishers, hop kernels and the
+// CTA-resident solver are in batch_impl.cuh.
 //
 // Every problem keeps its own lattice, links, kappa, fields and CG scalars.
-// The half lattices of all problems are cut into tiles of kTile sites; a
-// tile table maps every tile to its problem, and every kernel of the batch is
-// a persistent grid that walks the tile table, so one launch serves all
-// problems whatever their sizes.  Per-problem reductions are tile partials
-// summed in a fixed order by the problem's last tile (no block waits for
-// another).
+// Problems with at most SolveParams::batch_small_vh sites per parity are each
+// solved by one thread block (small_solve_kernel).  The others are grouped
+// by lattice size into classes; each class's half lattices are cut into
+// tiles of kTile sites, a tile table maps every tile to its problem, and
+// every kernel of the class walks the tile table (one block per tile by
+// default), so one launch serves all its problems whatever their sizes.
+// Per-problem reductions are tile partials summed in a fixed order by the
+// problem's last tile (no block waits for another).
 //
 // Each problem runs the solver of solver.cu (CGNR on the even Schur
 // complement; FP64 outer corrections with reliable updates around an inner
@@ -17,14 +21,16 @@
 //           (or out of budget), else s = r, e = 0, r' = Mhat'^dag s,
 //           p = r' + beta p  -> INNER
 //   INNER:  one CG iteration (six kernels as in solver.cu) -> OUTER when
-//           |s| <= delta |r| (or maxiter)
+//           |s| <= delta |r| (or the per-correction iteration cap)
 //
-// The graph is: prologue (|b|^2, bhat, zeroed iterates) -> a device-side
-// while loop whose body runs the OUTER kernels and the INNER kernels as two
+// The graph is: prologue (|b|^2, bhat, zeroed iterates) -> the small
+// problems' CTA solves and, per class, a device-side while loop (conditional
+// node) whose body runs the OUTER kernels and the INNER kernels as two
 // parallel branches (disjoint problems) and then a one-block commit kernel
-// that advances every problem's phase and sets the loop condition -> epilogue
-// (x_o = b_o + kappa D_oe x_e, true residuals, completion times).  The commit
-// kernel stops the loop after a hard number of iterations or a wall-clock
+// that advances the class's problems and sets its loop condition; smaller
+// classes' kernels carry higher graph-node priorities -> epilogue (x_o =
+// b_o + kappa D_oe x_e, true residuals, completion times).  Each commit
+// kernel stops its loop after a hard number of iterations or a wall-clock
 // budget even if some problem has not finished, so the launch always ends.
 #include <algorithm>
 #include <chrono>
