@@ -410,10 +410,13 @@ def run_batch_block(w, torch, dev, stream):
     torch.cuda.synchronize(dev)
     t_seq = time.perf_counter() - t0
     q = lambda a, f: a[min(len(a) - 1, int(round(f * (len(a) - 1))))]
-    by_size = {}
+    by_size, iters = {}, {}
     for p, s_ in zip(probs, st):
-        by_size.setdefault("x".join(map(str, p["dims"])), []).append(s_["seconds"])
-    by_size = {k: {"n": len(v), "median_s": round(sorted(v)[len(v) // 2], 4), "max_s": round(max(v), 4)}
+        key = "x".join(map(str, p["dims"]))
+        by_size.setdefault(key, []).append(s_["seconds"])
+        iters[key] = iters.get(key, 0) + s_["inner_iters"]
+    by_size = {k: {"n": len(v), "median_s": round(sorted(v)[len(v) // 2], 4), "max_s": round(max(v), 4),
+                   "inner_iters": iters[k]}
                for k, v in by_size.items()}
     out = {"workload": "batch64_uneven", "problems": len(probs), "sites": sites, "inner": "f16", "rc": rc,
            "device_seconds": round(info["device_seconds"], 4), "call_seconds": round(info["seconds"], 4),
@@ -442,6 +445,49 @@ def oracle_sample(dims, U, src, reps=1):
         oracle.dslash_eo(U, src, dims, 1)
     t = time.perf_counter() - t0
     return model.FLOPS_PER_SITE * Vh * reps / t / 1e9, cores, t
+
+
+def oracle_cg_per_iteration(dims, U, b, kappa, iters=10):
+    """Seconds per CGNR iteration of the FP64 oracle (iters timed; the set-up
+    and the final residual are included, about 3 of the 4 x iters hops)."""
+    import oracle
+    t0 = time.perf_counter()
+    _, info = oracle.cg_solve(U, b, dims, kappa, maxiter=iters)
+    return (time.perf_counter() - t0) / max(info["iterations"], 1)
+
+
+def oracle_solver_baselines(line):
+    """CPU baselines of the solver workloads, extrapolated from a bounded
+    sample: the oracle's seconds per CG iteration times the iteration count
+    of the GPU solve of the same workload."""
+    import oracle
+    cfg = inputs.WORKLOADS["cg_mixed_24^3x48"]
+    dims = cfg["dims"]
+    U = inputs.gauge_field(dims, cfg["gauge"], eps=cfg["eps"], seed=cfg["gauge_seed"])
+    b = inputs.gaussian_spinor(dims, seed=cfg["spinor_seed"])
+    per_it = {"24x24x24x48": oracle_cg_per_iteration(dims, U, b, cfg["kappa"])}
+    out = {}
+    gpu = line.get("cg", {}).get("f64", {})
+    if gpu.get("inner_iters"):
+        out["cg_24^3x48_fp64"] = {
+            "seconds_per_iteration": round(per_it["24x24x24x48"], 4), "iterations": gpu["inner_iters"],
+            "seconds_extrapolated": round(per_it["24x24x24x48"] * gpu["inner_iters"], 2),
+            "gpu_fp64_seconds": gpu["seconds"], "gpu_f16_mixed_seconds": line["cg"]["f16"]["seconds"]}
+    batch = line.get("batch", {}).get("latency_by_lattice")
+    if batch:
+        total = 0.0
+        for key, rec in batch.items():
+            d = tuple(int(v) for v in key.split("x"))
+            if key not in per_it:
+                Us = inputs.gauge_field(d, "weak", eps=0.3, seed=inputs.SEED_BASE + 90)
+                bs = inputs.gaussian_spinor(d, seed=inputs.SEED_BASE + 91)
+                per_it[key] = oracle_cg_per_iteration(d, Us, bs, 0.13)
+            total += per_it[key] * rec["inner_iters"]
+        out["batch64_uneven"] = {"seconds_extrapolated": round(total, 2),
+                                 "gpu_device_seconds": line["batch"]["device_seconds"],
+                                 "sample": "10 oracle CG iterations per lattice size, times the GPU batch's "
+                                           "iterations of that size"}
+    return out
 
 
 def run_reference(args, ws, rank):
@@ -482,10 +528,17 @@ def main():
     line = run_ours(args, ws, rank, local, fields)
     if rank == 0 and ws == 1 and not args.no_cpu:
         cfg, dims, U, src = fields
+        import oracle
         v, cores, t = oracle_sample(dims, U, src)
+        oracle.set_num_threads(1)
+        v1, _, t1 = oracle_sample(dims, U, src)
+        oracle.set_num_threads(cores)
         line["cpu_baseline"] = {"value": round(v, 4), "unit": "GFlop/s", "cores": cores, "kind": "oracle",
                                 "sample": f"one FP64 even-odd application on the full 32^3x64 lattice "
-                                          f"({t:.1f} s of CPU time)"}
+                                          f"({t:.1f} s of CPU time)",
+                                "value_1core": round(v1, 4)}
+        if not args.no_solver:
+            line["cpu_baseline"]["solvers"] = oracle_solver_baselines(line)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if ws > 1:
