@@ -121,6 +121,15 @@ __device__ __forceinline__ T ldro(const T* p) {
     else return __ldg(p);
 }
 
+// Stores of outputs that are not read again soon (several right-hand sides
+// streamed through L2) use the evict-first hint (CS = true), so that they do
+// not displace the inputs' neighbour reuse from L2.
+template <bool CS, class T>
+__device__ __forceinline__ void st_hint(T* p, const T& v) {
+    if constexpr (CS) __stcs(p, v);
+    else *p = v;
+}
+
 // ---------------------------------------------------------------------------
 // low-precision helpers
 // ---------------------------------------------------------------------------
@@ -182,10 +191,11 @@ struct SpinorFmt<P_F64> {
         load<COH>(base, stride, i, v);
         s = 1.0;
     }
+    template <bool CS = false>
     __device__ static __forceinline__ void store(void* base, int stride, int i, const cpx<double> v[12]) {
         double2* b = static_cast<double2*>(base) + i;
 #pragma unroll
-        for (int c = 0; c < 12; c++) b[(size_t)c * stride] = make_double2(v[c].re, v[c].im);
+        for (int c = 0; c < 12; c++) st_hint<CS>(b + (size_t)c * stride, make_double2(v[c].re, v[c].im));
     }
 };
 
@@ -243,12 +253,15 @@ struct SpinorFmt<P_F32> {
         }
         s = 1.0f;
     }
+    template <bool CS = false>
     __device__ static __forceinline__ void store_packed(void* base, int stride, int i, const PSpinor& q) {
         float4* b = static_cast<float4*>(base) + i;
 #pragma unroll
         for (int c = 0; c < 3; c++) {
-            b[(size_t)(2 * c) * stride] = make_float4(q.re01[c].x, q.re01[c].y, q.im01[c].x, q.im01[c].y);
-            b[(size_t)(2 * c + 1) * stride] = make_float4(q.re23[c].x, q.re23[c].y, q.im23[c].x, q.im23[c].y);
+            st_hint<CS>(b + (size_t)(2 * c) * stride,
+                        make_float4(q.re01[c].x, q.re01[c].y, q.im01[c].x, q.im01[c].y));
+            st_hint<CS>(b + (size_t)(2 * c + 1) * stride,
+                        make_float4(q.re23[c].x, q.re23[c].y, q.im23[c].x, q.im23[c].y));
         }
     }
     template <bool COH = false>
@@ -264,10 +277,11 @@ struct SpinorFmt<P_F32> {
         load<COH>(base, stride, i, v);
         s = 1.0f;
     }
+    template <bool CS = false>
     __device__ static __forceinline__ void store(void* base, int stride, int i, const cpx<float> v[12]) {
         PSpinor q;
         pack_pairs(v, q);
-        store_packed(base, stride, i, q);
+        store_packed<CS>(base, stride, i, q);
     }
 };
 
@@ -304,6 +318,7 @@ struct SpinorLowFmt {
             q.im23[c] = LT::to_f2(d.w);
         }
     }
+    template <bool CS = false>
     __device__ static __forceinline__ void store_packed(void* base, int stride, int i, const PSpinor& q) {
         float m = 0.f;
 #pragma unroll
@@ -320,10 +335,10 @@ struct SpinorLowFmt {
             d.y = LT::from_f2(q.im01[c].x * inv, q.im01[c].y * inv);
             d.z = LT::from_f2(q.re23[c].x * inv, q.re23[c].y * inv);
             d.w = LT::from_f2(q.im23[c].x * inv, q.im23[c].y * inv);
-            b[(size_t)c * stride] = d;
+            st_hint<CS>(b + (size_t)c * stride, d);
         }
         float* sc = reinterpret_cast<float*>(static_cast<char*>(base) + 48LL * stride);
-        sc[i] = m;
+        st_hint<CS>(sc + i, m);
     }
     template <bool COH = false>
     __device__ static __forceinline__ void load_raw(const void* base, int stride, int i, cpx<float> v[12],
@@ -339,10 +354,11 @@ struct SpinorLowFmt {
 #pragma unroll
         for (int k = 0; k < 12; k++) v[k] = {v[k].re * s, v[k].im * s};
     }
+    template <bool CS = false>
     __device__ static __forceinline__ void store(void* base, int stride, int i, const cpx<float> v[12]) {
         PSpinor q;
         pack_pairs(v, q);
-        store_packed(base, stride, i, q);
+        store_packed<CS>(base, stride, i, q);
     }
 };
 template <>

@@ -236,7 +236,8 @@ __global__ void __launch_bounds__(256, MINB) hop_kernel(const HopParams P) {
             for (int k = 0; k < 12; k++) n2 += cnorm2(acc[k]);
             nrm += (double)n2;
         }
-        SF::store(out, g.stride, h, acc);
+        if (P.nrhs > 1) SF::template store<true>(out, g.stride, h, acc);
+        else SF::store(out, g.stride, h, acc);
     }
     if (P.reduce) grid_reduce(nrm, P.red, k, nb * gridDim.y, sb + nb * blockIdx.y);
 }
@@ -453,7 +454,8 @@ __global__ void __launch_bounds__(256, MINB) hop_kernel_p(const HopParams P) {
             }
             nrm += (double)n2.x + (double)n2.y;
         }
-        SF::store_packed(out, g.stride, h, acc);
+        if (P.nrhs > 1) SF::template store_packed<true>(out, g.stride, h, acc);
+        else SF::store_packed(out, g.stride, h, acc);
     }
     if (P.reduce) grid_reduce(nrm, P.red, k, nb * gridDim.y, sb + nb * blockIdx.y);
 }
@@ -591,7 +593,7 @@ __global__ void __launch_bounds__(256, MINB) hop_kernel_pm(const HopParams P) {
                 }
                 nrm[r] += (double)n2.x + (double)n2.y;
             }
-            if (act >> r & 1u) SF::store_packed(out + r * P.out_rstep, g.stride, h, A);
+            if (act >> r & 1u) SF::template store_packed<true>(out + r * P.out_rstep, g.stride, h, A);
         }
     }
     if (P.reduce) {
