@@ -215,8 +215,13 @@ int wilson_spinor_destroy(wilson_spinor* s);
 long long wilson_spinor_bytes(const wilson_spinor* s);
 
 /* canon: nrhs fields back to back, each V (full) or V/2 (half) canonical
- * spinors; host or device memory (host memory is staged through the
- * library's workspace; pinned host memory copies fastest). */
+ * spinors; host or device memory.  Device and page-locked (pinned) host
+ * memory: asynchronous and ordered on the stream, like cudaMemcpyAsync (an
+ * import's source must stay unchanged, and an export's destination unread,
+ * until the stream has been synchronized); host copies run on the library's
+ * own copy streams through its workspace, so that they overlap kernels
+ * already queued on the stream.  Pageable host memory: staged, and the call
+ * returns when it is done. */
 int wilson_spinor_import(wilson_spinor* s, const double* canon, void* stream);
 int wilson_spinor_export(const wilson_spinor* s, double* canon, void* stream);
 

@@ -91,6 +91,49 @@ Staging& staging() {
     return s;
 }
 
+// Staging for page-locked host memory, with its own copy streams, so that
+// the copies of one call overlap the kernels of another: an import's
+// host-to-device copy runs on copy_in while the caller's stream still
+// computes, and only the pack kernel waits for it; an export unpacks into
+// one of two buffers, copies out on copy_out, and orders the caller's stream
+// after the copy.  Events guard the buffers' reuse; nothing waits on the host.
+struct AsyncStaging {
+    std::mutex m;
+    int device = -1;
+    DevBuf in, out[2];
+    int next_out = 0;
+    cudaStream_t copy_in = nullptr, copy_out = nullptr;
+    cudaEvent_t in_free = nullptr, in_ready = nullptr, out_ready = nullptr, out_free[2] = {nullptr, nullptr};
+    // Set up on the current device the first time; false if another device
+    // owns it (the caller then takes the synchronous path).
+    bool bind() {
+        int dev = 0;
+        WL_CUDA(cudaGetDevice(&dev));
+        if (device >= 0) return device == dev;
+        WL_CUDA(cudaStreamCreateWithFlags(&copy_in, cudaStreamNonBlocking));
+        WL_CUDA(cudaStreamCreateWithFlags(&copy_out, cudaStreamNonBlocking));
+        for (cudaEvent_t* e : {&in_free, &in_ready, &out_ready, &out_free[0], &out_free[1]})
+            WL_CUDA(cudaEventCreateWithFlags(e, cudaEventDisableTiming));
+        // the "free" events start out complete
+        for (cudaEvent_t e : {in_free, out_free[0], out_free[1]}) WL_CUDA(cudaEventRecord(e, copy_in));
+        device = dev;
+        return true;
+    }
+};
+AsyncStaging& async_staging() {
+    static AsyncStaging s;
+    return s;
+}
+
+bool is_pinned_host(const void* p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeHost;
+}
+
 // Copy a canonical field to the device if it lives in host memory; returns a
 // device pointer valid until the next staging call on the stream.
 const double* device_view(const double* p, size_t bytes, DevBuf& tmp, cudaStream_t st) {
@@ -454,7 +497,24 @@ int wilson_spinor_import(wilson_spinor* s, const double* canon, void* stream) {
         const size_t per = sizeof(double) * 24 * (size_t)s->g.Vh * (s->f.subset == 2 ? 2 : 1);
         if (is_device_ptr(canon)) {
             for (int k = 0; k < s->f.nrhs; k++) pack_spinor(s->f, k, canon + (per / sizeof(double)) * k, st);
-        } else {
+            return;
+        }
+        AsyncStaging& as = async_staging();
+        std::unique_lock<std::mutex> lk(as.m);
+        if (is_pinned_host(canon) && as.bind()) {
+            const size_t bytes = per * s->f.nrhs;
+            as.in.ensure(bytes);
+            WL_CUDA(cudaStreamWaitEvent(as.copy_in, as.in_free, 0));  // the last pack is done with the buffer
+            WL_CUDA(cudaMemcpyAsync(as.in.p, canon, bytes, cudaMemcpyHostToDevice, as.copy_in));
+            WL_CUDA(cudaEventRecord(as.in_ready, as.copy_in));
+            WL_CUDA(cudaStreamWaitEvent(st, as.in_ready, 0));
+            for (int k = 0; k < s->f.nrhs; k++)
+                pack_spinor(s->f, k, as.in.as<const double>() + (per / sizeof(double)) * k, st);
+            WL_CUDA(cudaEventRecord(as.in_free, st));
+            return;
+        }
+        lk.unlock();
+        {
             Staging& sg = staging();
             std::lock_guard<std::mutex> lk(sg.m);
             sg.buf.ensure(per * s->f.nrhs);
@@ -475,7 +535,31 @@ int wilson_spinor_export(const wilson_spinor* s, double* canon, void* stream) {
         const size_t per = sizeof(double) * 24 * (size_t)s->g.Vh * (s->f.subset == 2 ? 2 : 1);
         if (is_device_ptr(canon)) {
             for (int k = 0; k < s->f.nrhs; k++) unpack_spinor(s->f, k, canon + (per / sizeof(double)) * k, st);
-        } else {
+            return;
+        }
+        AsyncStaging& as = async_staging();
+        std::unique_lock<std::mutex> lk(as.m);
+        if (is_pinned_host(canon) && as.bind()) {
+            const size_t bytes = per * s->f.nrhs;
+            const int i = as.next_out;
+            as.next_out ^= 1;
+            DevBuf& ob = as.out[i];
+            if (ob.bytes < bytes) {
+                WL_CUDA(cudaEventSynchronize(as.out_free[i]));  // the buffer is about to be replaced
+                ob.ensure(bytes);
+            }
+            WL_CUDA(cudaStreamWaitEvent(st, as.out_free[i], 0));  // its last copy-out is done
+            for (int k = 0; k < s->f.nrhs; k++)
+                unpack_spinor(s->f, k, ob.as<double>() + (per / sizeof(double)) * k, st);
+            WL_CUDA(cudaEventRecord(as.out_ready, st));
+            WL_CUDA(cudaStreamWaitEvent(as.copy_out, as.out_ready, 0));
+            WL_CUDA(cudaMemcpyAsync(canon, ob.p, bytes, cudaMemcpyDeviceToHost, as.copy_out));
+            WL_CUDA(cudaEventRecord(as.out_free[i], as.copy_out));
+            WL_CUDA(cudaStreamWaitEvent(st, as.out_free[i], 0));  // the caller's stream is ordered after the copy
+            return;
+        }
+        lk.unlock();
+        {
             Staging& sg = staging();
             std::lock_guard<std::mutex> lk(sg.m);
             sg.buf.ensure(per * s->f.nrhs);

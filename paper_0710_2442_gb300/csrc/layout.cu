@@ -89,26 +89,40 @@ __global__ void pack_spinor_kernel(const double2* __restrict__ canon, char* base
     }
 }
 
+// Each block converts its sites into shared memory and then writes their
+// canonical 192 bytes as one contiguous run (consecutive threads, consecutive
+// 16-byte words), instead of 12 strided stores per thread.
+constexpr int kUnpackBlock = 128;
+
 template <int SP>
-__global__ void unpack_spinor_kernel(double2* __restrict__ canon, const char* base, long long pbytes, int subset,
-                                     Geom g) {
+__global__ void __launch_bounds__(kUnpackBlock) unpack_spinor_kernel(double2* __restrict__ canon, const char* base,
+                                                                     long long pbytes, int subset, Geom g) {
     using SF = SpinorFmt<SP>;
     using T = typename SF::real;
+    __shared__ double2 stage[kUnpackBlock * 12];
     const long long n = subset == 2 ? 2LL * g.Vh : (long long)g.Vh;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-        int p = 0;
-        long long h = i;
-        if (subset == 2) {
-            int c[4];
-            site_coords_full(i, g, c);
-            p = (c[0] + c[1] + c[2] + c[3]) & 1;
-            h = i >> 1;
-        }
-        cpx<T> v[12];
-        SF::load(base + (subset == 2 ? p * pbytes : 0), g.stride, (int)h, v);
-        double2* dst = canon + i * 12;
+    // block-uniform trip count: every thread reaches both barriers
+    for (long long i0 = (long long)blockIdx.x * kUnpackBlock; i0 < n; i0 += (long long)gridDim.x * kUnpackBlock) {
+        const long long i = i0 + threadIdx.x;
+        if (i < n) {
+            int p = 0;
+            long long h = i;
+            if (subset == 2) {
+                int c[4];
+                site_coords_full(i, g, c);
+                p = (c[0] + c[1] + c[2] + c[3]) & 1;
+                h = i >> 1;
+            }
+            cpx<T> v[12];
+            SF::load(base + (subset == 2 ? p * pbytes : 0), g.stride, (int)h, v);
 #pragma unroll
-        for (int k = 0; k < 12; k++) dst[k] = make_double2((double)v[k].re, (double)v[k].im);
+            for (int k = 0; k < 12; k++) stage[threadIdx.x * 12 + k] = make_double2((double)v[k].re, (double)v[k].im);
+        }
+        __syncthreads();
+        const long long words = (n - i0 < kUnpackBlock ? n - i0 : kUnpackBlock) * 12;
+        double2* dst = canon + i0 * 12;
+        for (int e = threadIdx.x; e < words; e += kUnpackBlock) dst[e] = stage[e];
+        __syncthreads();
     }
 }
 
@@ -135,7 +149,7 @@ void pack_spinor(const SpinorField& f, int rhs, const double* canon, cudaStream_
 
 void unpack_spinor(const SpinorField& f, int rhs, double* canon, cudaStream_t st) {
     const long long n = f.subset == 2 ? 2LL * f.g.Vh : (long long)f.g.Vh;
-    const int block = 256, grid = grid_for(n, block);
+    const int block = kUnpackBlock, grid = grid_for(n, block);
     const char* base = static_cast<const char*>(f.block(f.subset == 2 ? 0 : f.subset, rhs));
     double2* dst = reinterpret_cast<double2*>(canon);
     switch (f.prec) {

@@ -262,9 +262,9 @@ def test_blocked_variant_lockstep_solve(w, oracle_mod, monkeypatch, variant):
 @pytest.mark.parametrize("prec", ["f64", "f32", "f16"])
 def test_import_export_host_memory(w, oracle_mod, prec):
     """Spinor import and export through device memory, page-locked host
-    memory (read and written by the pack kernels directly) and pageable host
-    memory (staged) give the same fields: bit-exact for FP64 handles, and the
-    same hop result whichever way the field came in."""
+    memory (asynchronous copies on the library's copy streams) and pageable
+    host memory (staged, synchronous) give the same fields: bit-exact for
+    FP64 handles, and the same hop result whichever way the field came in."""
     import torch
     dims = (6, 4, 6, 10)
     Vh = inputs.volume(dims) // 2
@@ -285,6 +285,7 @@ def test_import_export_host_memory(w, oracle_mod, prec):
         a.store(back)
         res = np.full_like(src, np.nan)
         b.store(res)
+        torch.cuda.synchronize()  # exports to page-locked memory are asynchronous on the stream
         back = host(back) if name == "device" else (back.numpy() if name == "pinned" else back)
         if prec == "f64":
             assert np.array_equal(back, src), name
