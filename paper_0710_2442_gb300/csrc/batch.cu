@@ -615,9 +615,12 @@ void batch_solve(int n, const wilson_problem* probs, const SolveParams& prm, wil
         if (!smallrun) return;
         WL_CUDA(cudaEventRecord(fork3, s));
         WL_CUDA(cudaStreamWaitEvent(st3, fork3, 0));
+        // a cluster of blocks per small problem unless WILSON_BATCH_SMALL_CLUSTER=1
+        bool cluster = true;
+        if (const char* e = std::getenv("WILSON_BATCH_SMALL_CLUSTER")) cluster = std::atoi(e) != 1;
         dispatch_low(ip, [&](auto I) {
-            launch_small_ip<decltype(I)::value>(smallrun->A, smallrun->ids.as<int>(), smallrun->G(), budget_ns,
-                                                smallrun->nprob, st3);
+            launch_small_ip<decltype(I)::value>(cluster, smallrun->A, smallrun->ids.as<int>(), smallrun->G(),
+                                                budget_ns, smallrun->nprob, st3);
         });
         WL_LAUNCH_CHECK();
         WL_CUDA(cudaEventRecord(join3, st3));

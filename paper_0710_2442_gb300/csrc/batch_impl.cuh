@@ -5,6 +5,8 @@
 // that they compile in parallel.
 #pragma once
 
+#include <cooperative_groups.h>
+
 #include "../../include/wilson.h"
 #include "dslash_impl.cuh"
 #include "solver.h"
@@ -312,16 +314,16 @@ __global__ void __launch_bounds__(256, MINB) bhop_kernel_p(const BatchArgs A, co
 }
 
 // ---------------------------------------------------------------------------
-// CTA-resident solve of a small problem.  The paper's first layout keeps a
-// whole iterative solver in the SPEs' local stores (Sec. 5, "Data in on-chip
-// memory"); the GB300 analogue for lattices of a few thousand sites is one
-// thread block that runs the complete solve (the same FP64-corrected CG as
-// the rest of the batch) on its own SM, with the problem's fields resident in
-// L1/L2 and block barriers in place of kernel boundaries: no launch per step,
-// no device-wide synchronisation, and the problem finishes on its own clock
-// instead of advancing in lockstep with the largest lattice of the batch.
-// Loads that may see data written earlier in the same launch use the
-// coherent path (COH = true).
+// Cluster-resident solve of a small problem.  The paper's first layout keeps
+// a whole iterative solver in the SPEs' local stores (Sec. 5, "Data in
+// on-chip memory"); the GB300 analogue for lattices of a few thousand sites
+// is a thread-block cluster (or one block) that runs the complete solve (the
+// same FP64-corrected CG as the rest of the batch) on its own SMs, with the
+// problem's fields resident in L2 and cluster barriers in place of kernel
+// boundaries: no launch per step, no device-wide synchronisation, and the
+// problem finishes on its own clock instead of advancing in lockstep with the
+// largest lattice of the batch.  Loads that may see data written earlier in
+// the same launch go to L2 (COH = true).
 // ---------------------------------------------------------------------------
 constexpr int kSmallThreads = 256;
 
@@ -335,11 +337,47 @@ __device__ inline double cta_sum(double v) {  // block-wide sum, valid in every 
     return r;
 }
 
-// out (parity p) = a * D in + x over the problem's sites; returns |out|^2.
-// Ends with a block barrier, so out is visible to the whole block.
-template <int SP, int GP, int R, bool DAG>
+// The barrier of a solve that runs on a cluster of CL thread blocks (one
+// block: __syncthreads).  The cluster barrier has release/acquire semantics,
+// so global writes before it are visible to the cluster's other blocks
+// after it (their loads of such data go to L2: COH loads).
+template <int CL>
+__device__ __forceinline__ void solve_sync() {
+    if constexpr (CL == 1) __syncthreads();
+    else cooperative_groups::this_cluster().sync();
+}
+
+// Sum over the solve's threads, the same value in every thread.  On a
+// cluster each block's sum is read by every block from the others' shared
+// memory (distributed shared memory) in rank order, so all blocks add the
+// same numbers in the same order and take the same decisions.
+template <int CL>
+__device__ inline double solve_sum(double v) {
+    if constexpr (CL == 1) {
+        return cta_sum(v);
+    } else {
+        namespace cg = cooperative_groups;
+        __shared__ double s_part, s_tot;
+        const double t = block_sum(v);
+        if (threadIdx.x == 0) s_part = t;
+        cg::cluster_group cl = cg::this_cluster();
+        cl.sync();
+        if (threadIdx.x == 0) {
+            double tot = 0.0;
+            for (int r = 0; r < CL; r++) tot += *cl.map_shared_rank(&s_part, r);
+            s_tot = tot;
+        }
+        cl.sync();  // every block has read s_part before it is written again
+        return s_tot;
+    }
+}
+
+// out (parity p) = a * D in + x over the problem's sites, thread tid of nt;
+// returns |out|^2.  Ends with the solve's barrier, so out is visible to all
+// of its threads.
+template <int SP, int GP, int R, bool DAG, int CL>
 __device__ double cta_hop(const Geom& g, const char* gauge, char* out, const char* in, const char* x, double a,
-                          int p) {
+                          int p, int tid, int nt) {
     using SF = SpinorFmt<SP>;
     using T = typename SF::real;
     HopParams P;
@@ -347,7 +385,7 @@ __device__ double cta_hop(const Geom& g, const char* gauge, char* out, const cha
     P.gauge = gauge;
     const T at = (T)a;
     double nrm = 0.0;
-    for (int h = threadIdx.x; h < g.Vh; h += blockDim.x) {
+    for (int h = tid; h < g.Vh; h += nt) {
         int c[4], s;
         site_of_half(h, p, g, c, s);
         cpx<T> acc[12];
@@ -373,15 +411,15 @@ __device__ double cta_hop(const Geom& g, const char* gauge, char* out, const cha
         nrm += (double)n2;
         SF::store(out, g.stride, h, acc);
     }
-    return cta_sum(nrm);
+    return solve_sum<CL>(nrm);
 }
 
-template <int IP>
-__global__ void __launch_bounds__(kSmallThreads, 1) small_solve_kernel(const BatchArgs A, const int* ids,
-                                                                       const BatchGlobal* G,
-                                                                       unsigned long long budget_ns) {
+// The whole solve of problem ids[blockIdx.x / CL], on CL blocks.
+template <int IP, int CL>
+__device__ __forceinline__ void small_solve_body(const BatchArgs& A, const int* ids, const BatchGlobal* G,
+                                                 unsigned long long budget_ns) {
     using TI = typename SpinorFmt<IP>::real;
-    const int pid = ids[blockIdx.x];
+    const int pid = ids[blockIdx.x / CL];
     const BatchProb& Pr = A.probs[pid];
     BatchState& S = A.state[pid];
     const Geom g = Pr.g;
@@ -391,7 +429,9 @@ __global__ void __launch_bounds__(kSmallThreads, 1) small_solve_kernel(const Bat
     const char* b_o = f[BF_B] + Pr.fp[BF_B];
     char* x_e = f[BF_X];
     char* x_o = f[BF_X] + Pr.fp[BF_X];
-    const int tid = threadIdx.x, nt = blockDim.x;
+    const int tid = (int)(blockIdx.x % CL) * (int)blockDim.x + (int)threadIdx.x, nt = CL * (int)blockDim.x;
+    // the wall-clock budget, decided the same way in every block of the solve
+    auto late = [&]() { return solve_sum<CL>(globaltimer() - G->t_start > budget_ns ? 1.0 : 0.0) > 0.0; };
 
     // set-up: zeroed iterates, |b|^2, bhat_e = b_e + kappa D_eo b_o
     for (int h = tid; h < g.Vh; h += nt) {
@@ -416,8 +456,8 @@ __global__ void __launch_bounds__(kSmallThreads, 1) small_solve_kernel(const Bat
 #pragma unroll
         for (int k = 0; k < 12; k++) nb += cnorm2(v[k]) + cnorm2(w[k]);
     }
-    const double bnorm2 = cta_sum(nb);
-    cta_hop<P_F64, P_F64, 18, false>(g, Pr.g64, f[BF_BHAT], b_o, b_e, kappa, 0);
+    const double bnorm2 = solve_sum<CL>(nb);
+    cta_hop<P_F64, P_F64, 18, false, CL>(g, Pr.g64, f[BF_BHAT], b_o, b_e, kappa, 0, tid, nt);
     const double target2 = Pr.tol * Pr.tol * bnorm2;
 
     int iter = 0, outer = 0, status = 0;
@@ -437,9 +477,9 @@ __global__ void __launch_bounds__(kSmallThreads, 1) small_solve_kernel(const Bat
             }
             SpinorFmt<P_F64>::store(x_e, g.stride, h, xv);
         }
-        __syncthreads();
-        cta_hop<P_F64, P_F64, 18, false>(g, Pr.g64, f[BF_T64], x_e, nullptr, 1.0, 1);
-        cta_hop<P_F64, P_F64, 18, false>(g, Pr.g64, f[BF_Q64], f[BF_T64], x_e, -k2, 0);
+        solve_sync<CL>();
+        cta_hop<P_F64, P_F64, 18, false, CL>(g, Pr.g64, f[BF_T64], x_e, nullptr, 1.0, 1, tid, nt);
+        cta_hop<P_F64, P_F64, 18, false, CL>(g, Pr.g64, f[BF_Q64], f[BF_T64], x_e, -k2, 0, tid, nt);
         double rn = 0.0;
         for (int h = tid; h < g.Vh; h += nt) {
             cpx<double> bv[12], qv[12];
@@ -461,7 +501,7 @@ __global__ void __launch_bounds__(kSmallThreads, 1) small_solve_kernel(const Bat
             SpinorFmt<IP>::store(f[BF_SLOW], g.stride, h, lv);
             SpinorFmt<P_F32>::store(f[BF_XIN], g.stride, h, z32);
         }
-        const double rn2 = cta_sum(rn);
+        const double rn2 = solve_sum<CL>(rn);
         if (!isfinite(rn2)) { status = WILSON_ERR_NUMERIC; break; }
         if (rn2 <= target2) break;
         if (outer >= Pr.max_outer || iter >= Pr.maxiter || rn2 > kDivergence * kDivergence * best2) {
@@ -469,11 +509,11 @@ __global__ void __launch_bounds__(kSmallThreads, 1) small_solve_kernel(const Bat
             break;
         }
         best2 = fmin(best2, rn2);
-        if (globaltimer() - G->t_start > budget_ns) { status = WILSON_ERR_TIMEOUT; break; }
+        if (late()) { status = WILSON_ERR_TIMEOUT; break; }
         outer++;
         // r' = Mhat'^dag s; p = r' + beta p (beta = 0 at the start)
-        cta_hop<IP, IP, 12, true>(g, Pr.glo, f[BF_T], f[BF_SLOW], nullptr, 1.0, 1);
-        const double rr0 = cta_hop<IP, IP, 12, true>(g, Pr.glo, f[BF_R], f[BF_T], f[BF_SLOW], -k2, 0);
+        cta_hop<IP, IP, 12, true, CL>(g, Pr.glo, f[BF_T], f[BF_SLOW], nullptr, 1.0, 1, tid, nt);
+        const double rr0 = cta_hop<IP, IP, 12, true, CL>(g, Pr.glo, f[BF_R], f[BF_T], f[BF_SLOW], -k2, 0, tid, nt);
         if (!isfinite(rr0)) { status = WILSON_ERR_NUMERIC; break; }
         double beta = (first || !(gam > 0.0)) ? 0.0 : rr0 / gam;
         gam = rr0;
@@ -493,9 +533,9 @@ __global__ void __launch_bounds__(kSmallThreads, 1) small_solve_kernel(const Bat
                 }
                 SpinorFmt<IP>::store(f[BF_P], g.stride, h, pv);
             }
-            __syncthreads();
-            cta_hop<IP, IP, 12, false>(g, Pr.glo, f[BF_T], f[BF_P], nullptr, 1.0, 1);
-            const double pq = cta_hop<IP, IP, 12, false>(g, Pr.glo, f[BF_Q], f[BF_T], f[BF_P], -k2, 0);
+            solve_sync<CL>();
+            cta_hop<IP, IP, 12, false, CL>(g, Pr.glo, f[BF_T], f[BF_P], nullptr, 1.0, 1, tid, nt);
+            const double pq = cta_hop<IP, IP, 12, false, CL>(g, Pr.glo, f[BF_Q], f[BF_T], f[BF_P], -k2, 0, tid, nt);
             if (!isfinite(pq)) { status = WILSON_ERR_NUMERIC; break; }
             if (!(pq > 0.0)) break;
             const float alpha = (float)(gam / pq);
@@ -522,13 +562,13 @@ __global__ void __launch_bounds__(kSmallThreads, 1) small_solve_kernel(const Bat
                 SpinorFmt<P_F32>::store(f[BF_S], g.stride, h, sv);
                 SpinorFmt<IP>::store(f[BF_SLOW], g.stride, h, lv);
             }
-            const double ss = cta_sum(sn);
+            const double ss = solve_sum<CL>(sn);
             iter++;
             if (!isfinite(ss)) { status = WILSON_ERR_NUMERIC; break; }
             if (ss <= stop2 || iter >= iter_cap) break;
-            if ((iter & 15) == 0 && globaltimer() - G->t_start > budget_ns) break;
-            cta_hop<IP, IP, 12, true>(g, Pr.glo, f[BF_T], f[BF_SLOW], nullptr, 1.0, 1);
-            const double rr = cta_hop<IP, IP, 12, true>(g, Pr.glo, f[BF_R], f[BF_T], f[BF_SLOW], -k2, 0);
+            if ((iter & 15) == 0 && late()) break;
+            cta_hop<IP, IP, 12, true, CL>(g, Pr.glo, f[BF_T], f[BF_SLOW], nullptr, 1.0, 1, tid, nt);
+            const double rr = cta_hop<IP, IP, 12, true, CL>(g, Pr.glo, f[BF_R], f[BF_T], f[BF_SLOW], -k2, 0, tid, nt);
             if (!isfinite(rr)) { status = WILSON_ERR_NUMERIC; break; }
             beta = gam > 0.0 ? rr / gam : 0.0;
             gam = rr;
@@ -536,9 +576,9 @@ __global__ void __launch_bounds__(kSmallThreads, 1) small_solve_kernel(const Bat
         if (status) break;
     }
     // x_o = b_o + kappa D_oe x_e; true residual |b - M x|^2 over both parities
-    cta_hop<P_F64, P_F64, 18, false>(g, Pr.g64, x_o, x_e, b_o, kappa, 1);
-    cta_hop<P_F64, P_F64, 18, false>(g, Pr.g64, f[BF_Q64], x_o, x_e, -kappa, 0);
-    cta_hop<P_F64, P_F64, 18, false>(g, Pr.g64, f[BF_T64], x_e, x_o, -kappa, 1);
+    cta_hop<P_F64, P_F64, 18, false, CL>(g, Pr.g64, x_o, x_e, b_o, kappa, 1, tid, nt);
+    cta_hop<P_F64, P_F64, 18, false, CL>(g, Pr.g64, f[BF_Q64], x_o, x_e, -kappa, 0, tid, nt);
+    cta_hop<P_F64, P_F64, 18, false, CL>(g, Pr.g64, f[BF_T64], x_e, x_o, -kappa, 1, tid, nt);
     double rs = 0.0;
     for (int h = tid; h < g.Vh; h += nt) {
         cpx<double> a[12], m[12];
@@ -551,7 +591,7 @@ __global__ void __launch_bounds__(kSmallThreads, 1) small_solve_kernel(const Bat
 #pragma unroll
         for (int k = 0; k < 12; k++) rs += cnorm2(csub(a[k], m[k]));
     }
-    const double res2 = cta_sum(rs);
+    const double res2 = solve_sum<CL>(rs);
     if (tid == 0) {
         S.sc.iter = iter;
         S.outer = outer;
@@ -561,6 +601,24 @@ __global__ void __launch_bounds__(kSmallThreads, 1) small_solve_kernel(const Bat
         S.t_done = globaltimer();
         S.phase = S.next_phase = PH_DONE;
     }
+}
+
+// One block per small problem, or a cluster of kSmallCluster blocks on as
+// many SMs (the solve's parallel width grows, its barriers become cluster
+// barriers and its sums go through distributed shared memory).
+constexpr int kSmallCluster = 4;
+
+template <int IP>
+__global__ void __launch_bounds__(kSmallThreads, 1) small_solve_kernel(const BatchArgs A, const int* ids,
+                                                                       const BatchGlobal* G,
+                                                                       unsigned long long budget_ns) {
+    small_solve_body<IP, 1>(A, ids, G, budget_ns);
+}
+
+template <int IP>
+__global__ void __cluster_dims__(kSmallCluster, 1, 1) __launch_bounds__(kSmallThreads, 1)
+    small_solve_cluster_kernel(const BatchArgs A, const int* ids, const BatchGlobal* G, unsigned long long budget_ns) {
+    small_solve_body<IP, kSmallCluster>(A, ids, G, budget_ns);
 }
 
 // ---------------------------------------------------------------------------
@@ -596,17 +654,19 @@ extern template void launch_bhop<P_F64, P_F64>(const BatchArgs&, const BOp&, int
 // precision IP.  Instantiated one inner precision per translation unit
 // (batch_small_*.cu).
 template <int IP>
-void launch_small_ip(const BatchArgs& A, const int* ids, const BatchGlobal* G, unsigned long long budget_ns,
-                     int nprob, cudaStream_t st) {
-    small_solve_kernel<IP><<<nprob, kSmallThreads, 0, st>>>(A, ids, G, budget_ns);
+void launch_small_ip(bool cluster, const BatchArgs& A, const int* ids, const BatchGlobal* G,
+                     unsigned long long budget_ns, int nprob, cudaStream_t st) {
+    if (cluster)
+        small_solve_cluster_kernel<IP><<<nprob * kSmallCluster, kSmallThreads, 0, st>>>(A, ids, G, budget_ns);
+    else small_solve_kernel<IP><<<nprob, kSmallThreads, 0, st>>>(A, ids, G, budget_ns);
 }
 
-extern template void launch_small_ip<P_F32>(const BatchArgs&, const int*, const BatchGlobal*, unsigned long long,
-                                            int, cudaStream_t);
-extern template void launch_small_ip<P_F16>(const BatchArgs&, const int*, const BatchGlobal*, unsigned long long,
-                                            int, cudaStream_t);
-extern template void launch_small_ip<P_BF16>(const BatchArgs&, const int*, const BatchGlobal*, unsigned long long,
-                                             int, cudaStream_t);
+extern template void launch_small_ip<P_F32>(bool, const BatchArgs&, const int*, const BatchGlobal*,
+                                            unsigned long long, int, cudaStream_t);
+extern template void launch_small_ip<P_F16>(bool, const BatchArgs&, const int*, const BatchGlobal*,
+                                            unsigned long long, int, cudaStream_t);
+extern template void launch_small_ip<P_BF16>(bool, const BatchArgs&, const int*, const BatchGlobal*,
+                                             unsigned long long, int, cudaStream_t);
 
 }  // namespace bt
 }  // namespace wl

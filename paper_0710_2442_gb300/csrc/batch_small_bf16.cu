@@ -4,7 +4,7 @@
 
 namespace wl {
 namespace bt {
-template void launch_small_ip<P_BF16>(const BatchArgs&, const int*, const BatchGlobal*, unsigned long long, int,
-                                   cudaStream_t);
+template void launch_small_ip<P_BF16>(bool, const BatchArgs&, const int*, const BatchGlobal*, unsigned long long,
+                                   int, cudaStream_t);
 }  // namespace bt
 }  // namespace wl

@@ -113,11 +113,13 @@ __device__ __forceinline__ void site_of_half(int h, int p, const Geom& g, int c[
 }
 
 // Read-only loads go through the non-coherent path (__ldg) by default.  A
-// kernel that reads data it wrote itself earlier in the same launch (the
-// CTA-resident solver) instantiates the loads with COH = true: plain loads.
+// kernel that reads data written earlier in the same launch, possibly by
+// another block of its cluster on another SM (the CTA-resident solver),
+// instantiates the loads with COH = true: loads from L2 (__ldcg), which the
+// other SMs' writes have reached after the cluster barrier.
 template <bool COH, class T>
 __device__ __forceinline__ T ldro(const T* p) {
-    if constexpr (COH) return *p;
+    if constexpr (COH) return __ldcg(p);
     else return __ldg(p);
 }
 

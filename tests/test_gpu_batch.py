@@ -166,3 +166,19 @@ def test_batch_single_and_degenerate_problems(w, oracle_mod, monkeypatch, small_
     dims, U, b, kappa = hf[1]
     assert true_resid(oracle_mod, U, host(probs[1]["x"]), b, dims, kappa) <= 1.1e-10
     assert np.all(host(probs[2]["x"]) == 0)
+
+
+@pytest.mark.parametrize("cluster", ["1", "4"])
+@pytest.mark.parametrize("inner", ["f16", "f32"])
+def test_small_path_block_and_cluster(w, oracle_mod, monkeypatch, cluster, inner):
+    """The CTA-resident solves on one thread block per problem and on a
+    cluster of four blocks (cluster barriers, sums through distributed shared
+    memory) both reach the target against the oracle."""
+    monkeypatch.setenv("WILSON_BATCH_SMALL_VH", "4096")
+    monkeypatch.setenv("WILSON_BATCH_SMALL_CLUSTER", cluster)
+    probs, hf = make_batch(w, MIX, seed0=530)
+    rc, st, info = w.wilson_batch_solve(probs, w.solver_defaults(w.PREC[inner]))
+    assert rc == 0 and info["tiles"] == 0
+    for q, (dims, U, b, kappa), s in zip(probs, hf, st):
+        assert s["status"] == 0
+        assert true_resid(oracle_mod, U, host(q["x"]), b, dims, kappa) <= 1.1e-10
