@@ -54,6 +54,8 @@ def parse():
                     help="skip the solver, multi-RHS and batch blocks (CG time-to-solution comparisons)")
     ap.add_argument("--blocks", default="cg,multirhs,batch",
                     help="solver blocks to run after the headline (comma list of cg, multirhs, batch)")
+    ap.add_argument("--cg-prec", default="f64,f16,bf16,f32",
+                    help="inner precisions of the cg block's solves (comma list; f64 = plain FP64 CG)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--apps", type=int, default=None, help="applications per step (default 100)")
     ap.add_argument("--prec", choices=["f32", "f16", "bf16", "f64"], default="f32",
@@ -275,7 +277,7 @@ def run_ours(args, ws, rank, local, fields):
     if rank == 0 and not args.no_solver:
         blocks = {b.strip() for b in args.blocks.split(",")}
         if "cg" in blocks:
-            line["cg"] = run_solver_block(w, torch, dev, stream)
+            line["cg"] = run_solver_block(w, torch, dev, stream, args.cg_prec.split(","))
         if "multirhs" in blocks:
             line["multirhs"] = run_multirhs_block(w, torch, dev, stream, fields)
         if "batch" in blocks:
@@ -283,7 +285,7 @@ def run_ours(args, ws, rank, local, fields):
     return line
 
 
-def run_solver_block(w, torch, dev, stream):
+def run_solver_block(w, torch, dev, stream, precs):
     cfg = inputs.WORKLOADS["cg_mixed_24^3x48"]
     dims = cfg["dims"]
     U = inputs.gauge_field(dims, cfg["gauge"], eps=cfg["eps"], seed=cfg["gauge_seed"])
@@ -294,6 +296,8 @@ def run_solver_block(w, torch, dev, stream):
     res = {"workload": "cg_mixed_24^3x48", "kappa": cfg["kappa"], "tol": cfg["tol"]}
     for name, prec in (("f64", w.WILSON_F64), ("f16", w.WILSON_F16), ("bf16", w.WILSON_BF16),
                        ("f32", w.WILSON_F32)):
+        if name not in precs:
+            continue
         x = torch.zeros_like(bd)
         p = w.solver_defaults(prec)
         # the first solve tunes the launch configurations; time the second
@@ -303,7 +307,7 @@ def run_solver_block(w, torch, dev, stream):
         res[name] = {"seconds": round(st["seconds"], 4), "inner_iters": st["inner_iters"],
                      "outer_iters": st["outer_iters"], "hops": st["hop_applications"],
                      "true_rel_resid": st["true_rel_resid"], "rc": st["rc"]}
-    if res["f64"]["rc"] == 0 and res["f16"]["rc"] == 0:
+    if res.get("f64", {}).get("rc") == 0 and res.get("f16", {}).get("rc") == 0:
         res["speedup_f16_vs_f64"] = round(res["f64"]["seconds"] / res["f16"]["seconds"], 3)
     return res
 
@@ -472,7 +476,8 @@ def oracle_solver_baselines(line):
         out["cg_24^3x48_fp64"] = {
             "seconds_per_iteration": round(per_it["24x24x24x48"], 4), "iterations": gpu["inner_iters"],
             "seconds_extrapolated": round(per_it["24x24x24x48"] * gpu["inner_iters"], 2),
-            "gpu_fp64_seconds": gpu["seconds"], "gpu_f16_mixed_seconds": line["cg"]["f16"]["seconds"]}
+            "gpu_fp64_seconds": gpu["seconds"],
+            "gpu_f16_mixed_seconds": line["cg"].get("f16", {}).get("seconds")}
     batch = line.get("batch", {}).get("latency_by_lattice")
     if batch:
         total = 0.0

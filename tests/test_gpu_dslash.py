@@ -2,7 +2,8 @@
 element, through the C ABI.
 
 Tolerances (relative L2 over the whole output): 1e-13 for FP64 fields,
-1e-6 for FP32, 5e-3 for FP16 / BF16 storage.  Sizes span several 128-site
+1e-6 for FP32, 5e-3 for FP16 / BF16 storage; every component must also lie
+within 10x that tolerance times the RMS modulus of the oracle's output.  Sizes span several 128-site
 blocks with a ragged tail (Vh not a multiple of the block size) plus the
 8^4 random-SU(3) lattice of the FP64 workload and the 32^3 x 64 weak-field
 lattice of the FP32 even-odd workload.
@@ -10,7 +11,7 @@ lattice of the FP32 even-odd workload.
 import numpy as np
 import pytest
 
-from conftest import parity_merge, parity_split, rel_l2
+from conftest import assert_parity, parity_merge, parity_split
 from gpu_helpers import dev, empty_like_dev, handle_hop, host
 from paper_0710_2442_gb300 import inputs
 
@@ -40,7 +41,7 @@ def test_f64_full_dslash(w, oracle_mod, dims, op):
     got = host(out)
     want = oracle_mod.dslash(U, psi, dims, CPLX_PHASES) if op == "hop" else \
         oracle_mod.wilson_m(U, psi, dims, kappa, CPLX_PHASES)
-    assert rel_l2(got, want) <= TOL["f64"]
+    assert_parity(got, want, TOL["f64"])
 
 
 def test_f64_config_8x8x8x8_default_phases(w, oracle_mod):
@@ -54,7 +55,7 @@ def test_f64_config_8x8x8x8_default_phases(w, oracle_mod):
         w.wilson_dslash(out, dev(U), dev(psi), L, cfg["kappa"], op)
         want = oracle_mod.wilson_m(U, psi, dims, cfg["kappa"]) if op == w.WILSON_OP_M else \
             oracle_mod.dslash(U, psi, dims)
-        assert rel_l2(host(out), want) <= TOL["f64"]
+        assert_parity(host(out), want, TOL["f64"])
 
 
 @pytest.mark.parametrize("dims", SHAPES)
@@ -66,7 +67,7 @@ def test_f64_eo_hop(w, oracle_mod, dims, out_parity):
     out = empty_like_dev(src)
     w.wilson_dslash_eo(out, dev(U), dev(src), L, out_parity, 0.0, w.WILSON_OP_HOP)
     want = oracle_mod.dslash_eo(U, src, dims, out_parity, CPLX_PHASES)
-    assert rel_l2(host(out), want) <= TOL["f64"]
+    assert_parity(host(out), want, TOL["f64"])
 
 
 @pytest.mark.parametrize("dims", [(4, 4, 4, 4), (6, 4, 6, 10), (2, 2, 2, 4)])
@@ -81,7 +82,7 @@ def test_f64_schur(w, oracle_mod, dims, parity, dag):
     w.wilson_dslash_eo(out, dev(U), dev(src), L, parity, kappa,
                        w.WILSON_OP_SCHUR_DAG if dag else w.WILSON_OP_SCHUR)
     want = oracle_mod.schur(U, src, dims, kappa, parity, dag, CPLX_PHASES)
-    assert rel_l2(host(out), want) <= TOL["f64"]
+    assert_parity(host(out), want, TOL["f64"])
 
 
 LOWP = [("f64", 18), ("f64", 12), ("f32", 12), ("f32", 18), ("f16", 12), ("bf16", 12), ("f16", 18), ("bf16", 18)]
@@ -96,7 +97,7 @@ def test_handle_eo_hop(w, oracle_mod, prec, recon, dims, out_parity):
     got = handle_hop(w, U, src, dims, CPLX_PHASES, w.PREC[prec], recon, 1 - out_parity, out_parity,
                      w.WILSON_OP_HOP)
     want = oracle_mod.dslash_eo(U, src, dims, out_parity, CPLX_PHASES)
-    assert rel_l2(got, want) <= TOL[prec]
+    assert_parity(got, want, TOL[prec])
 
 
 @pytest.mark.parametrize("prec,recon", LOWP)
@@ -110,7 +111,7 @@ def test_handle_full(w, oracle_mod, prec, recon, op):
                      w.WILSON_OP_HOP if op == "hop" else w.WILSON_OP_M, kappa)
     want = oracle_mod.dslash(U, psi, dims, CPLX_PHASES) if op == "hop" else \
         oracle_mod.wilson_m(U, psi, dims, kappa, CPLX_PHASES)
-    assert rel_l2(got, want) <= TOL[prec]
+    assert_parity(got, want, TOL[prec])
 
 
 def test_handle_multi_rhs_fields(w, oracle_mod):
@@ -122,7 +123,7 @@ def test_handle_multi_rhs_fields(w, oracle_mod):
     got = handle_hop(w, U, src, dims, CPLX_PHASES, w.WILSON_F32, 12, 1, 0, w.WILSON_OP_HOP, nrhs=3)
     for k in range(3):
         want = oracle_mod.dslash_eo(U, src[k], dims, 0, CPLX_PHASES)
-        assert rel_l2(got[k], want) <= TOL["f32"]
+        assert_parity(got[k], want, TOL["f32"])
 
 
 def test_f32_eo_workload_32x32x32x64(w, oracle_mod):
@@ -135,7 +136,7 @@ def test_f32_eo_workload_32x32x32x64(w, oracle_mod):
     src = src.astype(np.complex128)  # the workload's spinor is complex64 data
     got = handle_hop(w, U, src, dims, inputs.DEFAULT_PHASES, w.WILSON_F32, 12, 0, 1, w.WILSON_OP_HOP)
     want = oracle_mod.dslash_eo(U, src, dims, 1)
-    assert rel_l2(got, want) <= TOL["f32"]
+    assert_parity(got, want, TOL["f32"])
 
 
 def test_nan_sentinels_overwritten(w):
@@ -168,7 +169,7 @@ def test_handle_schur(w, oracle_mod, prec, recon, dag):
                      w.WILSON_OP_SCHUR_DAG if dag else w.WILSON_OP_SCHUR, kappa, nrhs=2)
     for k in range(2):
         want = oracle_mod.schur(U, src[k], dims, kappa, 0, dag, CPLX_PHASES)
-        assert rel_l2(got[k], want) <= TOL[prec]
+        assert_parity(got[k], want, TOL[prec])
 
 
 # Every kernel variant (register budgets 0-2 of the scalar stencil, 3-5 of the
@@ -184,15 +185,15 @@ def test_every_variant_eo_and_schur(w, oracle_mod, monkeypatch, variant, prec, r
     src = inputs.gaussian_spinor(inputs.volume(dims) // 2, seed=119, nrhs=2)
     got = handle_hop(w, U, src, dims, CPLX_PHASES, w.PREC[prec], recon, 1, 0, w.WILSON_OP_HOP, nrhs=2)
     for k in range(2):
-        assert rel_l2(got[k], oracle_mod.dslash_eo(U, src[k], dims, 0, CPLX_PHASES)) <= TOL[prec]
+        assert_parity(got[k], oracle_mod.dslash_eo(U, src[k], dims, 0, CPLX_PHASES), TOL[prec])
     got = handle_hop(w, U, src, dims, CPLX_PHASES, w.PREC[prec], recon, 1, 1, w.WILSON_OP_SCHUR_DAG, 0.1350,
                      nrhs=2)
     for k in range(2):
-        assert rel_l2(got[k], oracle_mod.schur(U, src[k], dims, 0.1350, 1, True, CPLX_PHASES)) <= TOL[prec]
+        assert_parity(got[k], oracle_mod.schur(U, src[k], dims, 0.1350, 1, True, CPLX_PHASES), TOL[prec])
     psi = inputs.gaussian_spinor(dims, seed=120)
     got = handle_hop(w, U, psi, dims, CPLX_PHASES, w.PREC[prec], recon, w.WILSON_FULL, w.WILSON_FULL,
                      w.WILSON_OP_M, 0.1350)
-    assert rel_l2(got, oracle_mod.wilson_m(U, psi, dims, 0.1350, CPLX_PHASES)) <= TOL[prec]
+    assert_parity(got, oracle_mod.wilson_m(U, psi, dims, 0.1350, CPLX_PHASES), TOL[prec])
 
 
 @pytest.mark.parametrize("variant", [0, 3])
@@ -222,16 +223,16 @@ def test_blocked_multi_rhs_variants(w, oracle_mod, monkeypatch, variant, prec):
     src[5] *= 1e-3  # right-hand sides of different magnitudes (F16 per-site scales)
     got = handle_hop(w, U, src, dims, CPLX_PHASES, w.PREC[prec], 12, 1, 0, w.WILSON_OP_HOP, nrhs=12)
     for k in range(12):
-        assert rel_l2(got[k], oracle_mod.dslash_eo(U, src[k], dims, 0, CPLX_PHASES)) <= TOL[prec]
+        assert_parity(got[k], oracle_mod.dslash_eo(U, src[k], dims, 0, CPLX_PHASES), TOL[prec])
     got = handle_hop(w, U, src, dims, CPLX_PHASES, w.PREC[prec], 12, 1, 1, w.WILSON_OP_SCHUR_DAG, 0.1350,
                      nrhs=12)
     for k in range(12):
-        assert rel_l2(got[k], oracle_mod.schur(U, src[k], dims, 0.1350, 1, True, CPLX_PHASES)) <= TOL[prec]
+        assert_parity(got[k], oracle_mod.schur(U, src[k], dims, 0.1350, 1, True, CPLX_PHASES), TOL[prec])
     psi = inputs.gaussian_spinor(dims, seed=125, nrhs=12)
     got = handle_hop(w, U, psi, dims, CPLX_PHASES, w.PREC[prec], 12, w.WILSON_FULL, w.WILSON_FULL,
                      w.WILSON_OP_M, 0.1350, nrhs=12)
     for k in range(12):
-        assert rel_l2(got[k], oracle_mod.wilson_m(U, psi[k], dims, 0.1350, CPLX_PHASES)) <= TOL[prec]
+        assert_parity(got[k], oracle_mod.wilson_m(U, psi[k], dims, 0.1350, CPLX_PHASES), TOL[prec])
 
 
 @pytest.mark.parametrize("variant", [6, 8, 9])
@@ -290,11 +291,11 @@ def test_import_export_host_memory(w, oracle_mod, prec):
         if prec == "f64":
             assert np.array_equal(back, src), name
         else:
-            assert rel_l2(back, src) <= TOL[prec], name
+            assert_parity(back, src, TOL[prec], name)
         outs[name] = res
         a.close(); b.close()
     g.close()
     for name in ("pinned", "pageable"):
         assert np.array_equal(outs[name], outs["device"]), name
     for k in range(2):
-        assert rel_l2(outs["device"][k], oracle_mod.dslash_eo(U, src[k], dims, 0, CPLX_PHASES)) <= TOL[prec]
+        assert_parity(outs["device"][k], oracle_mod.dslash_eo(U, src[k], dims, 0, CPLX_PHASES), TOL[prec])

@@ -11,7 +11,7 @@ This file is collected last on purpose.
 import numpy as np
 import pytest
 
-from conftest import rel_l2
+from conftest import assert_parity
 from gpu_helpers import dev, empty_like_dev, host
 from paper_0710_2442_gb300 import inputs
 
@@ -47,7 +47,7 @@ def test_noalloc_matches_allocating_call_twice(w):
         torch.cuda.synchronize()
         got = host(out)
         want = reference(w, U, src, L, parity, kappa, op)
-        assert rel_l2(got, want) <= 1e-13
+        assert_parity(got, want, 1e-13)
 
 
 def test_noalloc_small_lattice_and_dagger(w):
@@ -61,7 +61,7 @@ def test_noalloc_small_lattice_and_dagger(w):
         out = empty_like_dev(np.zeros((Vh, 4, 3)))
         w.wilson_dslash_eo_noalloc(out, U, src, L, 1, 0.125, op)
         torch.cuda.synchronize()
-        assert rel_l2(host(out), reference(w, U, src, L, 1, 0.125, op)) <= 1e-13
+        assert_parity(host(out), reference(w, U, src, L, 1, 0.125, op), 1e-13)
 
 
 def test_noalloc_rejects_lattice_beyond_scratch(w):
