@@ -248,7 +248,7 @@ def run_ours(args, ws, rank, local, fields):
     t_e2e = max_over_ranks(time.perf_counter() - t0, ws)
     e2e = {"value": round(flops * apps * e2e_steps * ws / t_e2e / 1e9, 2), "unit": "GFlop/s",
            "h2d_bytes_per_step": int(host_in.numel() * 16), "d2h_bytes_per_step": int(host_out.numel() * 16),
-           "steps": e2e_steps, "api": "wilson_spinor_import(host) + 100 x wilson_dslash_h + wilson_spinor_export(host)"}
+           "steps": e2e_steps, "api": f"wilson_spinor_import(host) + {apps} x wilson_dslash_h + wilson_spinor_export(host)"}
     del src_dev
     for h in (even, odd, g):
         h.close()
