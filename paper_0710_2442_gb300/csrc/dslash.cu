@@ -101,6 +101,7 @@ void launch_hop(const HopLaunch& L, cudaStream_t st) {
         });
     }
     WL_REQUIRE(hop_variant_valid(cfg.variant, sp, R, P.nrhs), "hop variant does not fit this launch");
+    if (L.tune_only) return;
     if (L.red) {
         P.reduce = 1;
         P.red = *L.red;

@@ -164,6 +164,7 @@ struct HopLaunch {
     int block;             // threads per block (0 = autotuned)
     int variant;           // kernel register-budget variant when block > 0
     int grid_cap;          // max blocks of a reducing launch (0 = no cap)
+    int tune_only;         // 1: tune the launch configuration if it is not known yet, launch nothing else
 };
 void launch_hop(const HopLaunch& L, cudaStream_t st);
 int hop_grid_blocks(const Geom& g, int block, int grid_cap);

@@ -47,9 +47,13 @@
 
 namespace wl {
 
-void schur_apply(const GaugeField& gf, Prec sp, Vec out, Vec in, Vec tmp, int nrhs, double kappa, int dag,
-                 const RedArgs* red, const int* skip, int skip_stride, int grid_cap, cudaStream_t st) {
+namespace {
+
+void schur_launch(const GaugeField& gf, Prec sp, Vec out, Vec in, Vec tmp, int nrhs, double kappa, int dag,
+                  const RedArgs* red, const int* skip, int skip_stride, int grid_cap, bool tune_only,
+                  cudaStream_t st) {
     HopLaunch a{};
+    a.tune_only = tune_only;
     a.out = tmp.p;
     a.in = in.p;
     a.nrhs = nrhs;
@@ -64,6 +68,7 @@ void schur_apply(const GaugeField& gf, Prec sp, Vec out, Vec in, Vec tmp, int nr
     a.skip_stride = skip_stride;
     launch_hop(a, st);
     HopLaunch b{};
+    b.tune_only = tune_only;
     b.out = out.p;
     b.in = tmp.p;
     b.x = in.p;
@@ -82,6 +87,17 @@ void schur_apply(const GaugeField& gf, Prec sp, Vec out, Vec in, Vec tmp, int nr
     b.skip_stride = skip_stride;
     b.grid_cap = red ? grid_cap : 0;
     launch_hop(b, st);
+}
+
+}  // namespace
+
+void schur_apply(const GaugeField& gf, Prec sp, Vec out, Vec in, Vec tmp, int nrhs, double kappa, int dag,
+                 const RedArgs* red, const int* skip, int skip_stride, int grid_cap, cudaStream_t st) {
+    schur_launch(gf, sp, out, in, tmp, nrhs, kappa, dag, red, skip, skip_stride, grid_cap, false, st);
+}
+
+void schur_tune(const GaugeField& gf, Prec sp, Vec out, Vec in, Vec tmp, int nrhs, int dag, cudaStream_t st) {
+    schur_launch(gf, sp, out, in, tmp, nrhs, 0.0, dag, nullptr, nullptr, 0, 0, true, st);
 }
 
 namespace {
@@ -186,12 +202,12 @@ std::vector<SolveStats> cg_solve_prepared(SpinorField& x, const SpinorField& b, 
     if (!(delta > 0.0)) delta = default_delta(prm.inner);
 
     // Tune the operator launches before capture (tuning cannot run inside a
-    // captured stream).  The launches below only write scratch fields.
+    // captured stream).  Tuning launches write only scratch fields; once the
+    // configurations are known this launches nothing.
     for (int k = 0; k < nr; k++) WL_CUDA(cudaMemsetAsync(in.p.block(0, k), 0, in.p.pbytes, st));
     for (int dag = 0; dag < 2; dag++)
-        schur_apply(glo, in.ip, vec(in.q, 0), vec(in.p, 0), vec(in.t, 1), nr, kappa, dag, nullptr, nullptr, 0, 0,
-                    st);
-    schur_apply(g64, P_F64, vec(q64, 0), vec(x, 0), vec(t64, 1), nr, kappa, 0, nullptr, nullptr, 0, 0, st);
+        schur_tune(glo, in.ip, vec(in.q, 0), vec(in.p, 0), vec(in.t, 1), nr, dag, st);
+    schur_tune(g64, P_F64, vec(q64, 0), vec(x, 0), vec(t64, 1), nr, 0, st);
 
     auto iteration = [&](cudaStream_t s) {
         const int* skip = &sc->done;
@@ -230,10 +246,16 @@ std::vector<SolveStats> cg_solve_prepared(SpinorField& x, const SpinorField& b, 
     bool first = true;
     try {
         while (true) {
-            // r64 = bhat - Mhat x_e (FP64)
+            // r64 = bhat - Mhat x_e (FP64); the first residual of a solve from
+            // x_e = 0 is bhat itself
             NvtxRange nvtx_outer("fp64 correction");
-            schur_apply(g64, P_F64, vec(q64, 0), vec(x, 0), vec(t64, 1), nr, kappa, 0, nullptr, nullptr, 0, 0, st);
-            hops += 2;
+            if (outer == 0 && !prm.use_initial_guess) {
+                for (int k = 0; k < nr; k++) WL_CUDA(cudaMemsetAsync(q64.block(0, k), 0, q64.pbytes, st));
+            } else {
+                schur_apply(g64, P_F64, vec(q64, 0), vec(x, 0), vec(t64, 1), nr, kappa, 0, nullptr, nullptr, 0, 0,
+                            st);
+                hops += 2;
+            }
             xmy_norm64(vec(r64, 0), vec(bhat, 0), vec(q64, 0), g, nr,
                        red.args(slot(5), FIN_STORE, d_res + 2 * nr, nullptr), grid_cap, st);
             WL_CUDA(cudaMemcpyAsync(h_res + 2 * nr, d_res + 2 * nr, nr * sizeof(double), cudaMemcpyDeviceToHost,
