@@ -16,6 +16,16 @@
 
 namespace wl {
 
+// Programmatic dependent launch (sm_90 and later).  A kernel launched with
+// the programmatic-serialization attribute may be scheduled while the
+// previous kernel on its stream is still running; pdl_wait() returns once that
+// kernel has completed and its memory operations are visible, so a kernel
+// calls it before it reads or writes anything an earlier kernel touches.
+// pdl_trigger() lets the next such kernel be scheduled once every block of
+// this one has started.  Both are no-ops for a plain launch.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 enum Prec { P_F64 = 0, P_F32 = 1, P_F16 = 2, P_BF16 = 3 };
 
 // ---------------------------------------------------------------------------

@@ -23,6 +23,14 @@ int device_sm_count() {
     return sms[dev];
 }
 
+bool pdl_enabled() {
+    static const bool on = [] {
+        const char* e = std::getenv("WILSON_PDL");
+        return !(e && e[0] == '0');
+    }();
+    return on;
+}
+
 int hop_grid_blocks(const Geom& g, int block, int grid_cap) {
     int blocks = (g.Vh + block - 1) / block;
     if (grid_cap > 0 && blocks > grid_cap) blocks = grid_cap;

@@ -197,8 +197,10 @@ __global__ void __launch_bounds__(256, MINB) hop_kernel(const HopParams P) {
     const int k = blockIdx.x % P.nrhs;
     const int sb = blockIdx.x / P.nrhs;
     const int nb = gridDim.x / P.nrhs;
-    if (P.skip && __ldcg(P.skip + (size_t)k * P.skip_stride)) return;
     const int p = P.full ? (int)blockIdx.y : P.out_parity;
+    pdl_trigger();
+    pdl_wait();
+    if (P.skip && __ldcg(P.skip + (size_t)k * P.skip_stride)) return;
     const int pin = 1 - p;
     char* out = P.out + (P.full ? p * P.out_pstep : 0) + k * P.out_rstep;
     const char* in = P.in + (P.full ? pin * P.in_pstep : 0) + k * P.in_rstep;
@@ -403,8 +405,10 @@ __global__ void __launch_bounds__(256, MINB) hop_kernel_p(const HopParams P) {
     const int k = blockIdx.x % P.nrhs;
     const int sb = blockIdx.x / P.nrhs;
     const int nb = gridDim.x / P.nrhs;
-    if (P.skip && __ldcg(P.skip + (size_t)k * P.skip_stride)) return;
     const int p = P.full ? (int)blockIdx.y : P.out_parity;
+    pdl_trigger();
+    pdl_wait();
+    if (P.skip && __ldcg(P.skip + (size_t)k * P.skip_stride)) return;
     const int pin = 1 - p;
     char* out = P.out + (P.full ? p * P.out_pstep : 0) + k * P.out_rstep;
     const char* in = P.in + (P.full ? pin * P.in_pstep : 0) + k * P.in_rstep;
@@ -533,6 +537,8 @@ __global__ void __launch_bounds__(256, MINB) hop_kernel_pm(const HopParams P) {
     const int sb = blockIdx.x / ng;
     const int nb = gridDim.x / ng;
     const int k0 = grp * NB;
+    pdl_trigger();
+    pdl_wait();
     unsigned act = 0;
 #pragma unroll
     for (int r = 0; r < NB; r++)
@@ -638,19 +644,19 @@ template <int SP, int GP, int R, int V>
 void launch_hop_mrhs_v(const HopParams& P, int block, int site_blocks, int ny, bool dag, cudaStream_t st) {
     constexpr int NB = hop_variant_nb(V), MINB = hop_variant_minb(V, SP);
     const dim3 grid(site_blocks * (P.nrhs / NB), ny);
-    if (dag) hop_kernel_pm<SP, GP, R, true, MINB, NB><<<grid, block, 0, st>>>(P);
-    else hop_kernel_pm<SP, GP, R, false, MINB, NB><<<grid, block, 0, st>>>(P);
+    if (dag) launch_dep(hop_kernel_pm<SP, GP, R, true, MINB, NB>, grid, dim3(block), st, P);
+    else launch_dep(hop_kernel_pm<SP, GP, R, false, MINB, NB>, grid, dim3(block), st, P);
 }
 
 template <int SP, int GP, int R, int V>
 void launch_hop_v(const HopParams& P, dim3 grid, int block, bool dag, cudaStream_t st) {
     constexpr int MINB = hop_variant_minb(V, SP);
     if constexpr (V >= 3 && float_storage(SP)) {
-        if (dag) hop_kernel_p<SP, GP, R, true, MINB><<<grid, block, 0, st>>>(P);
-        else hop_kernel_p<SP, GP, R, false, MINB><<<grid, block, 0, st>>>(P);
+        if (dag) launch_dep(hop_kernel_p<SP, GP, R, true, MINB>, grid, dim3(block), st, P);
+        else launch_dep(hop_kernel_p<SP, GP, R, false, MINB>, grid, dim3(block), st, P);
     } else {
-        if (dag) hop_kernel<SP, GP, R, true, MINB><<<grid, block, 0, st>>>(P);
-        else hop_kernel<SP, GP, R, false, MINB><<<grid, block, 0, st>>>(P);
+        if (dag) launch_dep(hop_kernel<SP, GP, R, true, MINB>, grid, dim3(block), st, P);
+        else launch_dep(hop_kernel<SP, GP, R, false, MINB>, grid, dim3(block), st, P);
     }
 }
 

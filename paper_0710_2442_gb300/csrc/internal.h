@@ -34,6 +34,33 @@ struct Error : std::runtime_error {
         if (!(cond)) throw ::wl::Error(1, std::string(msg));       \
     } while (0)
 
+// Launch of a kernel that begins with pdl_wait() (common.cuh), with the
+// programmatic-serialization attribute: its blocks may be scheduled while the
+// previous kernel on the stream drains, which hides the launch gap and the
+// last wave's tail.  Launches into a stream that is being captured stay plain:
+// measured, the attribute made the captured CG iterations slower (the graph
+// already removes the launch gaps).  WILSON_PDL=0 launches every one plainly.
+bool pdl_enabled();
+template <typename... KArgs, typename... Args>
+void launch_dep(void (*kernel)(KArgs...), dim3 grid, dim3 block, cudaStream_t st, const Args&... args) {
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = st;
+    cfg.attrs = attr;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cs) != cudaSuccess) {
+        (void)cudaGetLastError();
+        cs = cudaStreamCaptureStatusActive;
+    }
+    cfg.numAttrs = pdl_enabled() && cs == cudaStreamCaptureStatusNone ? 1 : 0;
+    WL_CUDA(cudaLaunchKernelEx(&cfg, kernel, args...));
+}
+
 // ---------------------------------------------------------------------------
 // device memory owned by the library
 // ---------------------------------------------------------------------------
