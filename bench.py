@@ -37,7 +37,7 @@ from paper_0710_2442_gb300 import inputs, model  # noqa: E402
 METRIC = "Dslash GFlop/s & HBM GB/s (% roofline); CG time-to-1e-10 mixed vs FP64"
 # DRAM bytes (read + write) per launch of the tuned kernel, from the ncu capture summarised in
 # profiles/hop_eo_32x32x32x64_f32_f16_f64.md (keyed by storage precision and link reals).
-NCU_TRAFFIC = {("f32", 12): 575.8e6, ("f16", 12): None, ("f64", 18): None}
+NCU_TRAFFIC = {("f32", 12): 576.3e6, ("f16", 12): 279.8e6, ("f64", 18): 1621.5e6}
 FP64_PEAK_GFLOPS = 1250.0  # nominal GB300 FP64 rate
 WORKLOAD = "dslash_eo_f32_32^3x64"
 L2_NOTE = ("inputs larger than L2: each application streams 403 MB of links plus 2 x 101 MB of spinors "
