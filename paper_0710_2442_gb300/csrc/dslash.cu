@@ -99,7 +99,9 @@ void launch_hop(const HopLaunch& L, cudaStream_t st) {
                  L.full, L.xpay, P.nrhs, P.g.L[0], P.g.L[1], P.g.L[2], P.g.L[3]);
         // tuning launches never reduce: the finishers are not idempotent
         const HopParams Pt = P;
-        std::vector<LaunchConfig> cands = hop_candidates();
+        std::vector<LaunchConfig> cands;
+        for (const LaunchConfig& c : hop_candidates())  // FP64 has three register budgets, not six
+            if (!wide_regs(sp) || c.variant < 3) cands.push_back(c);
         if (P.nrhs > 1)
             for (int block : {64, 128, 256})
                 for (int v = kHopBaseVariants; v < kHopVariants; v++)

@@ -106,28 +106,33 @@ LaunchConfig tune_launch(const std::string& key0, const std::vector<LaunchConfig
     cudaEvent_t e0, e1;
     WL_CUDA(cudaEventCreate(&e0));
     WL_CUDA(cudaEventCreate(&e1));
-    // Each candidate is timed as bursts of kBurst back-to-back launches (the
-    // way operators run), best of three bursts.  A later candidate replaces
-    // the best one only when it is more than 1 % faster, so candidates within
-    // timing noise of each other resolve to the same (earlier) choice in every
-    // process.
+    // Each candidate is timed once alone and then, unless that launch took
+    // longer than 300 us (its launch gap is then negligible and bursts would
+    // make tuning slow), twice as a burst of kBurst back-to-back launches, the
+    // way operators run; the best time per launch counts.  A later candidate
+    // replaces the best one only when it is more than 1 % faster, so candidates
+    // within timing noise of each other resolve to the same (earlier) choice
+    // in every process.
     constexpr int kBurst = 4;
     Entry best{fallback, 1e30f};
     for (const LaunchConfig& c : candidates) {
         run(c);  // warm-up
         if (cudaGetLastError() != cudaSuccess) continue;  // candidate not launchable here
         float ms_best = 1e30f;
+        int burst = 1;
         for (int rep = 0; rep < 3; rep++) {
             WL_CUDA(cudaEventRecord(e0, st));
-            for (int b = 0; b < kBurst; b++) run(c);
+            for (int b = 0; b < burst; b++) run(c);
             WL_CUDA(cudaEventRecord(e1, st));
             WL_CUDA(cudaEventSynchronize(e1));
             float ms = 0.f;
             WL_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+            ms /= burst;
             if (ms < ms_best) ms_best = ms;
+            if (rep == 0 && ms < 0.3f) burst = kBurst;
         }
         if (cudaGetLastError() != cudaSuccess) continue;
-        const float us = ms_best * 1e3f / kBurst;
+        const float us = ms_best * 1e3f;
         if (env_flag("WILSON_TUNE_VERBOSE", false))
             fprintf(stderr, "[wilson tune]   %s block %d variant %d: %.2f us\n", key.c_str(), c.block, c.variant, us);
         if (us < 0.99f * best.us) best = Entry{c, us};
