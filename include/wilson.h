@@ -233,7 +233,12 @@ int wilson_spinor_export(const wilson_spinor* s, double* canon, void* stream);
  *         other parity is allocated once and kept with the gauge handle)
  * All nrhs fields are applied in one launch per hop, right-hand sides of a
  * site tile back to back so that they share the tile's link loads; out must
- * not be in. */
+ * not be in.  Asynchronous and ordered on the stream.  Outside stream capture
+ * each hop is launched with programmatic dependent launch: its blocks may be
+ * scheduled while the previous kernel on the stream drains, but they touch
+ * no memory before that kernel has completed, so stream order holds for
+ * every earlier operation.  The environment variable WILSON_PDL=0 launches
+ * plainly. */
 int wilson_dslash_h(wilson_spinor* out, const wilson_gauge* g, const wilson_spinor* in, double kappa,
                     int op, void* stream);
 
