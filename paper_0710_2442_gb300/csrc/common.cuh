@@ -443,8 +443,26 @@ struct GaugeFmt<P_F32, 18> {
 template <>
 struct GaugeFmt<P_F32, 12> {
     using real = float;
+    using chunk_t = float4;
     static constexpr int nchunk = 3;
     static constexpr int chunk_bytes = 16;
+    // The link's stored chunks, copied to dst[c * dstride] (shared-memory
+    // staging), and their decoding: the same arithmetic as load().
+    __device__ static __forceinline__ void load_chunks(const void* base, int stride, int blk, int i, chunk_t* dst,
+                                                       int dstride) {
+        const float4* b = static_cast<const float4*>(base) + (size_t)blk * nchunk * stride + i;
+#pragma unroll
+        for (int c = 0; c < nchunk; c++) dst[c * dstride] = __ldcs(b + (size_t)c * stride);
+    }
+    __device__ static __forceinline__ void decode(const chunk_t* src, int sstride, cpx<float> U[3][3]) {
+#pragma unroll
+        for (int c = 0; c < 3; c++) {
+            const float4 d = src[c * sstride];
+            U[(2 * c) / 3][(2 * c) % 3] = {d.x, d.y};
+            U[(2 * c + 1) / 3][(2 * c + 1) % 3] = {d.z, d.w};
+        }
+        recon_row2(U);
+    }
     __device__ static __forceinline__ void load(const void* base, int stride, int blk, int i, cpx<float> U[3][3]) {
         const float4* b = static_cast<const float4*>(base) + (size_t)blk * nchunk * stride + i;
 #pragma unroll
@@ -461,8 +479,25 @@ template <int P>
 struct GaugeLow12 {
     using real = float;
     using LT = LowT<P>;
+    using chunk_t = uint2;
     static constexpr int nchunk = 3;
     static constexpr int chunk_bytes = 8;
+    __device__ static __forceinline__ void load_chunks(const void* base, int stride, int blk, int i, chunk_t* dst,
+                                                       int dstride) {
+        const uint2* b = static_cast<const uint2*>(base) + (size_t)blk * nchunk * stride + i;
+#pragma unroll
+        for (int c = 0; c < nchunk; c++) dst[c * dstride] = __ldcs(b + (size_t)c * stride);
+    }
+    __device__ static __forceinline__ void decode(const chunk_t* src, int sstride, cpx<float> U[3][3]) {
+#pragma unroll
+        for (int c = 0; c < 3; c++) {
+            const uint2 d = src[c * sstride];
+            const float2 f0 = LT::to_f2(d.x), f1 = LT::to_f2(d.y);
+            U[(2 * c) / 3][(2 * c) % 3] = {f0.x, f0.y};
+            U[(2 * c + 1) / 3][(2 * c + 1) % 3] = {f1.x, f1.y};
+        }
+        recon_row2(U);
+    }
     __device__ static __forceinline__ void load(const void* base, int stride, int blk, int i, cpx<float> U[3][3]) {
         const uint2* b = static_cast<const uint2*>(base) + (size_t)blk * nchunk * stride + i;
 #pragma unroll

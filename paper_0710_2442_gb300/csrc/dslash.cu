@@ -111,6 +111,9 @@ void launch_hop(const HopLaunch& L, cudaStream_t st) {
         });
     }
     WL_REQUIRE(hop_variant_valid(cfg.variant, sp, R, P.nrhs), "hop variant does not fit this launch");
+    // the link-staged kernel has no fused reduction: reducing launches take
+    // the paired kernel with the same block
+    if (L.red && cfg.variant >= kHopStagedVariant) cfg.variant = 3;
     if (L.tune_only) return;
     if (L.red) {
         P.reduce = 1;

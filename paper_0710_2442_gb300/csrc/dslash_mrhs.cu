@@ -13,6 +13,7 @@ void launch_hop_mrhs(const HopParams& P, int block, int site_blocks, int ny, boo
         case 7: launch_hop_mrhs_v<SP, GP, R, 7>(P, block, site_blocks, ny, dag, st); break;
         case 8: launch_hop_mrhs_v<SP, GP, R, 8>(P, block, site_blocks, ny, dag, st); break;
         case 9: launch_hop_mrhs_v<SP, GP, R, 9>(P, block, site_blocks, ny, dag, st); break;
+        case 10: launch_hop_rl_v<SP, GP, R, 10>(P, block, site_blocks, ny, dag, st); break;
         default: throw Error(7, "unknown register-blocked hop variant");
     }
 }

@@ -42,14 +42,15 @@ struct Error : std::runtime_error {
 // already removes the launch gaps).  WILSON_PDL=0 launches every one plainly.
 bool pdl_enabled();
 template <typename... KArgs, typename... Args>
-void launch_dep(void (*kernel)(KArgs...), dim3 grid, dim3 block, cudaStream_t st, const Args&... args) {
+void launch_dep_smem(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                     const Args&... args) {
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
     attr[0].val.programmaticStreamSerializationAllowed = 1;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = grid;
     cfg.blockDim = block;
-    cfg.dynamicSmemBytes = 0;
+    cfg.dynamicSmemBytes = smem;
     cfg.stream = st;
     cfg.attrs = attr;
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
@@ -59,6 +60,10 @@ void launch_dep(void (*kernel)(KArgs...), dim3 grid, dim3 block, cudaStream_t st
     }
     cfg.numAttrs = pdl_enabled() && cs == cudaStreamCaptureStatusNone ? 1 : 0;
     WL_CUDA(cudaLaunchKernelEx(&cfg, kernel, args...));
+}
+template <typename... KArgs, typename... Args>
+void launch_dep(void (*kernel)(KArgs...), dim3 grid, dim3 block, cudaStream_t st, const Args&... args) {
+    launch_dep_smem(kernel, grid, block, 0, st, args...);
 }
 
 // ---------------------------------------------------------------------------

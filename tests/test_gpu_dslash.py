@@ -210,9 +210,10 @@ def test_variant_solver(w, oracle_mod, monkeypatch, variant):
 
 
 # The register-blocked multi-RHS variants (NB = 2, 2, 3, 4 right-hand sides
-# per thread), pinned through WILSON_HOP_VARIANT, on 12 right-hand sides
-# (a multiple of every NB) over a lattice with a ragged last block.
-@pytest.mark.parametrize("variant", [6, 7, 8, 9])
+# per thread) and the link-staged one (10: links in shared memory, a loop over
+# the right-hand sides), pinned through WILSON_HOP_VARIANT, on 12 right-hand
+# sides (a multiple of every NB) over a lattice with a ragged last block.
+@pytest.mark.parametrize("variant", [6, 7, 8, 9, 10])
 @pytest.mark.parametrize("prec", ["f32", "f16", "bf16"])
 def test_blocked_multi_rhs_variants(w, oracle_mod, monkeypatch, variant, prec):
     monkeypatch.setenv("WILSON_HOP_VARIANT", str(variant))
@@ -235,7 +236,7 @@ def test_blocked_multi_rhs_variants(w, oracle_mod, monkeypatch, variant, prec):
         assert_parity(got[k], oracle_mod.wilson_m(U, psi[k], dims, 0.1350, CPLX_PHASES), TOL[prec])
 
 
-@pytest.mark.parametrize("variant", [6, 8, 9])
+@pytest.mark.parametrize("variant", [6, 8, 9, 10])
 def test_blocked_variant_lockstep_solve(w, oracle_mod, monkeypatch, variant):
     """The lockstep multi-RHS solve on a blocked kernel: right-hand sides that
     finish early (a zero source at once) are skipped inside their group while
