@@ -395,7 +395,8 @@ def run_multirhs_block(w, torch, dev, stream, fields, nrhs=12):
 
 
 def run_batch_block(w, torch, dev, stream):
-    """64 uneven solves in one graph launch against the same 64 solved one by one."""
+    """64 uneven solves in one graph launch against the same 64 solved one by one, with the
+    same mixed-precision solver and with plain FP64 CG."""
     probs = inputs.batch_problems()
     fields = []
     for p in probs:
@@ -427,6 +428,25 @@ def run_batch_block(w, torch, dev, stream):
         w.wilson_cg_solve(f["x"], f["gauge"], f["b"], f["L"], f["kappa"], prm, stream, check=False)
     torch.cuda.synchronize(dev)
     t_seq = time.perf_counter() - t0
+    # the same 64 problems with plain FP64 CG, one by one (one untimed solve per size tunes first)
+    p64 = w.solver_defaults(w.WILSON_F64)
+    seen = set()
+    for p, f in zip(probs, fields):
+        if tuple(p["dims"]) in seen:
+            continue
+        seen.add(tuple(p["dims"]))
+        xw = torch.zeros_like(f["x"])
+        w.wilson_cg_solve(xw, f["gauge"], f["b"], f["L"], f["kappa"], p64, stream, check=False)
+        del xw
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    rc64 = 0
+    for f in fields:
+        f["x"].zero_()
+        s64 = w.wilson_cg_solve(f["x"], f["gauge"], f["b"], f["L"], f["kappa"], p64, stream, check=False)
+        rc64 = rc64 or s64["rc"]
+    torch.cuda.synchronize(dev)
+    t_seq64 = time.perf_counter() - t0
     q = lambda a, f: a[min(len(a) - 1, int(round(f * (len(a) - 1))))]
     by_size, iters = {}, {}
     for p, s_ in zip(probs, st):
@@ -444,6 +464,8 @@ def run_batch_block(w, torch, dev, stream):
            "device_loop": info["device_loop"], "timed_out": info["timed_out"],
            "max_true_rel_resid": max(s["true_rel_resid"] for s in st),
            "sequential_seconds": round(t_seq, 4), "speedup_vs_sequential": round(t_seq / info["device_seconds"], 3),
+           "fp64_sequential_seconds": round(t_seq64, 4), "fp64_sequential_rc": rc64,
+           "speedup_vs_fp64_sequential": round(t_seq64 / info["device_seconds"], 3),
            "latency_by_lattice": by_size}
     del fields
     torch.cuda.empty_cache()
