@@ -35,6 +35,8 @@ sys.path.insert(0, ROOT)
 from paper_0710_2442_gb300 import inputs, model  # noqa: E402
 
 METRIC = "Dslash GFlop/s & HBM GB/s (% roofline); CG time-to-1e-10 mixed vs FP64"
+FIRST_APPLICATION = [None]  # the library's first hop application of the timed workload (host copy)
+ORACLE_OUTPUT = [None]      # the oracle's output for the same input (CPU leg)
 # DRAM bytes (read + write) per launch of the tuned kernel, from the ncu capture summarised in
 # profiles/hop_eo_32x32x32x64_f32_f16_f64.md (keyed by storage precision and link reals).
 NCU_TRAFFIC = {("f32", 12): 576.3e6, ("f16", 12): 279.8e6, ("f64", 18): 1621.5e6}
@@ -196,6 +198,14 @@ def run_ours(args, ws, rank, local, fields):
     odd = w.Spinor(L, w.WILSON_ODD, P)
     src_dev = torch.from_numpy(src).to(dev)
     even.load(src_dev, stream)
+    # one application kept for the parity record (compared with the oracle's output in the
+    # CPU leg); outside every timed region
+    first = torch.empty_like(src_dev)
+    w.wilson_dslash_h(odd, g, even, 0.0, w.WILSON_OP_HOP, stream)
+    odd.store(first, stream)
+    torch.cuda.synchronize(dev)
+    FIRST_APPLICATION[0] = first.cpu().numpy()
+    del first
 
     def step():
         for k in range(apps):
@@ -476,15 +486,28 @@ def run_batch_block(w, torch, dev, stream):
 # the FP64 CPU oracle (CPU baseline and the reference arm)
 # ---------------------------------------------------------------------------
 def oracle_sample(dims, U, src, reps=1):
+    """GFlop/s, threads and seconds of the FP64 oracle's even-odd hop (out
+    parity 1) on the full lattice; its last output is kept in ORACLE_OUTPUT."""
     import oracle
     oracle.build()
     cores = oracle.num_threads()
     Vh = inputs.volume(dims) // 2
     t0 = time.perf_counter()
     for _ in range(reps):
-        oracle.dslash_eo(U, src, dims, 1)
+        ORACLE_OUTPUT[0] = oracle.dslash_eo(U, src, dims, 1)
     t = time.perf_counter() - t0
     return model.FLOPS_PER_SITE * Vh * reps / t / 1e9, cores, t
+
+
+def parity_record(prec, got, want):
+    """The first timed-kernel application against the FP64 oracle, whole lattice."""
+    tol = {"f64": 1e-13, "f32": 1e-6, "f16": 5e-3, "bf16": 5e-3}[prec]
+    d = (got - want).ravel()
+    rms = float(np.sqrt(np.mean(np.abs(want) ** 2)))
+    return {"what": "one even-odd hop application on the full lattice against the FP64 oracle",
+            "rel_l2": float(np.linalg.norm(d) / np.linalg.norm(want)),
+            "max_component_error_over_rms": float(np.max(np.maximum(np.abs(d.real), np.abs(d.imag))) / rms),
+            "tolerance_rel_l2": tol, "sites": int(want.shape[0])}
 
 
 def oracle_cg_per_iteration(dims, U, b, kappa, iters=10):
@@ -578,6 +601,8 @@ def main():
                                 "sample": f"one FP64 even-odd application on the full 32^3x64 lattice "
                                           f"({t:.1f} s of CPU time)",
                                 "value_1core": round(v1, 4)}
+        if FIRST_APPLICATION[0] is not None and ORACLE_OUTPUT[0] is not None:
+            line["parity"] = parity_record(args.prec, FIRST_APPLICATION[0], ORACLE_OUTPUT[0])
         if not args.no_solver:
             line["cpu_baseline"]["solvers"] = oracle_solver_baselines(line)
     if rank == 0:
