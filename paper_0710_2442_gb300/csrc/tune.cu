@@ -2,11 +2,15 @@
 //
 // A launch is identified by a key (kernel, precisions, link format, flags,
 // lattice extents).  The first time a key is seen the candidates are timed
-// on the caller's stream with CUDA events (one warm-up launch, then the best
-// of three timed launches each) and the fastest is kept.  Tuning synchronises
-// the stream, so the first call for a new key is slower; it is skipped while
-// the stream is being captured into a graph (the fallback is used and the
-// key is not stored).
+// on the caller's stream with CUDA events (per candidate: a warm-up launch,
+// one timed launch, then two timed bursts of four back-to-back launches
+// unless the single launch took longer than 300 us; the best time per launch
+// counts), and the fastest is kept: a later candidate must be more than 1 %
+// faster to replace an earlier one.  Tuning synchronises the stream, so the
+// first call for a new key is slower; it is skipped while the stream is being
+// captured into a graph (the fallback is used and the key is not stored).
+// A decision from the cache file that is not among the current candidates
+// (written by another build) is ignored and the key is tuned again.
 //
 // Environment:
 //   WILSON_TUNE=0            never time candidates (use the fallback)
@@ -95,7 +99,12 @@ LaunchConfig tune_launch(const std::string& key0, const std::vector<LaunchConfig
         if (!g_cache) g_cache = new std::map<std::string, Entry>();
         if (!g_loaded) load_file();
         auto it = g_cache->find(key);
-        if (it != g_cache->end()) return it->second.cfg;
+        if (it != g_cache->end()) {
+            bool known = candidates.empty();
+            for (const LaunchConfig& c : candidates)
+                known = known || (c.block == it->second.cfg.block && c.variant == it->second.cfg.variant);
+            if (known) return it->second.cfg;
+        }
     }
     if (!env_flag("WILSON_TUNE", true) || candidates.empty()) return fallback;
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
