@@ -41,6 +41,27 @@
  *
  * There is no CPU fallback: every call runs on the current CUDA device and
  * returns WILSON_ERR_CUDA if there is none.
+ *
+ * Environment (none is needed; they serve measurement and tests):
+ *   WILSON_TUNE=0                 no autotuning: default launch configurations
+ *   WILSON_TUNE_CACHE=path        load tuning decisions from path, append new ones
+ *   WILSON_TUNE_VERBOSE=1         report tuning candidates and decisions on stderr
+ *   WILSON_HOP_VARIANT=v          pin the hop kernel variant (0..10) of every launch;
+ *                                 a variant that does not fit a launch runs variant 3
+ *   WILSON_HOP_BLOCK=n            block size with WILSON_HOP_VARIANT (64, 128, 256)
+ *   WILSON_PDL=0                  hops without programmatic dependent launch (read
+ *                                 once per process)
+ *   WILSON_BATCH_SMALL_VH=n       batched solves: lattices with at most n sites per
+ *                                 parity run on the on-chip solver
+ *   WILSON_BATCH_SMALL_CLUSTER=1  one CTA per small lattice instead of a cluster of four
+ *   WILSON_BATCH_CLASSES=n        at most n lattice-size classes (default 4)
+ *   WILSON_BATCH_PRIORITY=0       no graph-node priorities between the classes
+ *   WILSON_BATCH_GRID_PER_SM=n    n blocks per SM for the tile-walking kernels
+ *                                 (default: one block per tile)
+ *   WILSON_BATCH_HOST_LOOP=1      host-replayed graphs instead of device-side loops
+ *   WILSON_BATCH_MAX_LOOP=n       lower the batch loop's iteration cap
+ *   WILSON_BATCH_BUDGET_MS=t      lower the batch loop's wall-clock budget (60 s)
+ *   WILSON_BLOCK_VERBOSE=1        report each block-CG run on stderr
  */
 #ifndef WILSON_GB300_H
 #define WILSON_GB300_H
