@@ -317,6 +317,7 @@ struct BatchRun {
         o.phase = phase;
         o.skip_done = skip_done;
         o.fin = fin;
+        o.zero_first = 0;
         o.partials = partials.as<double>() + (size_t)rslot * ntiles;
         o.counters = counters.as<unsigned int>() + (size_t)rslot * nprob;
         return o;
@@ -562,8 +563,14 @@ void batch_solve(int n, const wilson_problem* probs, const SolveParams& prm, wil
         WL_CUDA(cudaStreamWaitEvent(st2, fork, 0));
         // branch A (OUTER problems) on s
         blas(R, baxpy_kernel, R.op(0, 0, -1, 0, 0, 0, PH_OUTER, 0, BF_NONE, 1), s);
-        R.hop(R.op(BF_T64, BF_X, -1, 1, 1, 0, PH_OUTER, 0, BF_NONE, 1), 0, s);
-        R.hop(R.op(BF_Q64, BF_T64, BF_X, 0, 1, 2, PH_OUTER, 0, BF_NONE, 1), 0, s);
+        // without an initial guess the iterate is zero during a problem's
+        // first correction (the prologue zeroes it): those two hops write 0
+        // and x without the stencil
+        BOp t64 = R.op(BF_T64, BF_X, -1, 1, 1, 0, PH_OUTER, 0, BF_NONE, 1);
+        BOp q64 = R.op(BF_Q64, BF_T64, BF_X, 0, 1, 2, PH_OUTER, 0, BF_NONE, 1);
+        t64.zero_first = q64.zero_first = prm.use_initial_guess ? 0 : 1;
+        R.hop(t64, 0, s);
+        R.hop(q64, 0, s);
         blas(R, bxmy_kernel, R.op(0, 0, -1, 0, 0, 0, PH_OUTER, 0, BFIN_OUTER, 1), s);
         dispatch_low(ip, [&](auto I) {
             bprep_kernel<decltype(I)::value><<<R.grid, 256, 0, s>>>(R.A, R.op(0, 0, -1, 0, 0, 0, PH_OUTER, 0,
@@ -775,7 +782,7 @@ void batch_solve(int n, const wilson_problem* probs, const SolveParams& prm, wil
             o.true_rel_resid = bn > 0 ? std::sqrt(S.res2) / bn : std::sqrt(S.res2);
             o.inner_iters = S.sc.iter;
             o.outer_iters = S.outer;
-            o.hop_applications = 4 * S.sc.iter + 4 * (S.outer + 1) + 4;
+            o.hop_applications = 4 * S.sc.iter + 4 * (S.outer + 1) + (prm.use_initial_guess ? 4 : 2);
             o.seconds = S.phase == PH_DONE && S.t_done >= t_first ? (double)(S.t_done - t_first) * 1e-9 : -1.0;
             int status = S.status;
             if (status == 0 && S.phase != PH_DONE) status = hg[r].timed_out ? WILSON_ERR_TIMEOUT : WILSON_ERR_NOCONV;

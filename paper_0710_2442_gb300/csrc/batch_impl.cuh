@@ -69,6 +69,8 @@ struct BOp {
     int phase;              // only problems in this phase (-1: all)
     int skip_done;          // also skip problems whose inner CG is done
     int fin;                // BFin of the fused reduction (BF_NONE: none)
+    int zero_first;         // the FP64 correction hops: while a problem's iterate is still zero
+                            // (its first correction), the hop term is zero and is not computed
     double* partials;       // [ntiles]
     unsigned int* counters; // [nprob]
 };
@@ -208,6 +210,8 @@ __global__ void __launch_bounds__(256, MINB) bhop_kernel(const BatchArgs A, cons
         const char* x = op.f_x >= 0 ? Pr.f[op.f_x] + p * Pr.fp[op.f_x] : nullptr;
         const T a = (T)coef_of(op.coef, Pr.kappa);
         const Geom& g = P.g;
+        // outer is written only by the correction finisher, a later kernel
+        const bool zero = op.zero_first && __ldcg(&A.state[pid].outer) == 0;
         double nrm = 0.0;
         const int h0 = (t - Pr.tile0) * kTile;
         for (int j = threadIdx.x; j < kTile; j += blockDim.x) {
@@ -216,10 +220,15 @@ __global__ void __launch_bounds__(256, MINB) bhop_kernel(const BatchArgs A, cons
             int c[4], s;
             site_of_half(h, p, g, c, s);
             cpx<T> acc[12];
-            hop_dir<SP, GP, R, DAG, 0, true>(acc, P, in, p, h, c, s);
-            hop_dir<SP, GP, R, DAG, 1, false>(acc, P, in, p, h, c, s);
-            hop_dir<SP, GP, R, DAG, 2, false>(acc, P, in, p, h, c, s);
-            hop_dir<SP, GP, R, DAG, 3, false>(acc, P, in, p, h, c, s);
+            if (zero) {
+#pragma unroll
+                for (int k = 0; k < 12; k++) acc[k] = {T(0), T(0)};
+            } else {
+                hop_dir<SP, GP, R, DAG, 0, true>(acc, P, in, p, h, c, s);
+                hop_dir<SP, GP, R, DAG, 1, false>(acc, P, in, p, h, c, s);
+                hop_dir<SP, GP, R, DAG, 2, false>(acc, P, in, p, h, c, s);
+                hop_dir<SP, GP, R, DAG, 3, false>(acc, P, in, p, h, c, s);
+            }
             if (x) {
                 cpx<T> xv[12];
                 SF::load(x, g.stride, h, xv);

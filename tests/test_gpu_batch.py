@@ -57,6 +57,24 @@ def test_batch_matches_oracle(w, oracle_mod, monkeypatch, inner, small_vh):
 
 
 @pytest.mark.parametrize("small_vh", ["0", "4096"])
+def test_batch_initial_guess(w, oracle_mod, monkeypatch, small_vh):
+    """use_initial_guess: every problem starts from a nonzero iterate (its
+    first FP64 correction applies the operator to it) and still reaches the
+    1e-10 true residual; the problems without the flag start from zero."""
+    monkeypatch.setenv("WILSON_BATCH_SMALL_VH", small_vh)
+    probs, hf = make_batch(w, MIX, seed0=460)
+    for i, (q, (dims, _, b, _)) in enumerate(zip(probs, hf)):
+        q["x"] = dev(0.3 * inputs.gaussian_spinor(dims, seed=480 + i))
+    p = w.solver_defaults(w.WILSON_F16)
+    p.use_initial_guess = 1
+    rc, st, info = w.wilson_batch_solve(probs, p)
+    assert rc == 0 and not info["timed_out"]
+    for q, (dims, U, b, kappa), s in zip(probs, hf, st):
+        assert s["status"] == 0
+        assert true_resid(oracle_mod, U, host(q["x"]), b, dims, kappa) <= 1.1e-10
+
+
+@pytest.mark.parametrize("small_vh", ["0", "4096"])
 def test_batch_equals_single_solves(w, monkeypatch, small_vh):
     monkeypatch.setenv("WILSON_BATCH_SMALL_VH", small_vh)
     probs, hf = make_batch(w, MIX[:4], seed0=420)
