@@ -23,6 +23,16 @@
 // MINB selects the register budget: __launch_bounds__(256, MINB) caps a
 // thread at 65536 / (256 * MINB) registers, trading per-thread load
 // parallelism for resident warps; the autotuner picks the variant.
+//
+// Kernel families (the variant numbers the autotuner and WILSON_HOP_VARIANT
+// use):
+//   hop_kernel     0..2  scalar stencil (and every FP64 launch)
+//   hop_kernel_p   3..5  the same stencil on paired FP32 instructions
+//   hop_kernel_pm  6..9  several right-hand sides per thread (register-blocked)
+//   hop_kernel_rl  10    links staged in shared memory, loop over right-hand sides
+// Multi-RHS launches of the first two run the right-hand sides of a site
+// tile as consecutive blocks.  Every kernel starts with the programmatic-
+// dependent-launch wait, so it can be launched with that attribute.
 #pragma once
 
 #include "internal.h"
