@@ -783,10 +783,15 @@ void launch_hop_rl_v(const HopParams& P, int block, int site_blocks, int ny, boo
     constexpr size_t per_thread = (size_t)8 * GF::nchunk * sizeof(typename GF::chunk_t);
     const dim3 grid(site_blocks, ny);
     auto k = dag ? hop_kernel_rl<SP, GP, R, true, MINB> : hop_kernel_rl<SP, GP, R, false, MINB>;
-    static bool opted[2] = {false, false};  // per dagger: the larger dynamic shared memory, once
-    if (!opted[dag]) {
+    // the larger dynamic shared memory, once per device and dagger (the
+    // attribute is per device)
+    static bool opted[64][2] = {};
+    int dev = 0;
+    WL_CUDA(cudaGetDevice(&dev));
+    WL_REQUIRE(dev >= 0 && dev < 64, "device ordinal out of range");
+    if (!opted[dev][dag]) {
         WL_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(per_thread * 256)));
-        opted[dag] = true;
+        opted[dev][dag] = true;
     }
     launch_dep_smem(k, grid, dim3(block), per_thread * block, st, P);
 }
