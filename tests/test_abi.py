@@ -135,3 +135,19 @@ def test_batch_and_multi_rhs_arguments_rejected(w):
     for nrhs in (0, 65):
         rc, _ = w.wilson_cg_solve_multi(base + 1024, base, base + 512, nrhs, L, 0.12, p, check=False)
         assert rc == w.WILSON_ERR_ARG
+
+
+def test_environment_variables_documented():
+    """The header's environment section lists exactly the variables the
+    library reads (getenv, or the autotuner's flag helper)."""
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    header = open(os.path.join(root, "include", "wilson.h")).read()
+    section = header[header.index(" * Environment"):header.index(" */", header.index(" * Environment"))]
+    documented = set(re.findall(r"\b(WILSON_[A-Z_]+)=", section))
+    csrc = os.path.join(root, "paper_0710_2442_gb300", "csrc")
+    read = set()
+    for name in os.listdir(csrc):
+        if name.endswith((".cu", ".cuh", ".h")):
+            text = open(os.path.join(csrc, name)).read()
+            read |= set(re.findall(r'(?:getenv|env_flag)\("(WILSON_[A-Z_]+)"', text))
+    assert documented == read, (sorted(documented - read), sorted(read - documented))
