@@ -9,10 +9,12 @@ Rates: 1320 flops per output site (Sec. 5 of the paper) and 576 compulsory
 bytes per output site (spinor in 96 B + 8 links x 48 B + spinor out 96 B).
 
 Also reported: the end-to-end rate through the C ABI with host buffers
-(spinor copied in from pinned host memory and out again every step), the
-FP64 CPU oracle on the host cores, and a CG time-to-solution comparison on
-the 24^3 x 48 lattice (mixed F16/BF16-inner vs plain FP64, true residual
-1e-10).
+(spinor copied in from pinned host memory and out again every step); the
+FP64 CPU oracle on the host cores, and the timed kernel's first application
+against the oracle's output (parity record); a CG time-to-solution
+comparison on the 24^3 x 48 lattice (mixed F32/F16/BF16-inner vs plain FP64,
+true residual 1e-10); the 12-RHS hop and solves; and the batch of 64 uneven
+solves against the same problems solved one by one (mixed and plain FP64).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 """
