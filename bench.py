@@ -39,10 +39,15 @@ from paper_0710_2442_gb300 import inputs, model  # noqa: E402
 METRIC = "Dslash GFlop/s & HBM GB/s (% roofline); CG time-to-1e-10 mixed vs FP64"
 FIRST_APPLICATION = [None]  # the library's first hop application of the timed workload (host copy)
 ORACLE_OUTPUT = [None]      # the oracle's output for the same input (CPU leg)
-# DRAM bytes (read + write) per launch of the tuned kernel, from the ncu capture summarised in
-# profiles/hop_eo_32x32x32x64_f32_f16_f64.md (keyed by storage precision and link reals).
+# GPU solutions kept (host copies) for the oracle's residual check in the CPU leg:
+# a list of (record, key, [(gauge, b, x, dims, kappa), ...][, FP64 GPU solution to compare x with]);
+# gauge and b may be callables that regenerate the field from its seed
+SOLUTIONS = []
+# DRAM bytes (read + write) per launch of the tuned 32^3 x 64 even-odd kernel, read from one
+# ncu capture of that kernel (keyed by storage precision and link reals); a fixed figure, not
+# measured by this run.
 NCU_TRAFFIC = {("f32", 12): 576.3e6, ("f16", 12): 279.8e6, ("f64", 18): 1621.5e6}
-FP64_PEAK_GFLOPS = 1250.0  # nominal GB300 FP64 rate
+TRAFFIC_SOURCE = "ncu capture of the tuned kernel (dram__bytes_read.sum + dram__bytes_write.sum), fixed figure"
 WORKLOAD = "dslash_eo_f32_32^3x64"
 L2_NOTE = ("inputs larger than L2: each application streams 403 MB of links plus 2 x 101 MB of spinors "
            "through the 126 MB L2")
@@ -195,6 +200,12 @@ def run_ours(args, ws, rank, local, fields):
     L = w.lattice(dims)
     stream = torch.cuda.current_stream(dev)
     P = w.PREC[args.prec]
+    # the device's measured FMA peaks (the ALU rooflines), before any timed region
+    alu = {"f64_gflops": round(w.wilson_probe_fma_peak(w.WILSON_PROBE_FMA_F64, stream), 1),
+           "f32_gflops": round(w.wilson_probe_fma_peak(w.WILSON_PROBE_FMA_F32, stream), 1),
+           "f32x2_gflops": round(w.wilson_probe_fma_peak(w.WILSON_PROBE_FMA_F32X2, stream), 1),
+           "how": "wilson_probe_fma_peak: 8 independent FMA chains per thread, 2048 threads per SM on every "
+                  "SM, best of 3 CUDA-event-timed launches; 2 flops per FMA and lane"}
     g = w.Gauge(U, L, P, args.recon, stream)
     even = w.Spinor(L, w.WILSON_EVEN, P)
     odd = w.Spinor(L, w.WILSON_ODD, P)
@@ -274,22 +285,26 @@ def run_ours(args, ws, rank, local, fields):
         "hbm_gbs": round(achieved * ws, 1),
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                      "frac": round(achieved / peak, 4), "traffic": NCU_TRAFFIC.get((args.prec, args.recon)),
-                     "peak_kind": peak_kind,
+                     "traffic_source": TRAFFIC_SOURCE, "peak_kind": peak_kind,
                      "algorithmic_bytes_per_launch": comp_bytes, "launch_us": round(t_launch * 1e6, 2)},
     }
     if args.prec == "f64":
         # FP64 is bound by GB300's FP64 rate (FP64 pipe 91 % busy at 12 % DRAM
-        # throughput): roofline against the nominal 1.25 TFLOP/s FP64 peak.
+        # throughput): roofline against the FP64 FMA peak measured above.
         gf_launch = flops / t_launch / 1e9
-        line["roofline"] = {"bound": "alu", "achieved": round(gf_launch, 1), "peak": FP64_PEAK_GFLOPS,
-                            "unit": "GFLOP/s", "frac": round(gf_launch / FP64_PEAK_GFLOPS, 4),
-                            "traffic": NCU_TRAFFIC.get((args.prec, args.recon)), "peak_kind": "nominal",
-                            "launch_us": round(t_launch * 1e6, 2)}
-    line.update({"clocks": clocks, "e2e": e2e, "gpu_launches": launches})
+        f64_peak = alu["f64_gflops"]
+        line["roofline"] = {"bound": "alu", "achieved": round(gf_launch, 1), "peak": f64_peak,
+                            "unit": "GFLOP/s", "frac": round(gf_launch / f64_peak, 4),
+                            "traffic": NCU_TRAFFIC.get((args.prec, args.recon)), "traffic_source": TRAFFIC_SOURCE,
+                            "peak_kind": "measured (wilson_probe_fma_peak, FP64 FMA)",
+                            "launch_us": round(t_launch * 1e6, 2),
+                            "hbm": {"achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                                    "frac": round(achieved / peak, 4)}}
+    line.update({"clocks": clocks, "e2e": e2e, "gpu_launches": launches, "alu_peaks": alu})
     if rank == 0 and not args.no_solver:
         blocks = {b.strip() for b in args.blocks.split(",")}
         if "cg" in blocks:
-            line["cg"] = run_solver_block(w, torch, dev, stream, args.cg_prec.split(","))
+            line["cg"] = run_solver_block(w, torch, dev, stream, args.cg_prec.split(","), peak)
         if "multirhs" in blocks:
             line["multirhs"] = run_multirhs_block(w, torch, dev, stream, fields)
         if "batch" in blocks:
@@ -297,7 +312,7 @@ def run_ours(args, ws, rank, local, fields):
     return line
 
 
-def run_solver_block(w, torch, dev, stream, precs):
+def run_solver_block(w, torch, dev, stream, precs, hbm_peak):
     cfg = inputs.WORKLOADS["cg_mixed_24^3x48"]
     dims = cfg["dims"]
     U = inputs.gauge_field(dims, cfg["gauge"], eps=cfg["eps"], seed=cfg["gauge_seed"])
@@ -305,7 +320,9 @@ def run_solver_block(w, torch, dev, stream, precs):
     Ud = torch.from_numpy(U).to(dev)
     bd = torch.from_numpy(b).to(dev)
     L = w.lattice(dims)
+    Vh = inputs.volume(dims) // 2
     res = {"workload": "cg_mixed_24^3x48", "kappa": cfg["kappa"], "tol": cfg["tol"]}
+    sols = {}
     for name, prec in (("f64", w.WILSON_F64), ("f16", w.WILSON_F16), ("bf16", w.WILSON_BF16),
                        ("f32", w.WILSON_F32)):
         if name not in precs:
@@ -316,11 +333,28 @@ def run_solver_block(w, torch, dev, stream, precs):
         w.wilson_cg_solve(x, Ud, bd, L, cfg["kappa"], p, stream, check=False)
         x.zero_()
         st = w.wilson_cg_solve(x, Ud, bd, L, cfg["kappa"], p, stream, check=False)
-        res[name] = {"seconds": round(st["seconds"], 4), "inner_iters": st["inner_iters"],
-                     "outer_iters": st["outer_iters"], "hops": st["hop_applications"],
-                     "true_rel_resid": st["true_rel_resid"], "rc": st["rc"]}
+        rec = {"seconds": round(st["seconds"], 4), "inner_iters": st["inner_iters"],
+               "outer_iters": st["outer_iters"], "hops": st["hop_applications"],
+               "true_rel_resid": st["true_rel_resid"], "rc": st["rc"]}
+        if st["inner_iters"] > 0 and st["inner_seconds"] > 0:
+            # roofline of one inner CG iteration (six launches): algorithmic bytes over the
+            # device time of the inner iterations, measured by the solver with CUDA events
+            recon = 18 if name == "f64" else 12
+            byts = model.cg_inner_bytes_per_site(name, recon) * Vh
+            t_it = st["inner_seconds"] / st["inner_iters"]
+            rec["roofline_inner_iteration"] = {
+                "bound": "alu" if name == "f64" else "hbm", "bytes_per_site": model.cg_inner_bytes_per_site(name, recon),
+                "algorithmic_bytes": byts, "us_per_iteration": round(t_it * 1e6, 2),
+                "achieved_GBs": round(byts / t_it / 1e9, 1), "peak_GBs": hbm_peak,
+                "frac": round(byts / t_it / 1e9 / hbm_peak, 4),
+                "inner_share_of_solve": round(st["inner_seconds"] / st["seconds"], 3)}
+        res[name] = rec
+        sols[name] = x.cpu().numpy()
     if res.get("f64", {}).get("rc") == 0 and res.get("f16", {}).get("rc") == 0:
         res["speedup_f16_vs_f64"] = round(res["f64"]["seconds"] / res["f16"]["seconds"], 3)
+    for name, xs in sols.items():
+        SOLUTIONS.append((res[name], "oracle", [(U, b, xs, dims, cfg["kappa"])],
+                          sols.get("f64") if name != "f64" else None))
     return res
 
 
@@ -333,33 +367,41 @@ def run_multirhs_block(w, torch, dev, stream, fields, nrhs=12):
     Vh = inputs.volume(dims) // 2
     L = w.lattice(dims)
     kappa = inputs.WORKLOADS["multirhs12_32^3x64"]["kappa"]
-    out = {"workload": "multirhs12_32^3x64", "links": "the headline workload's field, f32 12-real"}
-    g = w.Gauge(U, L, w.WILSON_F32, 12, stream)
-    for n in (1, nrhs):
-        a = w.Spinor(L, w.WILSON_EVEN, w.WILSON_F32, n)
-        b = w.Spinor(L, w.WILSON_ODD, w.WILSON_F32, n)
-        a.load(torch.from_numpy(inputs.gaussian_spinor(Vh, seed=31, nrhs=n)).to(dev), stream)
-        for _ in range(3):
-            w.wilson_dslash_h(b, g, a, 0.0, w.WILSON_OP_HOP, stream)
-            w.wilson_dslash_h(a, g, b, 0.0, w.WILSON_OP_HOP, stream)
-        torch.cuda.synchronize(dev)
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        reps = 20
-        e0.record(stream)
-        for _ in range(reps // 2):
-            w.wilson_dslash_h(b, g, a, 0.0, w.WILSON_OP_HOP, stream)
-            w.wilson_dslash_h(a, g, b, 0.0, w.WILSON_OP_HOP, stream)
-        e1.record(stream)
-        torch.cuda.synchronize(dev)
-        t = e0.elapsed_time(e1) / 1e3 / reps
-        byts = model.compulsory_bytes_per_site("f32", 12, eo=True, nrhs=n) * Vh
-        out[f"hop_nrhs{n}"] = {"us_per_application": round(t * 1e6, 2), "us_per_rhs": round(t * 1e6 / n, 2),
-                               "GBs_compulsory": round(byts / t / 1e9, 1),
-                               "TFlops": round(model.FLOPS_PER_SITE * Vh * n / t / 1e12, 3)}
-        a.close()
-        b.close()
-    g.close()
-    out["rhs_speedup_per_rhs"] = round(out["hop_nrhs1"]["us_per_rhs"] / out[f"hop_nrhs{nrhs}"]["us_per_rhs"], 3)
+    hbm_peak, _ = measured_peaks()
+    out = {"workload": "multirhs12_32^3x64", "links": "the headline workload's field, 12-real"}
+    # the hop with 1 and 12 right-hand sides, F32 storage (keys hop_nrhs*) and the F16 storage
+    # of the inner solver (keys f16_hop_nrhs*); frac: compulsory bytes against measured HBM
+    for pname, prec, prefix in (("f32", w.WILSON_F32, ""), ("f16", w.WILSON_F16, "f16_")):
+        g = w.Gauge(U, L, prec, 12, stream)
+        for n in (1, nrhs):
+            a = w.Spinor(L, w.WILSON_EVEN, prec, n)
+            b = w.Spinor(L, w.WILSON_ODD, prec, n)
+            a.load(torch.from_numpy(inputs.gaussian_spinor(Vh, seed=31, nrhs=n)).to(dev), stream)
+            for _ in range(3):
+                w.wilson_dslash_h(b, g, a, 0.0, w.WILSON_OP_HOP, stream)
+                w.wilson_dslash_h(a, g, b, 0.0, w.WILSON_OP_HOP, stream)
+            torch.cuda.synchronize(dev)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            reps = 20
+            e0.record(stream)
+            for _ in range(reps // 2):
+                w.wilson_dslash_h(b, g, a, 0.0, w.WILSON_OP_HOP, stream)
+                w.wilson_dslash_h(a, g, b, 0.0, w.WILSON_OP_HOP, stream)
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            t = e0.elapsed_time(e1) / 1e3 / reps
+            bps = model.compulsory_bytes_per_site(pname, 12, eo=True, nrhs=n)
+            byts = bps * Vh
+            out[f"{prefix}hop_nrhs{n}"] = {
+                "us_per_application": round(t * 1e6, 2), "us_per_rhs": round(t * 1e6 / n, 2),
+                "GBs_compulsory": round(byts / t / 1e9, 1), "bytes_per_site_rhs": round(bps / n, 1),
+                "frac": round(byts / t / 1e9 / hbm_peak, 4),
+                "TFlops": round(model.FLOPS_PER_SITE * Vh * n / t / 1e12, 3)}
+            a.close()
+            b.close()
+        g.close()
+        out[f"{prefix}rhs_speedup_per_rhs"] = round(
+            out[f"{prefix}hop_nrhs1"]["us_per_rhs"] / out[f"{prefix}hop_nrhs{nrhs}"]["us_per_rhs"], 3)
     # lockstep 12-RHS CG vs 12 sequential solves (F16 inner, point sources at the origin)
     Ud = torch.from_numpy(U).to(dev)
     bsrc = torch.from_numpy(inputs.point_sources(dims, site=0)).to(dev)
@@ -372,6 +414,7 @@ def run_multirhs_block(w, torch, dev, stream, fields, nrhs=12):
     rc, st = w.wilson_cg_solve_multi(x, Ud, bsrc, nrhs, L, kappa, p, stream, check=False)
     torch.cuda.synchronize(dev)
     t_multi = time.perf_counter() - t0
+    x_lock = x.cpu().numpy()  # for the oracle's check in the CPU leg
     xw = torch.zeros_like(bsrc[0])
     w.wilson_cg_solve(xw, Ud, bsrc[0], L, kappa, p, stream, check=False)  # tunes the single-RHS launches
     del xw
@@ -401,6 +444,10 @@ def run_multirhs_block(w, torch, dev, stream, fields, nrhs=12):
                  "block_cg": {"rc": rcb, "seconds": round(t_block, 4),
                               "inner_iters": max(s["inner_iters"] for s in stb),
                               "max_true_rel_resid": max(s["true_rel_resid"] for s in stb)}}
+    b_host = bsrc.cpu().numpy()
+    SOLUTIONS.append((out["cg"]["block_cg"], "oracle",
+                      [(U, b_host[k], x[k].cpu().numpy(), dims, kappa) for k in range(nrhs)]))
+    SOLUTIONS.append((out["cg"], "oracle", [(U, b_host[k], x_lock[k], dims, kappa) for k in range(nrhs)]))
     del Ud, bsrc, x
     torch.cuda.empty_cache()
     return out
@@ -423,6 +470,7 @@ def run_batch_block(w, torch, dev, stream):
     torch.cuda.synchronize(dev)
     rc, st, info = w.wilson_batch_solve(fields, prm, stream, check=False)
     lat = sorted(s["seconds"] for s in st)
+    batch_x = [f["x"].cpu().numpy() for f in fields]  # for the oracle's check in the CPU leg
     sites = sum(inputs.volume(p["dims"]) for p in probs)
     # one untimed solve per lattice size tunes the single-solve launches first
     seen = set()
@@ -479,6 +527,11 @@ def run_batch_block(w, torch, dev, stream):
            "fp64_sequential_seconds": round(t_seq64, 4), "fp64_sequential_rc": rc64,
            "speedup_vs_fp64_sequential": round(t_seq64 / info["device_seconds"], 3),
            "latency_by_lattice": by_size}
+    # the oracle regenerates each problem's links from its seed in the CPU leg
+    SOLUTIONS.append((out, "oracle", [(
+        (lambda p=p: inputs.gauge_field(p["dims"], "weak", eps=p["eps"], seed=p["gauge_seed"])),
+        (lambda p=p: inputs.gaussian_spinor(p["dims"], seed=p["spinor_seed"])),
+        xk, p["dims"], p["kappa"]) for p, xk in zip(probs, batch_x)]))
     del fields
     torch.cuda.empty_cache()
     return out
@@ -556,6 +609,34 @@ def oracle_solver_baselines(line):
     return out
 
 
+def oracle_solution_checks():
+    """The oracle's verdict on every solver result the bench reports: each
+    GPU solution's true residual |b - M x| / |b| recomputed with the FP64
+    CPU oracle's Wilson matrix, and for the 24^3 x 48 solves the relative
+    difference from the plain FP64 GPU solution.  Stored into the records."""
+    import oracle
+    for entry in SOLUTIONS:
+        rec, key, probs = entry[0], entry[1], entry[2]
+        xref = entry[3] if len(entry) > 3 else None
+        t0 = time.perf_counter()
+        res = []
+        for U, b, x, dims, kappa in probs:
+            U = U() if callable(U) else U
+            b = b() if callable(b) else b
+            r = b - oracle.wilson_m(U, x, dims, kappa)
+            res.append(float(np.linalg.norm(r) / np.linalg.norm(b)))
+        out = {"true_rel_resid_max": max(res), "problems": len(res),
+               "how": "|b - M x| / |b| with the FP64 CPU oracle's M on the GPU solution"}
+        if len(res) > 1:
+            out["true_rel_resid_median"] = float(np.median(res))
+        if xref is not None:
+            x = probs[0][2]
+            out["rel_diff_vs_fp64_gpu_solution"] = float(np.linalg.norm(x - xref) / np.linalg.norm(xref))
+        out["seconds"] = round(time.perf_counter() - t0, 2)
+        rec[key] = out
+    SOLUTIONS.clear()
+
+
 def run_reference(args, ws, rank):
     if rank != 0:
         return None
@@ -606,6 +687,7 @@ def main():
         if FIRST_APPLICATION[0] is not None and ORACLE_OUTPUT[0] is not None:
             line["parity"] = parity_record(args.prec, FIRST_APPLICATION[0], ORACLE_OUTPUT[0])
         if not args.no_solver:
+            oracle_solution_checks()
             line["cpu_baseline"]["solvers"] = oracle_solver_baselines(line)
     if rank == 0:
         print(json.dumps(line), flush=True)

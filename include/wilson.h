@@ -101,7 +101,12 @@ typedef struct {
 /* ---------------------------------------------------------------------- */
 /* Stateless calls on canonical complex128 device fields (Sec. 5, Eq. 3).  */
 /* Computed in FP64 with 18-real links.  Each call packs its inputs into   */
-/* the library's workspace, so it allocates on first use.                  */
+/* workspace taken from a per-device memory pool of the library with       */
+/* stream-ordered allocation on the caller's stream (the pool keeps its    */
+/* memory, so only the first call of a size grows it).  The calls do not   */
+/* synchronise, except that the first call for a new lattice, operator    */
+/* and dagger flag times the kernel's launch configurations (autotuning)   */
+/* and so synchronises the stream once; WILSON_TUNE=0 turns that off.      */
 /* ---------------------------------------------------------------------- */
 
 /* out = D_h in (op = HOP) or M in (op = M), full lattice.
@@ -152,6 +157,8 @@ typedef struct {
     int hop_applications;     /* half-lattice hopping-term applications, all precisions */
     double true_rel_resid;    /* |b - M x| / |b|, FP64, recomputed at the end       */
     double seconds;           /* wall time of the solve (device-synchronised)        */
+    double inner_seconds;     /* device time of the inner CG iterations (CUDA events
+                                 around their replays; 0 for block CG and batches)  */
 } wilson_solve_stats;
 
 /* Default parameters for an inner precision (tol 1e-10). */
@@ -224,18 +231,32 @@ int wilson_batch_solve(int n, const wilson_problem* probs, const wilson_solver_p
 typedef struct wilson_gauge_s wilson_gauge;
 typedef struct wilson_spinor_s wilson_spinor;
 
-/* canon: 4V links, canonical complex128, host or device memory. */
+/* The link field U_{x,mu} of Eq. 3 (Sec. 5: 18 words per link, of which
+ * the 12-real form stores 12).  canon: 4V links, canonical complex128, host
+ * or device memory; prec: wilson_prec; recon: 12 or 18.  The handle owns
+ * its device copy; canon may be freed on return (the call synchronises the
+ * stream).  WILSON_ERR_ARG for invalid arguments, WILSON_ERR_OOM when the
+ * device copy cannot be allocated. */
 int wilson_gauge_create(wilson_gauge** g, const double* canon, const wilson_lattice* L, int prec,
                         int recon, void* stream);
+/* Frees the handle's device memory; NULL is accepted. */
 int wilson_gauge_destroy(wilson_gauge* g);
 
-/* subset: wilson_subset; nrhs >= 1 fields packed per site. */
+/* Storage for nrhs spinor fields psi_x of Eq. 3 (Sec. 5: 24 words per
+ * site) on one subset (wilson_subset: even, odd or full lattice), in one
+ * precision.  The contents are undefined until imported or written by an
+ * operator.  WILSON_ERR_ARG for invalid arguments, WILSON_ERR_OOM when the
+ * fields cannot be allocated. */
 int wilson_spinor_create(wilson_spinor** s, const wilson_lattice* L, int subset, int nrhs, int prec);
+/* Frees the handle's device memory; NULL is accepted. */
 int wilson_spinor_destroy(wilson_spinor* s);
 /* Bytes of device memory the handle holds. */
 long long wilson_spinor_bytes(const wilson_spinor* s);
 
-/* canon: nrhs fields back to back, each V (full) or V/2 (half) canonical
+/* Conversion between the canonical spinor layout and the handle's storage
+ * (the fields psi of Eq. 3, Sec. 5).  F16/BF16 storage quantises each
+ * site to max|component| * q with |q| <= 1 on import.
+ * canon: nrhs fields back to back, each V (full) or V/2 (half) canonical
  * spinors; host or device memory.  Device and page-locked (pinned) host
  * memory: asynchronous and ordered on the stream, like cudaMemcpyAsync (an
  * import's source must stay unchanged, and an export's destination unread,
@@ -247,7 +268,8 @@ int wilson_spinor_import(wilson_spinor* s, const double* canon, void* stream);
 int wilson_spinor_export(const wilson_spinor* s, double* canon, void* stream);
 
 /* Apply an operator to prepared fields of matching lattice and precision
- * (links stored in the spinors' precision, 12 or 18 reals).
+ * (links stored in the spinors' precision, 12 or 18 reals): the hopping
+ * term of Eq. 3 (Sec. 5) and the operators built from it.
  *   HOP:  full -> full (D_h) or parity 1-p -> parity p (D_{p,1-p})
  *   M:    full -> full
  *   SCHUR, SCHUR_DAG: parity p -> parity p (the intermediate field of the
@@ -266,9 +288,9 @@ int wilson_dslash_h(wilson_spinor* out, const wilson_gauge* g, const wilson_spin
 /* ---------------------------------------------------------------------- */
 /* No-allocation variant (the paper has no counterpart; this is a service  */
 /* of the library).  For callers that cannot let a library allocate device */
-/* memory: work issued while a stream is captured into a CUDA graph, hosts */
-/* whose allocator owns the whole device, loops that must not block in    */
-/* cudaMalloc/cudaFree.                                                     */
+/* memory: hosts whose memory manager owns the whole device (a framework's */
+/* caching allocator, a fixed arena sized to the card), and loops that     */
+/* must never block in an allocator or see a pool grow.                    */
 /* ---------------------------------------------------------------------- */
 #define WILSON_NOALLOC_SCRATCH_BYTES (32u << 20)
 
@@ -276,15 +298,36 @@ int wilson_dslash_h(wilson_spinor* out, const wilson_gauge* g, const wilson_spin
  * wilson_dslash_eo, but the packed fields live in one fixed device array of
  * WILSON_NOALLOC_SCRATCH_BYTES (32 MiB) that every GPU loading the library
  * holds until exit; nothing is allocated or freed.  Fits lattices with
- * V/2 up to about 19,000 sites (8^4, 12^4, 8^3 x 32); larger ones return
- * WILSON_ERR_ARG before any work.  The first call on a device resolves the
- * array's address on that device: make it before any stream capture.  The
- * call is asynchronous on the stream and does not synchronise.  All calls on
- * a device share the array (it keeps the last call's contents; nothing in it
- * needs clearing): calls whose GPU work overlaps race and must be serialised
- * by the caller. */
+ * V/2 up to about 19,000 sites (8^4, 12^4, 8^3 x 32, 12^3 x 22); larger ones
+ * return WILSON_ERR_ARG before any work.  The first call in a CUDA context
+ * resolves the array's device address in that context (cudaGetSymbolAddress)
+ * and caches it under the context's unique ID.  The call never times launch
+ * configurations: it uses the one an earlier wilson_dslash_eo call on the
+ * same lattice and operator chose (or the WILSON_TUNE_CACHE file holds), else
+ * a fixed default; it neither allocates nor synchronises and is
+ * asynchronous on the stream.  All calls on a device share the array (it
+ * keeps the last call's contents; nothing in it needs clearing): calls whose
+ * GPU work overlaps race on it and must be serialised by the caller. */
 int wilson_dslash_eo_noalloc(double* out, const double* gauge, const double* in, const wilson_lattice* L,
                              int out_parity, double kappa, int op, void* stream);
+
+/* ---------------------------------------------------------------------- */
+/* Measurement: the device's peak FP rate (Sec. 3: T_peak is the time the  */
+/* FP operations take at the machine's peak FP throughput, and the         */
+/* efficiency of Eq. 2's model is T_peak over the execution time).         */
+/* ---------------------------------------------------------------------- */
+typedef enum {
+    WILSON_PROBE_FMA_F64 = 0,    /* FP64 fused multiply-add                        */
+    WILSON_PROBE_FMA_F32 = 1,    /* FP32 fused multiply-add                        */
+    WILSON_PROBE_FMA_F32X2 = 2   /* paired FP32 fused multiply-add (two lanes each) */
+} wilson_probe_kind;
+
+/* Measures the current device's peak rate of one kind of FMA: a kernel of
+ * independent FMA chains on every SM at full occupancy, timed with CUDA
+ * events on the stream (best of three launches of about 50-100 ms each).
+ * *gflops: 2 flops per FMA (per lane).  Allocates a small result buffer and
+ * synchronises the stream.  WILSON_ERR_ARG for an unknown kind. */
+int wilson_probe_fma_peak(int kind, double* gflops, void* stream);
 
 /* ---------------------------------------------------------------------- */
 /* Errors and version                                                      */

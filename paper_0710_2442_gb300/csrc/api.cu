@@ -40,42 +40,6 @@ int guarded(F&& f) {
     }
 }
 
-// Checks shared by all entry points; returns the geometry.
-Geom checked_geom(const wilson_lattice* L) {
-    WL_REQUIRE(L != nullptr, "lattice descriptor is NULL");
-    long long V = 1;
-    for (int mu = 0; mu < 4; mu++) {
-        const int d = L->dims[mu];
-        WL_REQUIRE(d >= 2 && (d % 2) == 0, "every lattice extent must be even and >= 2");
-        V *= d;
-        const double re = L->bc_phase[mu][0], im = L->bc_phase[mu][1];
-        WL_REQUIRE(std::isfinite(re) && std::isfinite(im) && std::fabs(re * re + im * im - 1.0) <= 1e-12,
-                   "boundary phases must have unit modulus");
-    }
-    WL_REQUIRE(V < (1LL << 31), "lattice volume must be below 2^31 sites");
-    return make_geom(L->dims, L->bc_phase);
-}
-
-void check_ptr(const void* p, const char* what) {
-    WL_REQUIRE(p != nullptr, std::string(what) + " is NULL");
-    WL_REQUIRE((reinterpret_cast<uintptr_t>(p) & 15) == 0, std::string(what) + " is not 16-byte aligned");
-}
-
-void check_device() {
-    int n = 0;
-    cudaError_t e = cudaGetDeviceCount(&n);
-    if (e != cudaSuccess || n == 0) throw Error(WILSON_ERR_CUDA, "no CUDA device available");
-}
-
-bool is_device_ptr(const void* p) {
-    cudaPointerAttributes a;
-    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
-        cudaGetLastError();
-        return false;
-    }
-    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
-}
-
 Prec to_prec(int p) {
     WL_REQUIRE(p >= WILSON_F64 && p <= WILSON_BF16, "unknown precision");
     return static_cast<Prec>(p);
@@ -159,9 +123,115 @@ SolveStream& solve_stream() {
     return ss;
 }
 
+
+// Workspace of the stateless operator calls: one memory pool per device that
+// keeps its memory after release (release threshold: unlimited).  A call
+// takes its packed fields from the pool with cudaMallocFromPoolAsync and
+// returns them with cudaFreeAsync, both ordered on the caller's stream, so
+// the call never synchronises: the pool reuses the memory once the stream
+// has passed the release (a later call on another stream gets other memory
+// or an ordering dependency the pool inserts).  Only the first call of a new
+// size grows the pool.
+cudaMemPool_t stateless_pool() {
+    static std::mutex m;
+    static cudaMemPool_t pools[64] = {};
+    int dev = 0;
+    WL_CUDA(cudaGetDevice(&dev));
+    WL_REQUIRE(dev >= 0 && dev < 64, "device ordinal out of range");
+    std::lock_guard<std::mutex> lk(m);
+    if (!pools[dev]) {
+        cudaMemPoolProps props = {};
+        props.allocType = cudaMemAllocationTypePinned;
+        props.handleTypes = cudaMemHandleTypeNone;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = dev;
+        cudaMemPool_t pool = nullptr;
+        WL_CUDA(cudaMemPoolCreate(&pool, &props));
+        unsigned long long keep = ~0ULL;
+        WL_CUDA(cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep));
+        pools[dev] = pool;
+    }
+    return pools[dev];
+}
+
+// Stream-ordered allocations of one call, released on the stream when the
+// call's scope ends (also when it throws).
+struct StreamAllocs {
+    cudaStream_t st;
+    void* p[4] = {nullptr, nullptr, nullptr, nullptr};
+    int n = 0;
+    explicit StreamAllocs(cudaStream_t s) : st(s) {}
+    void* get(size_t bytes) {
+        void* q = nullptr;
+        WL_CUDA(cudaMallocFromPoolAsync(&q, bytes, stateless_pool(), st));
+        p[n++] = q;
+        return q;
+    }
+    ~StreamAllocs() {
+        for (int i = 0; i < n; i++) cudaFreeAsync(p[i], st);
+    }
+};
+
+// A packed FP64 field of one parity subset (0, 1 or 2 = both) in pool memory.
+void borrow_spinor(SpinorField& f, int subset, const Geom& g, StreamAllocs& a, BorrowGuard& guard) {
+    f.prec = P_F64;
+    f.subset = subset;
+    f.nrhs = 1;
+    f.g = g;
+    f.pbytes = spinor_field_bytes(P_F64, g.stride);
+    const size_t bytes = (size_t)f.pbytes * f.nparity();
+    guard.borrow(f.buf, a.get(bytes), bytes);
+}
+void borrow_gauge(GaugeField& gf, const Geom& g, StreamAllocs& a, BorrowGuard& guard) {
+    gf.prec = P_F64;
+    gf.recon = 18;
+    gf.g = g;
+    const size_t bytes = (size_t)gauge_bytes(P_F64, 18, g.stride);
+    guard.borrow(gf.buf, a.get(bytes), bytes);
+}
+
 }  // namespace
 
 void wl::record_error(const std::string& msg) { g_last_error = msg; }
+
+// Checks shared by all entry points (declared in internal.h).
+Geom wl::checked_geom(const wilson_lattice* L) {
+    WL_REQUIRE(L != nullptr, "lattice descriptor is NULL");
+    long long V = 1;
+    for (int mu = 0; mu < 4; mu++) {
+        const int d = L->dims[mu];
+        WL_REQUIRE(d >= 2 && (d % 2) == 0, "every lattice extent must be even and >= 2");
+        V *= d;
+        const double re = L->bc_phase[mu][0], im = L->bc_phase[mu][1];
+        WL_REQUIRE(std::isfinite(re) && std::isfinite(im) && std::fabs(re * re + im * im - 1.0) <= 1e-12,
+                   "boundary phases must have unit modulus");
+    }
+    WL_REQUIRE(V < (1LL << 31), "lattice volume must be below 2^31 sites");
+    return make_geom(L->dims, L->bc_phase);
+}
+
+void wl::check_ptr(const void* p, const char* what) {
+    WL_REQUIRE(p != nullptr, std::string(what) + " is NULL");
+    WL_REQUIRE((reinterpret_cast<uintptr_t>(p) & 15) == 0, std::string(what) + " is not 16-byte aligned");
+}
+
+void wl::check_device() {
+    int n = 0;
+    cudaError_t e = cudaGetDeviceCount(&n);
+    if (e != cudaSuccess || n == 0) {
+        cudaGetLastError();
+        throw Error(WILSON_ERR_CUDA, "no CUDA device available");
+    }
+}
+
+bool wl::is_device_ptr(const void* p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
 
 struct wilson_gauge_s {
     GaugeField f;
@@ -208,15 +278,14 @@ int wilson_dslash(double* out, const double* gauge, const double* in, const wils
         WL_REQUIRE(is_device_ptr(out) && is_device_ptr(in) && is_device_ptr(gauge),
                    "wilson_dslash takes device pointers");
         cudaStream_t st = static_cast<cudaStream_t>(stream);
+        StreamAllocs mem(st);
         GaugeField gf;
-        gf.prec = P_F64;
-        gf.recon = 18;
-        gf.g = g;
-        gf.buf.alloc(gauge_bytes(P_F64, 18, g.stride));
-        pack_gauge(gf, gauge, st);
         SpinorField a, b;
-        a.alloc(P_F64, 2, 1, g);
-        b.alloc(P_F64, 2, 1, g);
+        BorrowGuard guard;  // declared last: detaches the views first, and mem releases the memory last
+        borrow_gauge(gf, g, mem, guard);
+        borrow_spinor(a, 2, g, mem, guard);
+        borrow_spinor(b, 2, g, mem, guard);
+        pack_gauge(gf, gauge, st);
         pack_spinor(a, 0, in, st);
         HopLaunch h{};
         h.out = b.block(0);
@@ -232,8 +301,6 @@ int wilson_dslash(double* out, const double* gauge, const double* in, const wils
         h.a = op == WILSON_OP_M ? -kappa : 1.0;
         launch_hop(h, st);
         unpack_spinor(b, 0, out, st);
-        // the temporaries are freed on return: finish before releasing them
-        WL_CUDA(cudaStreamSynchronize(st));
     });
 }
 
@@ -253,16 +320,15 @@ int wilson_dslash_eo(double* out, const double* gauge, const double* in, const w
         WL_REQUIRE(is_device_ptr(out) && is_device_ptr(in) && is_device_ptr(gauge),
                    "wilson_dslash_eo takes device pointers");
         cudaStream_t st = static_cast<cudaStream_t>(stream);
-        GaugeField gf;
-        gf.prec = P_F64;
-        gf.recon = 18;
-        gf.g = g;
-        gf.buf.alloc(gauge_bytes(P_F64, 18, g.stride));
-        pack_gauge(gf, gauge, st);
+        StreamAllocs mem(st);
         const int pin = op == WILSON_OP_HOP ? 1 - out_parity : out_parity;
+        GaugeField gf;
         SpinorField a, b, t;
-        a.alloc(P_F64, pin, 1, g);
-        b.alloc(P_F64, out_parity, 1, g);
+        BorrowGuard guard;  // declared last: detaches the views first, and mem releases the memory last
+        borrow_gauge(gf, g, mem, guard);
+        borrow_spinor(a, pin, g, mem, guard);
+        borrow_spinor(b, out_parity, g, mem, guard);
+        pack_gauge(gf, gauge, st);
         pack_spinor(a, 0, in, st);
         if (op == WILSON_OP_HOP) {
             HopLaunch h{};
@@ -275,7 +341,7 @@ int wilson_dslash_eo(double* out, const double* gauge, const double* in, const w
             launch_hop(h, st);
         } else {
             // Mhat_p = 1 - kappa^2 D_{p,1-p} D_{1-p,p}
-            t.alloc(P_F64, 1 - out_parity, 1, g);
+            borrow_spinor(t, 1 - out_parity, g, mem, guard);
             const int dag = op == WILSON_OP_SCHUR_DAG;
             HopLaunch h1{};
             h1.out = t.block(1 - out_parity);
@@ -299,7 +365,6 @@ int wilson_dslash_eo(double* out, const double* gauge, const double* in, const w
             launch_hop(h2, st);
         }
         unpack_spinor(b, 0, out, st);
-        WL_CUDA(cudaStreamSynchronize(st));
     });
 }
 
@@ -329,6 +394,7 @@ static void copy_stats(wilson_solve_stats* o, const SolveStats& s, int rc) {
     o->hop_applications = s.hop_applications;
     o->true_rel_resid = s.true_rel_resid;
     o->seconds = s.seconds;
+    o->inner_seconds = s.inner_seconds;
 }
 
 int wilson_cg_solve(double* x, const double* gauge, const double* b, const wilson_lattice* L, double kappa,

@@ -106,9 +106,12 @@ void launch_hop(const HopLaunch& L, cudaStream_t st) {
             for (int block : {64, 128, 256})
                 for (int v = kHopBaseVariants; v < kHopVariants; v++)
                     if (hop_variant_valid(v, sp, R, P.nrhs)) cands.push_back(LaunchConfig{block, v});
-        cfg = tune_launch(key, cands, LaunchConfig{}, st, [&](const LaunchConfig& c) {
-            dispatch(Pt, sp, gp, R, c.block, hop_grid_blocks(Pt.g, c.block, 0), ny, dag, c.variant, st);
-        });
+        if (L.no_tune)
+            cfg = tune_lookup(key, cands, LaunchConfig{});
+        else
+            cfg = tune_launch(key, cands, LaunchConfig{}, st, [&](const LaunchConfig& c) {
+                dispatch(Pt, sp, gp, R, c.block, hop_grid_blocks(Pt.g, c.block, 0), ny, dag, c.variant, st);
+            });
     }
     WL_REQUIRE(hop_variant_valid(cfg.variant, sp, R, P.nrhs), "hop variant does not fit this launch");
     // the link-staged kernel has no fused reduction: reducing launches take

@@ -9,6 +9,7 @@
 
 #include <nvtx3/nvToolsExt.h>
 
+#include "../../include/wilson.h"
 #include "common.cuh"
 #include "reduce.cuh"
 
@@ -113,6 +114,11 @@ struct LaunchConfig {
 LaunchConfig tune_launch(const std::string& key, const std::vector<LaunchConfig>& candidates,
                          const LaunchConfig& fallback, cudaStream_t st,
                          const std::function<void(const LaunchConfig&)>& run);
+// The decision for `key` if one is cached (in memory or in the cache file)
+// and among `candidates`, else `fallback`; never times anything and never
+// synchronises.
+LaunchConfig tune_lookup(const std::string& key, const std::vector<LaunchConfig>& candidates,
+                         const LaunchConfig& fallback);
 const std::vector<LaunchConfig>& hop_candidates();
 
 // Geometry from dims and phases; stride rounded up to 64 sites.
@@ -197,6 +203,7 @@ struct HopLaunch {
     int variant;           // kernel register-budget variant when block > 0
     int grid_cap;          // max blocks of a reducing launch (0 = no cap)
     int tune_only;         // 1: tune the launch configuration if it is not known yet, launch nothing else
+    int no_tune;           // 1: take a cached decision or the default configuration, never time candidates
 };
 void launch_hop(const HopLaunch& L, cudaStream_t st);
 int hop_grid_blocks(const Geom& g, int block, int grid_cap);
@@ -216,5 +223,31 @@ struct NvtxRange {
 
 // Set the calling thread's message returned by wilson_last_error().
 void record_error(const std::string& msg);
+
+// Argument checks shared by the entry points (api.cu), so that every entry
+// point validates the same way.
+Geom checked_geom(const wilson_lattice* L);      // extents, phases, volume; WILSON_ERR_ARG
+void check_ptr(const void* p, const char* what);  // non-null and 16-byte aligned; WILSON_ERR_ARG
+void check_device();                              // a CUDA device exists; WILSON_ERR_CUDA
+bool is_device_ptr(const void* p);                // device or managed memory
+
+// DevBuf objects that borrow memory the library does not own through them
+// (a fixed array, a stream-ordered pool): the guard detaches them before
+// their destructors run, so those never free it.
+struct BorrowGuard {
+    DevBuf* bufs[8];
+    int n = 0;
+    void borrow(DevBuf& b, void* p, size_t bytes) {
+        b.p = p;
+        b.bytes = bytes;
+        bufs[n++] = &b;
+    }
+    ~BorrowGuard() {
+        for (int i = 0; i < n; i++) {
+            bufs[i]->p = nullptr;
+            bufs[i]->bytes = 0;
+        }
+    }
+};
 
 }  // namespace wl

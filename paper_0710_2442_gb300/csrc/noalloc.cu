@@ -2,26 +2,31 @@
 // Schur operator on canonical FP64 device fields, with no device allocation.
 //
 // Why it exists.  wilson_dslash_eo packs its canonical inputs into the
-// kernels' SoA layout in memory it allocates per call.  Some callers cannot
-// let a library call cudaMalloc: code issuing work while a stream is being
-// captured into a CUDA graph (allocation is not permitted there), hosts whose
-// memory manager owns the whole device (a framework caching allocator or a
-// fixed arena), and latency-critical loops that must never block on the
-// allocator or trigger an implicit device synchronisation in cudaFree.  This
-// entry point runs the same kernels with the packed fields placed in one
-// file-scope device array of fixed size instead.
+// kernels' SoA layout in memory it takes from a device memory pool.  Some
+// callers cannot let a library allocate device memory at all: hosts whose
+// memory manager owns the whole device (a framework's caching allocator, a
+// fixed arena sized to the card), and latency-critical loops that must never
+// block in the allocator or grow a pool behind the caller's back.  This entry
+// point runs the same kernels with the packed fields placed in one file-scope
+// device array of fixed size instead.
 //
 // The scratch array.  WILSON_NOALLOC_SCRATCH_BYTES (32 MiB) of device memory
 // declared below; every GPU that loads the library holds it until the
 // process exits.  It holds the packed FP64 links (1152 B per half-lattice
 // site) and up to three packed FP64 half fields (192 B per site each), so
-// lattices with V/2 up to about 19,000 sites fit (8^4, 12^4, 8^3 x 32, ...).
+// lattices with V/2 up to about 19,000 sites fit (8^4, 12^4, 12^3 x 22, ...).
 // Larger lattices are rejected with WILSON_ERR_ARG before anything runs.
 //
 // Host code cannot use the array's name as a device address: in host code
-// the name denotes a host-side stand-in.  The first call on each device (with
-// that device current) resolves the real address with cudaGetSymbolAddress
-// and caches it; make that first call before any stream capture begins.
+// the name denotes a host-side stand-in.  The first call in each CUDA
+// context (with that context's device current) resolves the real address
+// with cudaGetSymbolAddress and caches it under the context's unique ID, so
+// a context torn down and created again (cudaDeviceReset) resolves it anew.
+//
+// No tuning, no synchronisation.  The call never times launch
+// configurations: it takes the one an earlier wilson_dslash_eo call on the
+// same lattice chose (or the WILSON_TUNE_CACHE file holds), else a fixed
+// default.  It neither allocates nor synchronises.
 //
 // Sharing.  All calls on a device use the same array, and it keeps whatever
 // the previous call left there.  Nothing here needs it cleared: every byte a
@@ -29,7 +34,10 @@
 // on the given stream; two calls whose work overlaps on the GPU (different
 // streams, or host threads) race on the array and must be serialised by the
 // caller.
+#include <cuda.h>
+
 #include <cmath>
+#include <map>
 #include <mutex>
 #include <string>
 
@@ -42,51 +50,62 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[WILSON_NOALLOC_
 
 namespace {
 
-constexpr int kMaxDevices = 64;
 std::mutex g_scratch_mutex;
-void* g_scratch_addr[kMaxDevices] = {nullptr};
 
-// Device address of the scratch array on the current device (resolved once
-// per device).
-void* scratch_address() {
-    int dev = 0;
-    WL_CUDA(cudaGetDevice(&dev));
-    WL_REQUIRE(dev >= 0 && dev < kMaxDevices, "device ordinal out of range");
-    std::lock_guard<std::mutex> lk(g_scratch_mutex);
-    if (!g_scratch_addr[dev]) {
-        void* p = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        if (e != cudaSuccess || p == nullptr)
-            throw Error(WILSON_ERR_CUDA, std::string("cudaGetSymbolAddress(no-allocation scratch): ") +
-                                             cudaGetErrorString(e));
-        g_scratch_addr[dev] = p;
+// Unique ID of the current CUDA context (never reused within a process), or
+// 0 where the driver does not provide one.  Driver entry points are taken
+// through the runtime, so the library does not link the driver library.
+unsigned long long current_context_id() {
+    using GetCurrent = CUresult (*)(CUcontext*);
+    using GetId = CUresult (*)(CUcontext, unsigned long long*);
+    static GetCurrent get_current = nullptr;
+    static GetId get_id = nullptr;
+    static bool looked_up = false;
+    if (!looked_up) {
+        void* f1 = nullptr;
+        void* f2 = nullptr;
+        cudaDriverEntryPointQueryResult q1, q2;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f1, 12000, cudaEnableDefault, &q1) ==
+                cudaSuccess &&
+            q1 == cudaDriverEntryPointSuccess &&
+            cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000, cudaEnableDefault, &q2) == cudaSuccess &&
+            q2 == cudaDriverEntryPointSuccess) {
+            get_current = reinterpret_cast<GetCurrent>(f1);
+            get_id = reinterpret_cast<GetId>(f2);
+        }
+        cudaGetLastError();
+        looked_up = true;
     }
-    return g_scratch_addr[dev];
+    if (!get_current || !get_id) return 0;
+    CUcontext ctx = nullptr;
+    unsigned long long id = 0;
+    if (get_current(&ctx) != CUDA_SUCCESS || ctx == nullptr || get_id(ctx, &id) != CUDA_SUCCESS) return 0;
+    return id;
 }
 
-bool on_device(const void* p) {
-    cudaPointerAttributes a;
-    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
-        cudaGetLastError();
-        return false;
+// Device address of the scratch array in the current context (resolved once
+// per context; resolved on every call where the driver gives no context ID).
+void* scratch_address() {
+    // The runtime calls before this one (pointer attributes) made the device's
+    // primary context current; without a current context the ID is 0 and the
+    // address is resolved afresh.
+    std::lock_guard<std::mutex> lk(g_scratch_mutex);
+    static std::map<unsigned long long, void*> addr;
+    const unsigned long long ctx = current_context_id();
+    if (ctx != 0) {
+        auto it = addr.find(ctx);
+        if (it != addr.end()) return it->second;
     }
-    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || p == nullptr)
+        throw Error(WILSON_ERR_CUDA,
+                    std::string("cudaGetSymbolAddress(no-allocation scratch): ") + cudaGetErrorString(e));
+    if (ctx != 0) addr[ctx] = p;
+    return p;
 }
 
 size_t align256(size_t n) { return (n + 255) / 256 * 256; }
-
-// Non-owning views into the scratch array; the guard detaches them before
-// the views' destructors run, so nothing is ever freed.
-struct ViewGuard {
-    DevBuf* bufs[4];
-    int n = 0;
-    ~ViewGuard() {
-        for (int i = 0; i < n; i++) {
-            bufs[i]->p = nullptr;
-            bufs[i]->bytes = 0;
-        }
-    }
-};
 
 }  // namespace
 
@@ -94,27 +113,15 @@ extern "C" int wilson_dslash_eo_noalloc(double* out, const double* gauge, const 
                                         const wilson_lattice* L, int out_parity, double kappa, int op,
                                         void* stream) {
     try {
-        WL_REQUIRE(L != nullptr, "lattice descriptor is NULL");
-        long long V = 1;
-        for (int mu = 0; mu < 4; mu++) {
-            const int d = L->dims[mu];
-            WL_REQUIRE(d >= 2 && (d % 2) == 0, "every lattice extent must be even and >= 2");
-            V *= d;
-            const double re = L->bc_phase[mu][0], im = L->bc_phase[mu][1];
-            WL_REQUIRE(std::isfinite(re) && std::isfinite(im) && std::fabs(re * re + im * im - 1.0) <= 1e-12,
-                       "boundary phases must have unit modulus");
-        }
-        WL_REQUIRE(V < (1LL << 31), "lattice volume must be below 2^31 sites");
-        for (const void* p : {(const void*)out, (const void*)gauge, (const void*)in}) {
-            WL_REQUIRE(p != nullptr, "a field pointer is NULL");
-            WL_REQUIRE((reinterpret_cast<uintptr_t>(p) & 15) == 0, "field pointers must be 16-byte aligned");
-        }
+        const Geom g = checked_geom(L);
+        check_ptr(out, "out");
+        check_ptr(gauge, "gauge");
+        check_ptr(in, "in");
         WL_REQUIRE(out_parity == 0 || out_parity == 1, "out_parity must be 0 or 1");
         WL_REQUIRE(op == WILSON_OP_HOP || op == WILSON_OP_SCHUR || op == WILSON_OP_SCHUR_DAG,
                    "op must be HOP, SCHUR or SCHUR_DAG");
         WL_REQUIRE(std::isfinite(kappa), "kappa must be finite");
         WL_REQUIRE(out != in, "out must not alias in");
-        const Geom g = make_geom(L->dims, L->bc_phase);
 
         // scratch layout: links | in | out | tmp
         const size_t gbytes = align256((size_t)gauge_bytes(P_F64, 18, g.stride));
@@ -124,12 +131,8 @@ extern "C" int wilson_dslash_eo_noalloc(double* out, const double* gauge, const 
             throw Error(WILSON_ERR_ARG, "lattice too large for the no-allocation scratch: needs " +
                                             std::to_string(need) + " bytes, the array holds " +
                                             std::to_string((size_t)WILSON_NOALLOC_SCRATCH_BYTES));
-        int ndev = 0;
-        if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
-            cudaGetLastError();
-            throw Error(WILSON_ERR_CUDA, "no CUDA device available");
-        }
-        WL_REQUIRE(on_device(out) && on_device(in) && on_device(gauge),
+        check_device();
+        WL_REQUIRE(is_device_ptr(out) && is_device_ptr(in) && is_device_ptr(gauge),
                    "wilson_dslash_eo_noalloc takes device pointers");
         char* base = static_cast<char*>(scratch_address());
         cudaStream_t st = static_cast<cudaStream_t>(stream);
@@ -137,24 +140,18 @@ extern "C" int wilson_dslash_eo_noalloc(double* out, const double* gauge, const 
         const int pin = op == WILSON_OP_HOP ? 1 - out_parity : out_parity;
         GaugeField gf;
         SpinorField a, b, t;
-        ViewGuard guard;
-        guard.bufs[guard.n++] = &gf.buf;
-        guard.bufs[guard.n++] = &a.buf;
-        guard.bufs[guard.n++] = &b.buf;
-        guard.bufs[guard.n++] = &t.buf;
+        BorrowGuard guard;  // the views never free the array
         gf.prec = P_F64;
         gf.recon = 18;
         gf.g = g;
-        gf.buf.p = base;
-        gf.buf.bytes = gbytes;
+        guard.borrow(gf.buf, base, gbytes);
         auto view = [&](SpinorField& f, int subset, size_t off) {
             f.prec = P_F64;
             f.subset = subset;
             f.nrhs = 1;
             f.g = g;
             f.pbytes = (long long)pbytes;
-            f.buf.p = base + off;
-            f.buf.bytes = pbytes;
+            guard.borrow(f.buf, base + off, pbytes);
         };
         view(a, pin, gbytes);
         view(b, out_parity, gbytes + pbytes);
@@ -168,6 +165,7 @@ extern "C" int wilson_dslash_eo_noalloc(double* out, const double* gauge, const 
             h.in = a.block(pin);
             h.gauge = &gf;
             h.sprec = P_F64;
+            h.no_tune = 1;
             h.out_parity = out_parity;
             h.a = 1.0;
             launch_hop(h, st);
@@ -178,6 +176,7 @@ extern "C" int wilson_dslash_eo_noalloc(double* out, const double* gauge, const 
             h1.in = a.block(pin);
             h1.gauge = &gf;
             h1.sprec = P_F64;
+            h1.no_tune = 1;
             h1.out_parity = 1 - out_parity;
             h1.dagger = dag;
             h1.a = 1.0;
@@ -190,6 +189,7 @@ extern "C" int wilson_dslash_eo_noalloc(double* out, const double* gauge, const 
             h2.a = -kappa * kappa;
             h2.gauge = &gf;
             h2.sprec = P_F64;
+            h2.no_tune = 1;
             h2.out_parity = out_parity;
             h2.dagger = dag;
             launch_hop(h2, st);

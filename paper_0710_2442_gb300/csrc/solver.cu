@@ -244,6 +244,11 @@ std::vector<SolveStats> cg_solve_prepared(SpinorField& x, const SpinorField& b, 
     std::vector<double> best(nr, HUGE_VAL);  // smallest FP64 residual so far
     int outer = 0;
     bool first = true;
+    // device time of the inner iterations: events around each chunk's replay
+    cudaEvent_t ev_in0 = nullptr, ev_in1 = nullptr;
+    WL_CUDA(cudaEventCreate(&ev_in0));
+    WL_CUDA(cudaEventCreate(&ev_in1));
+    double inner_ms = 0.0;
     try {
         while (true) {
             // r64 = bhat - Mhat x_e (FP64); the first residual of a solve from
@@ -356,13 +361,20 @@ std::vector<SolveStats> cg_solve_prepared(SpinorField& x, const SpinorField& b, 
             first = false;
 
             while (true) {
+                WL_CUDA(cudaEventRecord(ev_in0, st));
                 if (gexec) {
                     WL_CUDA(cudaGraphLaunch(gexec, st));
                 } else {
                     for (int it = 0; it < chunk; it++) iteration(st);
                 }
+                WL_CUDA(cudaEventRecord(ev_in1, st));
                 WL_CUDA(cudaMemcpyAsync(h_sc, sc, sizeof(CGScalars) * nr, cudaMemcpyDeviceToHost, st));
                 WL_CUDA(cudaStreamSynchronize(st));
+                {
+                    float ms = 0.f;
+                    WL_CUDA(cudaEventElapsedTime(&ms, ev_in0, ev_in1));
+                    inner_ms += ms;
+                }
                 bool all = true;
                 for (int k = 0; k < nr; k++) all = all && h_sc[k].done != 0;
                 if (all) break;
@@ -383,10 +395,14 @@ std::vector<SolveStats> cg_solve_prepared(SpinorField& x, const SpinorField& b, 
     } catch (...) {
         if (gexec) cudaGraphExecDestroy(gexec);
         if (graph) cudaGraphDestroy(graph);
+        cudaEventDestroy(ev_in0);
+        cudaEventDestroy(ev_in1);
         throw;
     }
     if (gexec) cudaGraphExecDestroy(gexec);
     if (graph) cudaGraphDestroy(graph);
+    cudaEventDestroy(ev_in0);
+    cudaEventDestroy(ev_in1);
 
     // x_o = b_o + kappa D_oe x_e
     {
@@ -445,6 +461,7 @@ std::vector<SolveStats> cg_solve_prepared(SpinorField& x, const SpinorField& b, 
         s.outer_iters = outer;
         s.hop_applications = hops;
         s.seconds = secs;
+        s.inner_seconds = inner_ms * 1e-3;
         if (s.status == 0 && !(s.true_rel_resid <= prm.tol)) s.status = std::isfinite(s.true_rel_resid) ? 4 : 6;
     }
     return stats;

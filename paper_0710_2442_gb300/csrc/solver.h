@@ -51,6 +51,7 @@ struct SolveStats {
     int hop_applications = 0;
     double true_rel_resid = 0.0;
     double seconds = 0.0;
+    double inner_seconds = 0.0;  // device time of the inner CG iterations (graph replays)
 };
 
 // Mhat (dag = 0) or Mhat^dag (dag = 1) on even blocks of nrhs right-hand

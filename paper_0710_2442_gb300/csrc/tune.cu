@@ -44,16 +44,31 @@ bool env_flag(const char* name, bool dflt) {
     return !(v[0] == '0' && v[1] == 0);
 }
 
+// "sm<major><minor>-<SM count>" of the current device, looked up once per
+// device ordinal (every hop launch asks for it).
 std::string device_tag() {
+    static std::mutex m;
+    static std::string tags[64];
     int dev = 0;
     cudaGetDevice(&dev);
-    cudaDeviceProp prop;
-    if (cudaGetDeviceProperties(&prop, dev) != cudaSuccess) {
+    const bool cacheable = dev >= 0 && dev < 64;
+    if (cacheable) {
+        std::lock_guard<std::mutex> lk(m);
+        if (!tags[dev].empty()) return tags[dev];
+    }
+    int major = 0, minor = 0, sms = 0;
+    if (cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
         cudaGetLastError();
         return "dev?";
     }
     char buf[64];
-    snprintf(buf, sizeof(buf), "sm%d%d-%d", prop.major, prop.minor, prop.multiProcessorCount);
+    snprintf(buf, sizeof(buf), "sm%d%d-%d", major, minor, sms);
+    if (cacheable) {
+        std::lock_guard<std::mutex> lk(m);
+        tags[dev] = buf;
+    }
     return buf;
 }
 
@@ -90,21 +105,38 @@ const std::vector<LaunchConfig>& hop_candidates() {
     return c;
 }
 
+namespace {
+
+// The cached decision for the device-tagged key, if it is among the current
+// candidates.
+bool cached(const std::string& key, const std::vector<LaunchConfig>& candidates, LaunchConfig& out) {
+    std::lock_guard<std::mutex> lk(g_mutex);
+    if (!g_cache) g_cache = new std::map<std::string, Entry>();
+    if (!g_loaded) load_file();
+    auto it = g_cache->find(key);
+    if (it == g_cache->end()) return false;
+    bool known = candidates.empty();
+    for (const LaunchConfig& c : candidates)
+        known = known || (c.block == it->second.cfg.block && c.variant == it->second.cfg.variant);
+    if (known) out = it->second.cfg;
+    return known;
+}
+
+}  // namespace
+
+LaunchConfig tune_lookup(const std::string& key0, const std::vector<LaunchConfig>& candidates,
+                         const LaunchConfig& fallback) {
+    LaunchConfig c;
+    return cached(device_tag() + "|" + key0, candidates, c) ? c : fallback;
+}
+
 LaunchConfig tune_launch(const std::string& key0, const std::vector<LaunchConfig>& candidates,
                          const LaunchConfig& fallback, cudaStream_t st,
                          const std::function<void(const LaunchConfig&)>& run) {
     const std::string key = device_tag() + "|" + key0;
     {
-        std::lock_guard<std::mutex> lk(g_mutex);
-        if (!g_cache) g_cache = new std::map<std::string, Entry>();
-        if (!g_loaded) load_file();
-        auto it = g_cache->find(key);
-        if (it != g_cache->end()) {
-            bool known = candidates.empty();
-            for (const LaunchConfig& c : candidates)
-                known = known || (c.block == it->second.cfg.block && c.variant == it->second.cfg.variant);
-            if (known) return it->second.cfg;
-        }
+        LaunchConfig c;
+        if (cached(key, candidates, c)) return c;
     }
     if (!env_flag("WILSON_TUNE", true) || candidates.empty()) return fallback;
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;

@@ -50,3 +50,18 @@ def cell_table1(sites_per_spe, sites_per_cell, a_ext, clock_hz=3.2e9, n_spe=8,
     if sites_per_cell is not None:
         out["T_mem"] = sites_per_cell * compulsory_bytes_per_site("f64", 18, eo=False) / beta_mem * clock_hz
     return out
+
+
+def cg_inner_bytes_per_site(inner: str, recon: int = 12) -> int:
+    """Algorithmic bytes per even site of one inner CG iteration of the
+    solver, counted over its six launches: two Schur operators (four hops;
+    the second hop of each also reads the xpay field), the x/s update (x and s
+    read and written in the accumulation precision, p and q read, and for
+    F16/BF16 the copy of s in storage precision written), and p = r + beta p."""
+    S = SPINOR_BYTES[inner]
+    L = LINK_BYTES[(inner, recon)]
+    X = SPINOR_BYTES["f64" if inner == "f64" else "f32"]
+    schur = (2 * S + 8 * L) + (3 * S + 8 * L)
+    xs = 4 * X + 2 * S + (S if inner in ("f16", "bf16") else 0)
+    p_update = 3 * S
+    return 2 * schur + xs + p_update

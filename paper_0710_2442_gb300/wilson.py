@@ -21,6 +21,7 @@ WILSON_OK, WILSON_ERR_ARG, WILSON_ERR_CUDA, WILSON_ERR_OOM, WILSON_ERR_NOCONV, W
 WILSON_F64, WILSON_F32, WILSON_F16, WILSON_BF16 = range(4)
 WILSON_OP_HOP, WILSON_OP_M, WILSON_OP_SCHUR, WILSON_OP_SCHUR_DAG = range(4)
 WILSON_EVEN, WILSON_ODD, WILSON_FULL = range(3)
+WILSON_PROBE_FMA_F64, WILSON_PROBE_FMA_F32, WILSON_PROBE_FMA_F32X2 = range(3)
 PREC = {"f64": WILSON_F64, "f32": WILSON_F32, "f16": WILSON_F16, "bf16": WILSON_BF16}
 
 
@@ -43,7 +44,7 @@ class wilson_solver_params(ctypes.Structure):
 class wilson_solve_stats(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int), ("outer_iters", ctypes.c_int), ("inner_iters", ctypes.c_int),
                 ("hop_applications", ctypes.c_int), ("true_rel_resid", ctypes.c_double),
-                ("seconds", ctypes.c_double)]
+                ("seconds", ctypes.c_double), ("inner_seconds", ctypes.c_double)]
 
 
 class wilson_problem(ctypes.Structure):
@@ -84,6 +85,7 @@ def _declare(lib):
         "wilson_spinor_import": (I, [VP, VP, VP]),
         "wilson_spinor_export": (I, [VP, VP, VP]),
         "wilson_dslash_h": (I, [VP, VP, VP, D, I, VP]),
+        "wilson_probe_fma_peak": (I, [I, P(D), VP]),
         "wilson_last_error": (ctypes.c_char_p, []),
         "wilson_version": (I, []),
     }
@@ -273,6 +275,13 @@ class Spinor:
             self.close()
         except Exception:
             pass
+
+
+def wilson_probe_fma_peak(kind: int, stream=None) -> float:
+    """Measured peak GFLOP/s of one FMA kind (WILSON_PROBE_FMA_*)."""
+    v = ctypes.c_double(0.0)
+    _check(lib().wilson_probe_fma_peak(int(kind), ctypes.byref(v), _stream(stream)))
+    return v.value
 
 
 def wilson_dslash_h(out: Spinor, gauge: Gauge, inp: Spinor, kappa: float = 0.0, op: int = WILSON_OP_HOP,

@@ -18,3 +18,24 @@ def test_parity_record_values():
     assert abs(rec["max_component_error_over_rms"] - 0.5) < 1e-12
     assert abs(rec["rel_l2"] - 0.5 * rms / np.linalg.norm(want)) < 1e-12
     assert rec["tolerance_rel_l2"] == 5e-3
+
+
+def test_oracle_solution_check_record(oracle_mod):
+    """The CPU leg's check of solver results: an oracle CG solution on a 4^4
+    lattice has a true residual below its tolerance, and a planted error in
+    the solution is reported."""
+    from paper_0710_2442_gb300 import inputs
+    dims = (4, 4, 4, 4)
+    U = inputs.gauge_field(dims, "weak", eps=0.3, seed=11)
+    b = inputs.gaussian_spinor(dims, seed=12)
+    x, _ = oracle_mod.cg_solve(U, b, dims, 0.12, tol=1e-10)
+    good, bad = {}, {}
+    bench.SOLUTIONS.append((good, "oracle", [(U, b, x, dims, 0.12)], x))
+    xb = x.copy()
+    xb[5, 1, 2] += 1e-3 * np.linalg.norm(x)
+    bench.SOLUTIONS.append((bad, "oracle", [(lambda: U, lambda: b, xb, dims, 0.12)]))
+    bench.oracle_solution_checks()
+    assert not bench.SOLUTIONS
+    assert good["oracle"]["true_rel_resid_max"] <= 1e-10
+    assert good["oracle"]["rel_diff_vs_fp64_gpu_solution"] == 0.0
+    assert bad["oracle"]["true_rel_resid_max"] > 1e-4

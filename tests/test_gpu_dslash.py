@@ -70,6 +70,39 @@ def test_f64_eo_hop(w, oracle_mod, dims, out_parity):
     assert_parity(host(out), want, TOL["f64"])
 
 
+def test_stateless_calls_do_not_synchronise(w, oracle_mod):
+    """wilson_dslash_eo and wilson_dslash return before their stream has run
+    them: two calls are queued behind a GPU busy-wait of about half a second,
+    the stream is still busy when both have returned, and once it has run
+    them both results match the oracle.  A first pair of calls outside the
+    check tunes the launch configurations (that pass synchronises)."""
+    import torch
+    dims = (8, 6, 4, 10)
+    U = inputs.gauge_field(dims, "random", seed=131)
+    Vh = inputs.volume(dims) // 2
+    src_h = inputs.gaussian_spinor(Vh, seed=132)
+    src_f = inputs.gaussian_spinor(inputs.volume(dims), seed=133)
+    L = w.lattice(dims, CPLX_PHASES)
+    Ud, sh, sf = dev(U), dev(src_h), dev(src_f)
+    out_h, out_f = empty_like_dev(src_h), empty_like_dev(src_f)
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        for _ in range(2):
+            w.wilson_dslash_eo(out_h, Ud, sh, L, 1, 0.135, w.WILSON_OP_SCHUR, stream)
+            w.wilson_dslash(out_f, Ud, sf, L, 0.135, w.WILSON_OP_M, stream)
+        stream.synchronize()
+        out_h.fill_(float("nan"))
+        out_f.fill_(float("nan"))
+        torch.cuda._sleep(1_000_000_000)  # about 0.5 s of GPU time at 2 GHz
+        w.wilson_dslash_eo(out_h, Ud, sh, L, 1, 0.135, w.WILSON_OP_SCHUR, stream)
+        w.wilson_dslash(out_f, Ud, sf, L, 0.135, w.WILSON_OP_M, stream)
+        still_busy = not stream.query()
+        stream.synchronize()
+    assert still_busy, "a stateless call waited for its stream"
+    assert_parity(host(out_h), oracle_mod.schur(U, src_h, dims, 0.135, 1, False, CPLX_PHASES), TOL["f64"])
+    assert_parity(host(out_f), oracle_mod.wilson_m(U, src_f, dims, 0.135, CPLX_PHASES), TOL["f64"])
+
+
 @pytest.mark.parametrize("dims", [(4, 4, 4, 4), (6, 4, 6, 10), (2, 2, 2, 4)])
 @pytest.mark.parametrize("parity", [0, 1])
 @pytest.mark.parametrize("dag", [False, True])
