@@ -30,6 +30,8 @@
 //   hop_kernel_p   3..5  the same stencil on paired FP32 instructions
 //   hop_kernel_pm  6..9  several right-hand sides per thread (register-blocked)
 //   hop_kernel_rl  10    links staged in shared memory, loop over right-hand sides
+//   hop_kernel_mma 11    link x half-spinor products on the tensor cores, one
+//                        warp per site and 16 right-hand sides (dslash_mma.cu)
 // Multi-RHS launches of the first two run the right-hand sides of a site
 // tile as consecutive blocks.  Every kernel starts with the programmatic-
 // dependent-launch wait, so it can be launched with that attribute.
@@ -748,9 +750,11 @@ __global__ void __launch_bounds__(256, MINB) hop_kernel_rl(const HopParams P) {
 // register-blocked multi-RHS kernel with NB = 2, 2, 3, 4 right-hand sides per
 // thread and 255, 128, 255, 255 registers (single and reduced precision,
 // 12-real links, NB dividing nrhs; NB >= 3 spills at 128 registers).
-constexpr int kHopVariants = 11;
+// v = 10: the link-staged kernel; v = 11: the tensor-core kernel (F16/BF16).
+constexpr int kHopVariants = 12;
 constexpr int kHopBaseVariants = 6;
 constexpr int kHopStagedVariant = 10;  // hop_kernel_rl (128 registers)
+constexpr int kHopMmaVariant = 11;     // hop_kernel_mma (128 registers)
 constexpr int hop_variant_nb(int v) {
     return v < kHopBaseVariants || v >= kHopStagedVariant ? 1 : v == 6 || v == 7 ? 2 : v == 8 ? 3 : 4;
 }
@@ -766,6 +770,7 @@ constexpr int hop_variant_minb(int v, int sp) {
 inline bool hop_variant_valid(int v, Prec sp, int recon, int nrhs) {
     if (v < 0 || v >= kHopVariants) return false;
     if (v < kHopBaseVariants) return true;
+    if (v == kHopMmaVariant) return (sp == P_F16 || sp == P_BF16) && recon == 12 && nrhs > 1;
     if (v >= kHopStagedVariant) return float_storage(sp) && recon == 12 && nrhs > 1;
     const int nb = hop_variant_nb(v);
     return float_storage(sp) && recon == 12 && nrhs >= nb && nrhs % nb == 0;
@@ -775,6 +780,9 @@ inline bool hop_variant_valid(int v, Prec sp, int recon, int nrhs) {
 template <int SP, int GP, int R>
 void launch_hop_mrhs(const HopParams& P, int block, int site_blocks, int ny, bool dag, int variant,
                      cudaStream_t st);
+// The tensor-core kernel (dslash_mma.cu; F16 and BF16 storage, 12-real links).
+template <int SP>
+void launch_hop_mma(const HopParams& P, int block, int site_blocks, int ny, bool dag, cudaStream_t st);
 
 template <int SP, int GP, int R, int V>
 void launch_hop_rl_v(const HopParams& P, int block, int site_blocks, int ny, bool dag, cudaStream_t st) {

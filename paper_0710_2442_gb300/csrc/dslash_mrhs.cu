@@ -14,6 +14,12 @@ void launch_hop_mrhs(const HopParams& P, int block, int site_blocks, int ny, boo
         case 8: launch_hop_mrhs_v<SP, GP, R, 8>(P, block, site_blocks, ny, dag, st); break;
         case 9: launch_hop_mrhs_v<SP, GP, R, 9>(P, block, site_blocks, ny, dag, st); break;
         case 10: launch_hop_rl_v<SP, GP, R, 10>(P, block, site_blocks, ny, dag, st); break;
+        case kHopMmaVariant:
+            if constexpr ((SP == P_F16 || SP == P_BF16) && GP == SP && R == 12) {
+                launch_hop_mma<SP>(P, block, site_blocks, ny, dag, st);
+                break;
+            }
+            throw Error(7, "the tensor-core hop variant needs F16/BF16 spinors and 12-real links");
         default: throw Error(7, "unknown register-blocked hop variant");
     }
 }

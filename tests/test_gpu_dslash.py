@@ -269,7 +269,40 @@ def test_blocked_multi_rhs_variants(w, oracle_mod, monkeypatch, variant, prec):
         assert_parity(got[k], oracle_mod.wilson_m(U, psi[k], dims, 0.1350, CPLX_PHASES), TOL[prec])
 
 
-@pytest.mark.parametrize("variant", [6, 8, 9, 10])
+# The tensor-core multi-RHS kernel (variant 11: one warp per site, up to 16
+# right-hand sides as the rows of mma.sync m16n8k16), pinned through
+# WILSON_HOP_VARIANT: 2, 12 and 17 right-hand sides (17 = a full group of 16
+# plus a group of one), right-hand sides of very different magnitudes, a
+# ragged last warp tile (Vh = 720 = 22.5 tiles of 32 sites), complex boundary
+# phases, and the three launch forms (even-odd hop, the Schur operator's
+# xpay hop with the dagger projectors, the full-lattice M).
+@pytest.mark.parametrize("nrhs", [2, 12, 17])
+@pytest.mark.parametrize("prec", ["f16", "bf16"])
+@pytest.mark.parametrize("block", [64, 256])
+def test_tensor_core_multi_rhs_variant(w, oracle_mod, monkeypatch, nrhs, prec, block):
+    monkeypatch.setenv("WILSON_HOP_VARIANT", "11")
+    monkeypatch.setenv("WILSON_HOP_BLOCK", str(block))
+    dims = (6, 4, 6, 10)
+    U = inputs.gauge_field(dims, "weak", eps=0.3, seed=128)
+    src = inputs.gaussian_spinor(inputs.volume(dims) // 2, seed=129, nrhs=nrhs)
+    src[nrhs - 1] *= 1e-3
+    src[0] *= 40.0
+    got = handle_hop(w, U, src, dims, CPLX_PHASES, w.PREC[prec], 12, 1, 0, w.WILSON_OP_HOP, nrhs=nrhs)
+    for k in range(nrhs):
+        assert_parity(got[k], oracle_mod.dslash_eo(U, src[k], dims, 0, CPLX_PHASES), TOL[prec], f"rhs {k}")
+    got = handle_hop(w, U, src, dims, CPLX_PHASES, w.PREC[prec], 12, 1, 1, w.WILSON_OP_SCHUR_DAG, 0.1350,
+                     nrhs=nrhs)
+    for k in range(nrhs):
+        assert_parity(got[k], oracle_mod.schur(U, src[k], dims, 0.1350, 1, True, CPLX_PHASES), TOL[prec],
+                      f"rhs {k}")
+    psi = inputs.gaussian_spinor(dims, seed=130, nrhs=nrhs)
+    got = handle_hop(w, U, psi, dims, CPLX_PHASES, w.PREC[prec], 12, w.WILSON_FULL, w.WILSON_FULL,
+                     w.WILSON_OP_M, 0.1350, nrhs=nrhs)
+    for k in range(nrhs):
+        assert_parity(got[k], oracle_mod.wilson_m(U, psi[k], dims, 0.1350, CPLX_PHASES), TOL[prec], f"rhs {k}")
+
+
+@pytest.mark.parametrize("variant", [6, 8, 9, 10, 11])
 def test_blocked_variant_lockstep_solve(w, oracle_mod, monkeypatch, variant):
     """The lockstep multi-RHS solve on a blocked kernel: right-hand sides that
     finish early (a zero source at once) are skipped inside their group while
