@@ -102,28 +102,33 @@ void launch_hop(const HopLaunch& L, cudaStream_t st) {
         std::vector<LaunchConfig> cands;
         for (const LaunchConfig& c : hop_candidates())  // FP64 has three register budgets, not six
             if (!wide_regs(sp) || c.variant < 3) cands.push_back(c);
+        // two sites per thread, and the F16 packed projection
+        for (int block : {64, 128, 256})
+            for (int v = kHopSptVariant; v < kHopVariants; v++)
+                if (hop_variant_valid(v, sp, R, P.nrhs)) cands.push_back(LaunchConfig{block, v});
         if (P.nrhs > 1)
             for (int block : {64, 128, 256})
-                for (int v = kHopBaseVariants; v < kHopVariants; v++)
+                for (int v = kHopBaseVariants; v < kHopSptVariant; v++)
                     if (hop_variant_valid(v, sp, R, P.nrhs)) cands.push_back(LaunchConfig{block, v});
         if (L.no_tune)
             cfg = tune_lookup(key, cands, LaunchConfig{});
         else
             cfg = tune_launch(key, cands, LaunchConfig{}, st, [&](const LaunchConfig& c) {
-                dispatch(Pt, sp, gp, R, c.block, hop_grid_blocks(Pt.g, c.block, 0), ny, dag, c.variant, st);
+                dispatch(Pt, sp, gp, R, c.block, hop_grid_blocks(Pt.g, c.block * hop_variant_spt(c.variant), 0), ny,
+                         dag, c.variant, st);
             });
     }
     WL_REQUIRE(hop_variant_valid(cfg.variant, sp, R, P.nrhs), "hop variant does not fit this launch");
-    // the link-staged kernel has no fused reduction: reducing launches take
-    // the paired kernel with the same block
-    if (L.red && cfg.variant >= kHopStagedVariant) cfg.variant = 3;
+    // the link-staged and tensor-core kernels have no fused reduction:
+    // reducing launches take the paired kernel with the same block
+    if (L.red && (cfg.variant == kHopStagedVariant || cfg.variant == kHopMmaVariant)) cfg.variant = 3;
     if (L.tune_only) return;
     if (L.red) {
         P.reduce = 1;
         P.red = *L.red;
         WL_REQUIRE(!L.full, "reducing hop launches are single-parity");
     }
-    const int site_blocks = hop_grid_blocks(P.g, cfg.block, L.red ? L.grid_cap : 0);
+    const int site_blocks = hop_grid_blocks(P.g, cfg.block * hop_variant_spt(cfg.variant), L.red ? L.grid_cap : 0);
     WL_REQUIRE(!L.red || site_blocks <= L.red->slot_cap, "reduction capacity below the grid size");
     dispatch(P, sp, gp, R, cfg.block, site_blocks, ny, dag, cfg.variant, st);
     WL_LAUNCH_CHECK();

@@ -32,6 +32,8 @@
 //   hop_kernel_rl  10    links staged in shared memory, loop over right-hand sides
 //   hop_kernel_mma 11    link x half-spinor products on the tensor cores, one
 //                        warp per site and 16 right-hand sides (dslash_mma.cu)
+//   hop_kernel_ps  12-17 the paired stencil with 2 or 4 sites per thread, and
+//                        for F16 the projection on packed halves (dslash_spt.cu)
 // Multi-RHS launches of the first two run the right-hand sides of a site
 // tile as consecutive blocks.  Every kernel starts with the programmatic-
 // dependent-launch wait, so it can be launched with that attribute.
@@ -751,25 +753,36 @@ __global__ void __launch_bounds__(256, MINB) hop_kernel_rl(const HopParams P) {
 // thread and 255, 128, 255, 255 registers (single and reduced precision,
 // 12-real links, NB dividing nrhs; NB >= 3 spills at 128 registers).
 // v = 10: the link-staged kernel; v = 11: the tensor-core kernel (F16/BF16).
-constexpr int kHopVariants = 12;
+// v = 12..17: the paired kernel with SPT sites per thread (12: SPT 2 at 128
+// registers, 13: SPT 2 at 255, 14: SPT 4 at 255; at 85 registers two sites
+// spill about 1 KB) and, F16 only, the packed-half projection with one site
+// per thread (15, 16, 17: 128, 85, 64 registers).
+constexpr int kHopVariants = 18;
 constexpr int kHopBaseVariants = 6;
 constexpr int kHopStagedVariant = 10;  // hop_kernel_rl (128 registers)
 constexpr int kHopMmaVariant = 11;     // hop_kernel_mma (128 registers)
+constexpr int kHopSptVariant = 12;     // first hop_kernel_ps variant
 constexpr int hop_variant_nb(int v) {
     return v < kHopBaseVariants || v >= kHopStagedVariant ? 1 : v == 6 || v == 7 ? 2 : v == 8 ? 3 : 4;
 }
+constexpr int hop_variant_spt(int v) { return v == 12 || v == 13 ? 2 : v == 14 ? 4 : 1; }
+constexpr bool hop_variant_hproj(int v) { return v >= 15 && v <= 17; }
 // FP64 operands take two registers per real: their budgets start at 255
 // registers.
 constexpr bool wide_regs(int sp) { return sp == P_F64; }
 constexpr bool float_storage(int sp) { return sp == P_F32 || sp == P_F16 || sp == P_BF16; }
 constexpr int hop_variant_minb(int v, int sp) {
     return v < kHopBaseVariants ? (wide_regs(sp) ? 1 : 2) + v % 3
+           : v == 13 || v == 14 ? 1
+           : v == 16 ? 3
+           : v == 17 ? 4
            : v >= kHopStagedVariant ? 2
            : v == 7 ? 2 : 1;
 }
 inline bool hop_variant_valid(int v, Prec sp, int recon, int nrhs) {
     if (v < 0 || v >= kHopVariants) return false;
     if (v < kHopBaseVariants) return true;
+    if (v >= kHopSptVariant && v < kHopVariants) return hop_variant_hproj(v) ? sp == P_F16 : float_storage(sp);
     if (v == kHopMmaVariant) return (sp == P_F16 || sp == P_BF16) && recon == 12 && nrhs > 1;
     if (v >= kHopStagedVariant) return float_storage(sp) && recon == 12 && nrhs > 1;
     const int nb = hop_variant_nb(v);
@@ -783,6 +796,9 @@ void launch_hop_mrhs(const HopParams& P, int block, int site_blocks, int ny, boo
 // The tensor-core kernel (dslash_mma.cu; F16 and BF16 storage, 12-real links).
 template <int SP>
 void launch_hop_mma(const HopParams& P, int block, int site_blocks, int ny, bool dag, cudaStream_t st);
+// Sites per thread and the F16 packed projection (dslash_spt.cu; F32/F16/BF16).
+template <int SP, int GP, int R>
+void launch_hop_ps(const HopParams& P, int block, int site_blocks, int ny, bool dag, int variant, cudaStream_t st);
 
 template <int SP, int GP, int R, int V>
 void launch_hop_rl_v(const HopParams& P, int block, int site_blocks, int ny, bool dag, cudaStream_t st) {
@@ -829,6 +845,13 @@ void launch_hop_v(const HopParams& P, dim3 grid, int block, bool dag, cudaStream
 template <int SP, int GP, int R>
 void launch_hop_prec(const HopParams& P, int block, int site_blocks, int ny, bool dag, int variant,
                      cudaStream_t st) {
+    if (variant >= kHopSptVariant) {
+        if constexpr (float_storage(SP)) {
+            launch_hop_ps<SP, GP, R>(P, block, site_blocks, ny, dag, variant, st);
+            return;
+        }
+        throw Error(7, "the sites-per-thread hop variants need F32/F16/BF16 spinors");
+    }
     if (variant >= kHopBaseVariants) {
         if constexpr (float_storage(SP) && R == 12) {
             launch_hop_mrhs<SP, GP, R>(P, block, site_blocks, ny, dag, variant, st);
@@ -857,6 +880,12 @@ extern template void launch_hop_prec<P_F16, P_F16, 12>(const HopParams&, int, in
 extern template void launch_hop_prec<P_BF16, P_BF16, 12>(const HopParams&, int, int, int, bool, int, cudaStream_t);
 extern template void launch_hop_prec<P_F16, P_F16, 18>(const HopParams&, int, int, int, bool, int, cudaStream_t);
 extern template void launch_hop_prec<P_BF16, P_BF16, 18>(const HopParams&, int, int, int, bool, int, cudaStream_t);
+extern template void launch_hop_ps<P_F32, P_F32, 12>(const HopParams&, int, int, int, bool, int, cudaStream_t);
+extern template void launch_hop_ps<P_F32, P_F32, 18>(const HopParams&, int, int, int, bool, int, cudaStream_t);
+extern template void launch_hop_ps<P_F16, P_F16, 12>(const HopParams&, int, int, int, bool, int, cudaStream_t);
+extern template void launch_hop_ps<P_F16, P_F16, 18>(const HopParams&, int, int, int, bool, int, cudaStream_t);
+extern template void launch_hop_ps<P_BF16, P_BF16, 12>(const HopParams&, int, int, int, bool, int, cudaStream_t);
+extern template void launch_hop_ps<P_BF16, P_BF16, 18>(const HopParams&, int, int, int, bool, int, cudaStream_t);
 extern template void launch_hop_mrhs<P_F32, P_F32, 12>(const HopParams&, int, int, int, bool, int, cudaStream_t);
 extern template void launch_hop_mrhs<P_F16, P_F16, 12>(const HopParams&, int, int, int, bool, int, cudaStream_t);
 extern template void launch_hop_mrhs<P_BF16, P_BF16, 12>(const HopParams&, int, int, int, bool, int, cudaStream_t);

@@ -159,17 +159,26 @@ def test_handle_multi_rhs_fields(w, oracle_mod):
         assert_parity(got[k], want, TOL["f32"])
 
 
-def test_f32_eo_workload_32x32x32x64(w, oracle_mod):
-    """The FP32 even-odd workload at full size (Vh = 1,048,576), whole output
-    compared with the oracle, in the launch configuration the bench times."""
+@pytest.fixture(scope="module")
+def workload_32x32x32x64(oracle_mod):
+    """The 32^3 x 64 even-odd workload's fields and the oracle's output."""
     cfg = inputs.WORKLOADS["dslash_eo_f32_32^3x64"]
     dims = cfg["dims"]
     U = inputs.gauge_field(dims, cfg["gauge"], eps=cfg["eps"], seed=cfg["gauge_seed"])
     src = inputs.gaussian_spinor(inputs.volume(dims) // 2, seed=cfg["spinor_seed"]).astype(np.complex64)
     src = src.astype(np.complex128)  # the workload's spinor is complex64 data
-    got = handle_hop(w, U, src, dims, inputs.DEFAULT_PHASES, w.WILSON_F32, 12, 0, 1, w.WILSON_OP_HOP)
-    want = oracle_mod.dslash_eo(U, src, dims, 1)
-    assert_parity(got, want, TOL["f32"])
+    return dims, U, src, oracle_mod.dslash_eo(U, src, dims, 1)
+
+
+@pytest.mark.parametrize("prec", ["f32", "f16", "bf16"])
+def test_eo_workload_32x32x32x64(w, workload_32x32x32x64, prec):
+    """The even-odd workload at full size (Vh = 1,048,576), whole output
+    compared with the oracle element by element, in the launch configuration
+    the autotuner picks (the one the bench times), for the F32 headline
+    storage and for the F16 / BF16 storage of the inner solver."""
+    dims, U, src, want = workload_32x32x32x64
+    got = handle_hop(w, U, src, dims, inputs.DEFAULT_PHASES, w.PREC[prec], 12, 0, 1, w.WILSON_OP_HOP)
+    assert_parity(got, want, TOL[prec])
 
 
 def test_nan_sentinels_overwritten(w):
@@ -206,9 +215,12 @@ def test_handle_schur(w, oracle_mod, prec, recon, dag):
 
 
 # Every kernel variant (register budgets 0-2 of the scalar stencil, 3-5 of the
-# paired-FP32 stencil) against the oracle, pinned through WILSON_HOP_VARIANT so
-# that the autotuner's choice does not decide which code is tested.
-@pytest.mark.parametrize("variant", range(6))
+# paired-FP32 stencil, 12-14 two or four sites per thread, 15-17 the F16
+# projection on packed halves; a variant that does not fit a precision runs
+# variant 3)
+# against the oracle, pinned through WILSON_HOP_VARIANT so that the
+# autotuner's choice does not decide which code is tested.
+@pytest.mark.parametrize("variant", [0, 1, 2, 3, 4, 5, 12, 13, 14, 15, 16, 17])
 @pytest.mark.parametrize("prec,recon", [("f32", 12), ("f16", 12), ("bf16", 12), ("f32", 18), ("f16", 18)])
 def test_every_variant_eo_and_schur(w, oracle_mod, monkeypatch, variant, prec, recon):
     monkeypatch.setenv("WILSON_HOP_VARIANT", str(variant))
@@ -229,7 +241,7 @@ def test_every_variant_eo_and_schur(w, oracle_mod, monkeypatch, variant, prec, r
     assert_parity(got, oracle_mod.wilson_m(U, psi, dims, 0.1350, CPLX_PHASES), TOL[prec])
 
 
-@pytest.mark.parametrize("variant", [0, 3])
+@pytest.mark.parametrize("variant", [0, 3, 12, 14, 16])
 def test_variant_solver(w, oracle_mod, monkeypatch, variant):
     """The mixed-precision solve on each stencil family."""
     monkeypatch.setenv("WILSON_HOP_VARIANT", str(variant))
