@@ -286,6 +286,47 @@ int wilson_dslash_h(wilson_spinor* out, const wilson_gauge* g, const wilson_spin
                     int op, void* stream);
 
 /* ---------------------------------------------------------------------- */
+/* Domain decomposition along t (Sec. 5: the lattice split over SPEs and   */
+/* Cell nodes, whose external communication T_ext ships projected half     */
+/* spinors, 12 reals per boundary site and face; Table 1).  A sub-lattice  */
+/* of Lr consecutive t-slices (Lr even, so local parity = global parity)   */
+/* is an ordinary handle lattice {Lx, Ly, Lz, Lr} with the lattice's       */
+/* boundary phases; its half fields are the contiguous global half-site    */
+/* range [t0 Vs/2, (t0 + Lr) Vs/2), Vs = Lx Ly Lz.  One application of      */
+/* D_{p,1-p} on every sub-lattice is: wilson_dd_pack on each, move each     */
+/* send_prev buffer to the previous sub-lattice's recv_next and each        */
+/* send_next buffer to the next one's recv_prev (cyclically; a device copy  */
+/* on one GPU, NCCL send/recv or a peer copy between GPUs), then            */
+/* wilson_dd_hop on each.  F64 or F32 fields, one right-hand side.          */
+/* ---------------------------------------------------------------------- */
+
+/* Bytes of one face buffer of a sub-lattice (96 B per face site for F64,
+ * 48 B for F32, over Vs/2 face sites rounded up to 64); -1 on invalid
+ * arguments (wilson_last_error() says why). */
+long long wilson_dd_halo_bytes(const wilson_lattice* L, int prec);
+
+/* Fills the two face buffers (device memory, wilson_dd_halo_bytes each)
+ * from the input field in (parity 1-p) of this sub-lattice:
+ *   send_prev: (1 - g_4) psi on the first t-slice (the previous sub-lattice's
+ *              forward t-hop), or (1 + g_4) psi with dagger = 1;
+ *   send_next: U^dag_{y,4} (1 + g_4) psi(y) on the last t-slice (the next
+ *              sub-lattice's backward t-hop; the link lives here), or with
+ *              (1 - g_4) for dagger = 1.
+ * dagger = 1 applies the hop of g_5 D g_5.  Asynchronous on the stream. */
+int wilson_dd_pack(void* send_prev, void* send_next, const wilson_gauge* g, const wilson_spinor* in,
+                   int dagger, void* stream);
+
+/* out (parity p) = D_{p,1-p} in on this sub-lattice, the t-hops across its
+ * two faces taken from recv_next (the next sub-lattice's send_prev) and
+ * recv_prev (the previous one's send_next).  t_first / t_last: the sub-
+ * lattice holds the lattice's first / last t-slice, so that the boundary
+ * phase of t (g's lattice) applies on that face.  A single sub-lattice
+ * (t_first = t_last = 1, its own buffers) is the undecomposed operator.
+ * Asynchronous on the stream. */
+int wilson_dd_hop(wilson_spinor* out, const wilson_gauge* g, const wilson_spinor* in, const void* recv_next,
+                  const void* recv_prev, int dagger, int t_first, int t_last, void* stream);
+
+/* ---------------------------------------------------------------------- */
 /* No-allocation variant (the paper has no counterpart; this is a service  */
 /* of the library).  For callers that cannot let a library allocate device */
 /* memory: hosts whose memory manager owns the whole device (a framework's */

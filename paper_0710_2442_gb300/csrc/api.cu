@@ -233,16 +233,6 @@ bool wl::is_device_ptr(const void* p) {
     return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
-struct wilson_gauge_s {
-    GaugeField f;
-    mutable std::mutex m;
-    mutable SpinorField tmp;  // intermediate field of the Schur operator
-};
-struct wilson_spinor_s {
-    SpinorField f;
-    Geom g;
-};
-
 // ---------------------------------------------------------------------------
 extern "C" {
 

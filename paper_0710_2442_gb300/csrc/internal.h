@@ -3,6 +3,7 @@
 #pragma once
 
 #include <functional>
+#include <mutex>
 #include <stdexcept>
 #include <string>
 #include <vector>
@@ -251,3 +252,14 @@ struct BorrowGuard {
 };
 
 }  // namespace wl
+
+// The opaque handles of the C ABI (wilson.h).
+struct wilson_gauge_s {
+    wl::GaugeField f;
+    mutable std::mutex m;
+    mutable wl::SpinorField tmp;  // intermediate field of the Schur operator
+};
+struct wilson_spinor_s {
+    wl::SpinorField f;
+    wl::Geom g;
+};

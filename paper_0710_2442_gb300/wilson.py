@@ -86,6 +86,9 @@ def _declare(lib):
         "wilson_spinor_export": (I, [VP, VP, VP]),
         "wilson_dslash_h": (I, [VP, VP, VP, D, I, VP]),
         "wilson_probe_fma_peak": (I, [I, P(D), VP]),
+        "wilson_dd_halo_bytes": (ctypes.c_longlong, [P(wilson_lattice), I]),
+        "wilson_dd_pack": (I, [VP, VP, VP, VP, I, VP]),
+        "wilson_dd_hop": (I, [VP, VP, VP, VP, VP, I, I, I, VP]),
         "wilson_last_error": (ctypes.c_char_p, []),
         "wilson_version": (I, []),
     }
@@ -275,6 +278,23 @@ class Spinor:
             self.close()
         except Exception:
             pass
+
+
+def wilson_dd_halo_bytes(L: wilson_lattice, prec: int) -> int:
+    n = lib().wilson_dd_halo_bytes(ctypes.byref(L), int(prec))
+    if n < 0:
+        raise WilsonError(WILSON_ERR_ARG, lib().wilson_last_error().decode(errors="replace"))
+    return int(n)
+
+
+def wilson_dd_pack(send_prev, send_next, gauge: "Gauge", inp: "Spinor", dagger: int = 0, stream=None):
+    _check(lib().wilson_dd_pack(_ptr(send_prev), _ptr(send_next), gauge.h, inp.h, int(dagger), _stream(stream)))
+
+
+def wilson_dd_hop(out: "Spinor", gauge: "Gauge", inp: "Spinor", recv_next, recv_prev, dagger: int = 0,
+                  t_first: int = 1, t_last: int = 1, stream=None):
+    _check(lib().wilson_dd_hop(out.h, gauge.h, inp.h, _ptr(recv_next), _ptr(recv_prev), int(dagger),
+                               int(t_first), int(t_last), _stream(stream)))
 
 
 def wilson_probe_fma_peak(kind: int, stream=None) -> float:
