@@ -39,6 +39,7 @@ from paper_0710_2442_gb300 import inputs, model  # noqa: E402
 METRIC = "Dslash GFlop/s & HBM GB/s (% roofline); CG time-to-1e-10 mixed vs FP64"
 FIRST_APPLICATION = [None]  # the library's first hop application of the timed workload (host copy)
 ORACLE_OUTPUT = [None]      # the oracle's output for the same input (CPU leg)
+DD_OUTPUT = [None]          # the t-decomposed hop's first application (host copy), same input
 # GPU solutions kept (host copies) for the oracle's residual check in the CPU leg:
 # a list of (record, key, [(gauge, b, x, dims, kappa), ...][, FP64 GPU solution to compare x with]);
 # gauge and b may be callables that regenerate the field from its seed
@@ -61,8 +62,8 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-solver", action="store_true",
                     help="skip the solver, multi-RHS and batch blocks (CG time-to-solution comparisons)")
-    ap.add_argument("--blocks", default="cg,multirhs,batch",
-                    help="solver blocks to run after the headline (comma list of cg, multirhs, batch)")
+    ap.add_argument("--blocks", default="cg,multirhs,batch,dd",
+                    help="blocks to run after the headline (comma list of cg, multirhs, batch, dd)")
     ap.add_argument("--cg-prec", default="f64,f16,bf16,f32",
                     help="inner precisions of the cg block's solves (comma list; f64 = plain FP64 CG)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
@@ -307,6 +308,8 @@ def run_ours(args, ws, rank, local, fields):
             line["cg"] = run_solver_block(w, torch, dev, stream, args.cg_prec.split(","), peak)
         if "multirhs" in blocks:
             line["multirhs"] = run_multirhs_block(w, torch, dev, stream, fields)
+        if "dd" in blocks:
+            line["dd"] = run_dd_block(w, torch, dev, stream, fields, line["roofline"]["launch_us"])
         if "batch" in blocks:
             line["batch"] = run_batch_block(w, torch, dev, stream)
     return line
@@ -450,6 +453,75 @@ def run_multirhs_block(w, torch, dev, stream, fields, nrhs=12):
     SOLUTIONS.append((out["cg"], "oracle", [(U, b_host[k], x_lock[k], dims, kappa) for k in range(nrhs)]))
     del Ud, bsrc, x
     torch.cuda.empty_cache()
+    return out
+
+
+def run_dd_block(w, torch, dev, stream, fields, single_us, n=2):
+    """The headline hop on the lattice split along t into n sub-lattices on
+    this GPU: wilson_dd_pack on each, the loopback exchange of the face
+    buffers (device copies), wilson_dd_hop on each; timed per application
+    against the single-lattice hop, with the face bytes each application
+    moves (12 reals per face site, the paper's T_ext data)."""
+    from paper_0710_2442_gb300.dd import TSplit, exchange_loopback
+    cfg, dims, U, src = fields
+    sp = TSplit(dims, n)
+    L = w.lattice(sp.local_dims)
+    P = w.WILSON_F32
+    hb = w.wilson_dd_halo_bytes(L, P)
+    gauges = [w.Gauge(u, L, P, 12, stream) for u in sp.split_gauge(U)]
+    ins = [w.Spinor(L, w.WILSON_EVEN, P) for _ in range(n)]
+    outs = [w.Spinor(L, w.WILSON_ODD, P) for _ in range(n)]
+    for s_, part in zip(ins, sp.split_half(src)):
+        s_.load(torch.from_numpy(np.ascontiguousarray(part)).to(dev), stream)
+    buf = lambda: [torch.empty(hb, dtype=torch.uint8, device=dev) for _ in range(n)]
+    send_prev, send_next, recv_next, recv_prev = buf(), buf(), buf(), buf()
+
+    def pack():
+        for r in range(n):
+            w.wilson_dd_pack(send_prev[r], send_next[r], gauges[r], ins[r], 0, stream)
+
+    def hop():
+        for r in range(n):
+            w.wilson_dd_hop(outs[r], gauges[r], ins[r], recv_next[r], recv_prev[r], 0, sp.first(r), sp.last(r),
+                            stream)
+
+    def apply():
+        pack()
+        exchange_loopback(sp, send_prev, send_next, recv_next, recv_prev)
+        hop()
+
+    apply()
+    parts = []
+    for o in outs:
+        t = torch.empty((sp.Lr * sp.Vs // 2, 4, 3), dtype=torch.complex128, device=dev)
+        o.store(t, stream)
+        parts.append(t.cpu().numpy())
+    DD_OUTPUT[0] = sp.gather_half(parts)
+    reps = 20
+    res = {}
+    for name, fn in (("pack_exchange_hop", apply), ("hop_only", hop), ("pack_only", pack)):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        res[name] = e0.elapsed_time(e1) / reps * 1e3
+    Vh = inputs.volume(dims) // 2
+    peak, _ = measured_peaks()
+    byts = model.compulsory_bytes_per_site("f32", 12, eo=True) * Vh
+    out = {"workload": "dslash_eo_f32_32^3x64 split along t", "subdomains": n, "local_dims": list(sp.local_dims),
+           "exchange": "loopback device copies on one GPU",
+           "face_bytes_per_application": 2 * n * 48 * sp.Vs // 2,
+           "us_per_application": round(res["pack_exchange_hop"], 2),
+           "us_hops_only": round(res["hop_only"], 2), "us_pack_only": round(res["pack_only"], 2),
+           "single_lattice_us": single_us,
+           "hop_frac_of_hbm": round(byts / (res["hop_only"] * 1e-6) / 1e9 / peak, 4)}
+    for h in gauges + ins + outs:
+        h.close()
     return out
 
 
@@ -686,6 +758,8 @@ def main():
                                 "value_1core": round(v1, 4)}
         if FIRST_APPLICATION[0] is not None and ORACLE_OUTPUT[0] is not None:
             line["parity"] = parity_record(args.prec, FIRST_APPLICATION[0], ORACLE_OUTPUT[0])
+        if DD_OUTPUT[0] is not None and ORACLE_OUTPUT[0] is not None and "dd" in line:
+            line["dd"]["parity"] = parity_record("f32", DD_OUTPUT[0], ORACLE_OUTPUT[0])
         if not args.no_solver:
             oracle_solution_checks()
             line["cpu_baseline"]["solvers"] = oracle_solver_baselines(line)

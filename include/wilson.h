@@ -58,6 +58,8 @@
  *   WILSON_BATCH_PRIORITY=0       no graph-node priorities between the classes
  *   WILSON_BATCH_GRID_PER_SM=n    n blocks per SM for the tile-walking kernels
  *                                 (default: one block per tile)
+ *   WILSON_BATCH_TILE=n           batch tile size (128, 256 or 512 sites) instead of
+ *                                 the autotuned one
  *   WILSON_BATCH_HOST_LOOP=1      host-replayed graphs instead of device-side loops
  *   WILSON_BATCH_MAX_LOOP=n       lower the batch loop's iteration cap
  *   WILSON_BATCH_BUDGET_MS=t      lower the batch loop's wall-clock budget (60 s)
@@ -213,7 +215,8 @@ typedef struct {
     int graph_launches;     /* 1 when the loop runs on the device                          */
     int device_loop;        /* 1: conditional-node loop; 0: host-replayed graph chunks     */
     int timed_out;          /* 1: the iteration cap or wall-clock budget ended the loop    */
-    int tiles;              /* 256-site tiles over the problems the class loops solve      */
+    int tiles;              /* tiles over the problems the class loops solve (each class's
+                               tile size, 128, 256 or 512 sites, is autotuned)              */
 } wilson_batch_info;
 
 int wilson_batch_solve(int n, const wilson_problem* probs, const wilson_solver_params* p, wilson_solve_stats* st,

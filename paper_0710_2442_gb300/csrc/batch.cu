@@ -7,7 +7,8 @@
 // Problems with at most SolveParams::batch_small_vh sites per parity are each
 // solved by one thread block (small_solve_kernel).  The others are grouped
 // by lattice size into classes; each class's half lattices are cut into
-// tiles of kTile sites, a tile table maps every tile to its problem, and
+// tiles of a tuned number of sites (128, 256 or 512; the autotuner times
+// the class's inner hop with each), a tile table maps every tile to its problem, and
 // every kernel of the class walks the tile table (one block per tile by
 // default), so one launch serves all its problems whatever their sizes.
 // Per-problem reductions are tile partials summed in a fixed order by the
@@ -55,7 +56,7 @@ namespace bt {
         if (!tile_active(A, op, pid)) continue;                              \
         const BatchProb& Pr = A.probs[pid];                                  \
         const Geom& g = Pr.g;                                                \
-        const int h0 = (t - Pr.tile0) * kTile;
+        const int h0 = (t - Pr.tile0) * A.tile;
 #define WL_TILE_LOOP_END }
 
 // xin += alpha p; s -= alpha q; slow = s; |s|^2   (INNER)
@@ -65,7 +66,7 @@ __global__ void __launch_bounds__(256) bxs_kernel(const BatchArgs A, const BOp o
     WL_TILE_LOOP_BEGIN
     const float alpha = (float)__ldcg(&A.state[pid].sc.alpha);
     double nrm = 0.0;
-    for (int j = threadIdx.x; j < kTile; j += blockDim.x) {
+    for (int j = threadIdx.x; j < A.tile; j += blockDim.x) {
         const int h = h0 + j;
         if (h >= g.Vh) break;
         cpx<float> xv[12], sv[12];
@@ -101,7 +102,7 @@ __global__ void __launch_bounds__(256) bp_kernel(const BatchArgs A, const BOp op
     using TP = typename SpinorFmt<IP>::real;
     WL_TILE_LOOP_BEGIN
     const TP beta = (TP)__ldcg(&A.state[pid].sc.beta);
-    for (int j = threadIdx.x; j < kTile; j += blockDim.x) {
+    for (int j = threadIdx.x; j < A.tile; j += blockDim.x) {
         const int h = h0 + j;
         if (h >= g.Vh) break;
         cpx<TP> pv[12], rv[12];
@@ -120,7 +121,7 @@ __global__ void __launch_bounds__(256) bp_kernel(const BatchArgs A, const BOp op
 // x_e += xin (FP64 += FP32)   (OUTER)
 __global__ void __launch_bounds__(256) baxpy_kernel(const BatchArgs A, const BOp op) {
     WL_TILE_LOOP_BEGIN
-    for (int j = threadIdx.x; j < kTile; j += blockDim.x) {
+    for (int j = threadIdx.x; j < A.tile; j += blockDim.x) {
         const int h = h0 + j;
         if (h >= g.Vh) break;
         cpx<double> xv[12];
@@ -141,7 +142,7 @@ __global__ void __launch_bounds__(256) baxpy_kernel(const BatchArgs A, const BOp
 __global__ void __launch_bounds__(256) bxmy_kernel(const BatchArgs A, const BOp op) {
     WL_TILE_LOOP_BEGIN
     double nrm = 0.0;
-    for (int j = threadIdx.x; j < kTile; j += blockDim.x) {
+    for (int j = threadIdx.x; j < A.tile; j += blockDim.x) {
         const int h = h0 + j;
         if (h >= g.Vh) break;
         cpx<double> bv[12], qv[12];
@@ -163,7 +164,7 @@ template <int IP>
 __global__ void __launch_bounds__(256) bprep_kernel(const BatchArgs A, const BOp op) {
     using TP = typename SpinorFmt<IP>::real;
     WL_TILE_LOOP_BEGIN
-    for (int j = threadIdx.x; j < kTile; j += blockDim.x) {
+    for (int j = threadIdx.x; j < A.tile; j += blockDim.x) {
         const int h = h0 + j;
         if (h >= g.Vh) break;
         cpx<double> rv[12];
@@ -189,7 +190,7 @@ __global__ void __launch_bounds__(256) bnorm_kernel(const BatchArgs A, const BOp
     const char* v = Pr.f[op.f_in] + op.out_parity * Pr.fp[op.f_in];
     const char* m = op.f_x >= 0 ? Pr.f[op.f_x] + op.out_parity * Pr.fp[op.f_x] : nullptr;
     double nrm = 0.0;
-    for (int j = threadIdx.x; j < kTile; j += blockDim.x) {
+    for (int j = threadIdx.x; j < A.tile; j += blockDim.x) {
         const int h = h0 + j;
         if (h >= g.Vh) break;
         cpx<double> vv[12];
@@ -225,7 +226,7 @@ __global__ void __launch_bounds__(256) binit_kernel(const BatchArgs A, const BOp
         S.sc.maxiter = A.probs[i].maxiter;
     }
     WL_TILE_LOOP_BEGIN
-    for (int j = threadIdx.x; j < kTile; j += blockDim.x) {
+    for (int j = threadIdx.x; j < A.tile; j += blockDim.x) {
         const int h = h0 + j;
         if (h >= g.Vh) break;
         cpx<double> z64[12];
@@ -295,7 +296,7 @@ void dispatch_low(Prec p, F&& f) {
 using namespace bt;
 
 struct BatchRun {
-    int nprob = 0, ntiles = 0, sms = 1;
+    int nprob = 0, ntiles = 0, sms = 1, tile = kTile;
     Prec ip = P_F16;
     std::vector<int> members;  // global problem ids of this run's problems (local order)
     DevBuf probs, state, tile_prob, global, partials, counters, ids;
@@ -371,8 +372,9 @@ void build_problem(HostProb& P, const wilson_problem& in, Prec ip, const SolvePa
 
 // Device descriptors, states and the tile table of one run.
 std::unique_ptr<BatchRun> make_run(const std::vector<HostProb>& hp, const std::vector<int>& members, bool small,
-                                   const SolveParams& prm, cudaStream_t st) {
+                                   const SolveParams& prm, cudaStream_t st, int tile = kTile) {
     auto R = std::make_unique<BatchRun>();
+    R->tile = tile;
     R->members = members;
     R->nprob = (int)members.size();
     R->ip = prm.inner;
@@ -399,7 +401,7 @@ std::unique_ptr<BatchRun> make_run(const std::vector<HostProb>& hp, const std::v
         D.keep_x = prm.use_initial_guess;
         D.small = small ? 1 : 0;
         D.tile0 = (int)tiles.size();
-        D.ntiles = small ? 0 : (P.g.Vh + kTile - 1) / kTile;
+        D.ntiles = small ? 0 : (P.g.Vh + tile - 1) / tile;
         for (int t = 0; t < D.ntiles; t++) tiles.push_back(j);
         ids.push_back(j);
     }
@@ -424,6 +426,7 @@ std::unique_ptr<BatchRun> make_run(const std::vector<HostProb>& hp, const std::v
     R->A.tile_prob = R->tile_prob.as<int>();
     R->A.ntiles = R->ntiles;
     R->A.nprob = R->nprob;
+    R->A.tile = tile;
     // blocks per SM of the tile-walking kernels; 0 (default): one block per
     // tile, so that the block scheduler can interleave the classes' kernels
     // tile by tile in priority order
@@ -488,8 +491,41 @@ void batch_solve(int n, const wilson_problem* probs, const SolveParams& prm, wil
         if (std::atoi(e) > 0) max_classes = std::atoi(e);
     std::vector<int> small_ids, loop_ids;
     for (int i = 0; i < n; i++) (hp[i].g.Vh <= small_vh ? small_ids : loop_ids).push_back(i);
+    // Each class's tile size: WILSON_BATCH_TILE pins it; otherwise the
+    // autotuner times the class's inner hop (a non-reducing xpay hop of the
+    // inner precision) on tile tables of 128, 256 and 512 sites.
+    int tile_pin = 0;
+    if (const char* e = std::getenv("WILSON_BATCH_TILE")) tile_pin = std::atoi(e);
+    WL_REQUIRE(tile_pin == 0 || tile_pin == 128 || tile_pin == 256 || tile_pin == 512,
+               "WILSON_BATCH_TILE must be 128, 256 or 512");
     std::vector<std::unique_ptr<BatchRun>> loops;
-    for (const auto& c : size_classes(hp, loop_ids, max_classes)) loops.push_back(make_run(hp, c, false, prm, st));
+    for (const auto& c : size_classes(hp, loop_ids, max_classes)) {
+        if (tile_pin) {
+            loops.push_back(make_run(hp, c, false, prm, st, tile_pin));
+            continue;
+        }
+        // 256 first: the tuner resolves near-ties (within 1 %) to the earlier
+        // candidate, and an isolated hop does not see how the classes share
+        // the GPU inside the graph
+        std::unique_ptr<BatchRun> cand[3];
+        const int tiles[3] = {256, 128, 512};
+        long long vh = 0;
+        for (int i : c) vh += hp[i].g.Vh;
+        for (int k = 0; k < 3; k++) cand[k] = make_run(hp, c, false, prm, st, tiles[k]);
+        char key[96];
+        snprintf(key, sizeof(key), "btile:lo%d:n%d:vh%lld", (int)ip, (int)c.size(), vh);
+        // LaunchConfig.block carries the tile size here
+        const LaunchConfig pick = tune_launch(
+            key, {LaunchConfig{256, 0}, LaunchConfig{128, 0}, LaunchConfig{512, 0}}, LaunchConfig{kTile, 0}, st,
+            [&](const LaunchConfig& t) {
+                const BatchRun& Rt = *cand[t.block == 256 ? 0 : t.block == 128 ? 1 : 2];
+                const BOp o = Rt.op(BF_Q, BF_T, BF_P, 0, 0, 2, -1, 0, BF_NONE, 0);
+                dispatch_low(ip, [&](auto I) {
+                    Rt.hop_t<decltype(I)::value, decltype(I)::value>(o, 0, LaunchConfig{128, 4}, st);
+                });
+            });
+        loops.push_back(std::move(cand[pick.block == 256 ? 0 : pick.block == 128 ? 1 : 2]));
+    }
     std::unique_ptr<BatchRun> smallrun;
     if (!small_ids.empty()) smallrun = make_run(hp, small_ids, true, prm, st);
 

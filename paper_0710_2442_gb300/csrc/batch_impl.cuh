@@ -14,7 +14,7 @@
 namespace wl {
 namespace bt {
 
-constexpr int kTile = 256;  // half-lattice sites per tile
+constexpr int kTile = 256;  // default half-lattice sites per tile (the run's tile is tuned: 128, 256, 512)
 
 enum BField { BF_B, BF_X, BF_BHAT, BF_R64, BF_Q64, BF_T64, BF_XIN, BF_S, BF_SLOW, BF_P, BF_Q, BF_R, BF_T, BF_N };
 enum Phase { PH_OUTER = 0, PH_INNER = 1, PH_DONE = 2 };
@@ -59,6 +59,7 @@ struct BatchArgs {
     const int* tile_prob;
     int ntiles;
     int nprob;
+    int tile;  // half-lattice sites per tile
 };
 
 struct BOp {
@@ -213,8 +214,8 @@ __global__ void __launch_bounds__(256, MINB) bhop_kernel(const BatchArgs A, cons
         // outer is written only by the correction finisher, a later kernel
         const bool zero = op.zero_first && __ldcg(&A.state[pid].outer) == 0;
         double nrm = 0.0;
-        const int h0 = (t - Pr.tile0) * kTile;
-        for (int j = threadIdx.x; j < kTile; j += blockDim.x) {
+        const int h0 = (t - Pr.tile0) * A.tile;
+        for (int j = threadIdx.x; j < A.tile; j += blockDim.x) {
             const int h = h0 + j;
             if (h >= g.Vh) break;
             int c[4], s;
@@ -272,8 +273,8 @@ __global__ void __launch_bounds__(256, MINB) bhop_kernel_p(const BatchArgs A, co
         const float a = (float)coef_of(op.coef, Pr.kappa);
         const Geom& g = P.g;
         double nrm = 0.0;
-        const int h0 = (t - Pr.tile0) * kTile;
-        for (int j = threadIdx.x; j < kTile; j += blockDim.x) {
+        const int h0 = (t - Pr.tile0) * A.tile;
+        for (int j = threadIdx.x; j < A.tile; j += blockDim.x) {
             const int h = h0 + j;
             if (h >= g.Vh) break;
             int c[4], s;

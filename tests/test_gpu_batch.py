@@ -56,6 +56,23 @@ def test_batch_matches_oracle(w, oracle_mod, monkeypatch, inner, small_vh):
         assert 0 <= s["seconds"] <= info["device_seconds"] + 1e-6
 
 
+# WILSON_BATCH_TILE pins the tile size of every class (the autotuner's
+# candidates): 128, 256 and 512 sites, on MIX (half volumes 32 to 512 sites:
+# single, partial and many tiles per problem) through the device loop.
+@pytest.mark.parametrize("tile", ["128", "256", "512"])
+def test_batch_tile_sizes(w, oracle_mod, monkeypatch, tile):
+    monkeypatch.setenv("WILSON_BATCH_SMALL_VH", "0")
+    monkeypatch.setenv("WILSON_BATCH_TILE", tile)
+    probs, hf = make_batch(w, MIX, seed0=440)
+    rc, st, info = w.wilson_batch_solve(probs, w.solver_defaults(w.WILSON_F16))
+    assert rc == 0 and not info["timed_out"]
+    want_tiles = sum(-(-inputs.volume(dims) // 2 // int(tile)) for dims, _, _, _ in hf)
+    assert info["tiles"] == want_tiles
+    for q, (dims, U, b, kappa), s in zip(probs, hf, st):
+        assert s["status"] == 0
+        assert true_resid(oracle_mod, U, host(q["x"]), b, dims, kappa) <= 1.1e-10
+
+
 @pytest.mark.parametrize("small_vh", ["0", "4096"])
 def test_batch_initial_guess(w, oracle_mod, monkeypatch, small_vh):
     """use_initial_guess: every problem starts from a nonzero iterate (its
