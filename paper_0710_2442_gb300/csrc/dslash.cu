@@ -1,6 +1,7 @@
 // dslash.cu -- host-side dispatch of the hopping-term kernels (device code in
 // dslash_impl.cuh): picks the instantiation for the storage precisions and
 // link format, and the launch configuration from the autotuner.
+#include <algorithm>
 #include <cstdio>
 #include <cstdlib>
 #include <string>
@@ -128,7 +129,16 @@ void launch_hop(const HopLaunch& L, cudaStream_t st) {
         P.red = *L.red;
         WL_REQUIRE(!L.full, "reducing hop launches are single-parity");
     }
-    const int site_blocks = hop_grid_blocks(P.g, cfg.block * hop_variant_spt(cfg.variant), L.red ? L.grid_cap : 0);
+    // A reducing launch walks the lattice with a capped grid (one partial per
+    // block, summed by the last block in a fixed order).  It runs 256-thread
+    // blocks, one resident wave of them (the variant's guaranteed blocks per
+    // SM on every SM): no tail wave, and the finisher sums few partials.
+    int cap = 0;
+    if (L.red) {
+        cfg.block = 256;
+        cap = std::min(L.grid_cap, device_sm_count() * hop_variant_minb(cfg.variant, sp));
+    }
+    const int site_blocks = hop_grid_blocks(P.g, cfg.block * hop_variant_spt(cfg.variant), cap);
     WL_REQUIRE(!L.red || site_blocks <= L.red->slot_cap, "reduction capacity below the grid size");
     dispatch(P, sp, gp, R, cfg.block, site_blocks, ny, dag, cfg.variant, st);
     WL_LAUNCH_CHECK();
