@@ -131,7 +131,11 @@ int wilson_dslash_eo(double* out, const double* gauge, const double* in, const w
 /* stopped when the true relative residual |b - M x| / |b| <= tol,          */
 /* recomputed in FP64 on the GPU.  With inner = F32/F16/BF16 the CG runs in */
 /* that storage precision (FP32 arithmetic) inside an FP64 defect          */
-/* correction; with inner = F64 it is plain FP64 CG.                       */
+/* correction; with inner = F64 it is plain FP64 CG.  A correction whose    */
+/* expected residual (the last one times the inner reduction) is above      */
+/* 1e-4 |bhat| (and tol < 1e-7) computes it with FP32 fields and links      */
+/* (error about 1e-7 |Mhat| |x|); every other residual, and every          */
+/* convergence decision, is FP64.                                          */
 /* ---------------------------------------------------------------------- */
 typedef struct {
     int inner;              /* wilson_prec of the inner CG (F64 = plain FP64 CG)            */
@@ -161,6 +165,7 @@ typedef struct {
     double seconds;           /* wall time of the solve (device-synchronised)        */
     double inner_seconds;     /* device time of the inner CG iterations (CUDA events
                                  around their replays; 0 for block CG and batches)  */
+    int outer_f32;            /* corrections whose residual was computed in FP32     */
 } wilson_solve_stats;
 
 /* Default parameters for an inner precision (tol 1e-10). */

@@ -385,6 +385,7 @@ static void copy_stats(wilson_solve_stats* o, const SolveStats& s, int rc) {
     o->true_rel_resid = s.true_rel_resid;
     o->seconds = s.seconds;
     o->inner_seconds = s.inner_seconds;
+    o->outer_f32 = s.outer_f32;
 }
 
 int wilson_cg_solve(double* x, const double* gauge, const double* b, const wilson_lattice* L, double kappa,

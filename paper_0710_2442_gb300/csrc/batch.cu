@@ -821,6 +821,7 @@ void batch_solve(int n, const wilson_problem* probs, const SolveParams& prm, wil
             o.hop_applications = 4 * S.sc.iter + 4 * (S.outer + 1) + (prm.use_initial_guess ? 4 : 2);
             o.seconds = S.phase == PH_DONE && S.t_done >= t_first ? (double)(S.t_done - t_first) * 1e-9 : -1.0;
             o.inner_seconds = 0.0;
+            o.outer_f32 = 0;
             int status = S.status;
             if (status == 0 && S.phase != PH_DONE) status = hg[r].timed_out ? WILSON_ERR_TIMEOUT : WILSON_ERR_NOCONV;
             if (status == 0 && !(o.true_rel_resid <= prm.tol)) status = WILSON_ERR_NOCONV;

@@ -116,20 +116,23 @@ __global__ void __launch_bounds__(256) axpy_kernel(Vec y, Vec x, Geom g, int nrh
     }
 }
 
-// r = b - q, reduce |r|^2   (all FP64)
+// r = b - q, reduce |r|^2   (r, b and the sums FP64; q FP64 or FP32)
+template <int QP>
 __global__ void __launch_bounds__(256) xmy_norm_kernel(Vec rv, Vec b, Vec q, Geom g, int nrhs, RedArgs red) {
     const RhsIdx r = rhs_index(nrhs);
+    using TQ = typename SpinorFmt<QP>::real;
     char* Rr = rv.p ? at<char>(rv, r.k) : nullptr;
     const char* B = at<const char>(b, r.k);
     const char* Q = at<const char>(q, r.k);
     double nrm = 0.0;
     for (int h = r.sb * blockDim.x + threadIdx.x; h < g.Vh; h += r.nb * blockDim.x) {
-        cpx<double> bv[12], qv[12];
+        cpx<double> bv[12];
+        cpx<TQ> qv[12];
         SpinorFmt<P_F64>::load(B, g.stride, h, bv);
-        SpinorFmt<P_F64>::load(Q, g.stride, h, qv);
+        SpinorFmt<QP>::load(Q, g.stride, h, qv);
 #pragma unroll
         for (int c = 0; c < 12; c++) {
-            bv[c] = csub(bv[c], qv[c]);
+            bv[c] = csub(bv[c], cpx<double>{(double)qv[c].re, (double)qv[c].im});
             nrm += cnorm2(bv[c]);
         }
         if (Rr) SpinorFmt<P_F64>::store(Rr, g.stride, h, bv);
@@ -208,11 +211,18 @@ void axpy(Prec yp, Vec y, Prec xp, Vec x, double a, const Geom& g, int nrhs, cud
     WL_LAUNCH_CHECK();
 }
 
-void xmy_norm64(Vec r, Vec b, Vec q, const Geom& g, int nrhs, const RedArgs& red, int grid_cap, cudaStream_t st) {
+void xmy_norm(Prec qp, Vec r, Vec b, Vec q, const Geom& g, int nrhs, const RedArgs& red, int grid_cap,
+              cudaStream_t st) {
     const int block = 256, grid = blas_grid(g.Vh, block, grid_cap) * nrhs;
     WL_REQUIRE(grid / nrhs <= red.slot_cap, "reduction capacity below the grid size");
-    xmy_norm_kernel<<<grid, block, 0, st>>>(r, b, q, g, nrhs, red);
+    if (qp == P_F64) xmy_norm_kernel<P_F64><<<grid, block, 0, st>>>(r, b, q, g, nrhs, red);
+    else if (qp == P_F32) xmy_norm_kernel<P_F32><<<grid, block, 0, st>>>(r, b, q, g, nrhs, red);
+    else throw Error(7, "xmy_norm: q must be FP64 or FP32");
     WL_LAUNCH_CHECK();
+}
+
+void xmy_norm64(Vec r, Vec b, Vec q, const Geom& g, int nrhs, const RedArgs& red, int grid_cap, cudaStream_t st) {
+    xmy_norm(P_F64, r, b, q, g, nrhs, red, grid_cap, st);
 }
 
 void norm2(Prec p, Vec v, const Geom& g, int nrhs, const RedArgs& red, int grid_cap, cudaStream_t st) {

@@ -29,6 +29,9 @@ void axpy(Prec yp, Vec y, Prec xp, Vec x, double a, const Geom& g, int nrhs, cud
 
 // r = b - q (FP64; r.p may be null), |b - q|^2 -> red
 void xmy_norm64(Vec r, Vec b, Vec q, const Geom& g, int nrhs, const RedArgs& red, int grid_cap, cudaStream_t st);
+// the same with q in FP64 or FP32
+void xmy_norm(Prec qp, Vec r, Vec b, Vec q, const Geom& g, int nrhs, const RedArgs& red, int grid_cap,
+              cudaStream_t st);
 
 // |v|^2 -> red
 void norm2(Prec p, Vec v, const Geom& g, int nrhs, const RedArgs& red, int grid_cap, cudaStream_t st);

@@ -133,7 +133,7 @@ constexpr int kSkipStride = sizeof(CGScalars) / sizeof(int);
 
 std::vector<SolveStats> cg_solve_prepared(SpinorField& x, const SpinorField& b, const GaugeField& g64,
                                           const GaugeField& glo, double kappa, const SolveParams& prm,
-                                          cudaStream_t st) {
+                                          cudaStream_t st, const GaugeField* g32) {
     NvtxRange nvtx_solve("wilson cg solve");
     auto t0 = std::chrono::steady_clock::now();
     const int nr = b.nrhs;
@@ -181,13 +181,26 @@ std::vector<SolveStats> cg_solve_prepared(SpinorField& x, const SpinorField& b, 
     }
     if (!prm.use_initial_guess)
         for (int k = 0; k < nr; k++) WL_CUDA(cudaMemsetAsync(x.block(0, k), 0, x.pbytes, st));
-    WL_CUDA(cudaMemcpyAsync(h_res, d_res, 2 * nr * sizeof(double), cudaMemcpyDeviceToHost, st));
+    // |bhat_k|: the scale of the FP32-residual threshold
+    norm2(P_F64, vec(bhat, 0), g, nr, red.args(slot(7), FIN_STORE, d_res + 5 * nr, nullptr), grid_cap, st);
+    WL_CUDA(cudaMemcpyAsync(h_res, d_res, 6 * nr * sizeof(double), cudaMemcpyDeviceToHost, st));
     WL_CUDA(cudaStreamSynchronize(st));
-    std::vector<double> bnorm(nr), target(nr);
+    std::vector<double> bnorm(nr), target(nr), bhat_norm(nr);
     for (int k = 0; k < nr; k++) {
         bnorm[k] = std::sqrt(h_res[k] + h_res[nr + k]);
         target[k] = prm.tol * bnorm[k];
+        bhat_norm[k] = std::sqrt(h_res[5 * nr + k]);
     }
+    // FP32 outer residuals (kF32ResidualRel): x and the operator in FP32
+    const bool f32_ok = g32 != nullptr && prm.tol < 1e-7 && prm.inner != P_F64;
+    SpinorField x32, q32, t32;
+    if (f32_ok) {
+        x32.alloc(P_F32, 0, nr, g);
+        q32.alloc(P_F32, 0, nr, g);
+        t32.alloc(P_F32, 1, nr, g);
+    }
+    std::vector<double> last_rnorm(nr, HUGE_VAL);
+    int outer_f32 = 0;
 
     Inner in;
     in.alloc(prm.inner, g, nr);
@@ -244,6 +257,8 @@ std::vector<SolveStats> cg_solve_prepared(SpinorField& x, const SpinorField& b, 
     std::vector<double> best(nr, HUGE_VAL);  // smallest FP64 residual so far
     int outer = 0;
     bool first = true;
+    bool force64 = false;  // the next residual is FP64
+    bool f32_off = false;  // no more FP32 residuals in this solve
     // device time of the inner iterations: events around each chunk's replay
     cudaEvent_t ev_in0 = nullptr, ev_in1 = nullptr;
     WL_CUDA(cudaEventCreate(&ev_in0));
@@ -254,24 +269,53 @@ std::vector<SolveStats> cg_solve_prepared(SpinorField& x, const SpinorField& b, 
             // r64 = bhat - Mhat x_e (FP64); the first residual of a solve from
             // x_e = 0 is bhat itself
             NvtxRange nvtx_outer("fp64 correction");
+            // FP32 residual while every unfinished right-hand side's expected
+            // residual is above kF32ResidualRel |bhat| (never for a convergence
+            // decision: see below)
+            bool use32 = f32_ok && outer > 0 && !force64 && !f32_off;
+            for (int k = 0; k < nr && use32; k++)
+                if (!finished[k] && !(last_rnorm[k] * delta > kF32ResidualRel * bhat_norm[k])) use32 = false;
+            force64 = false;
             if (outer == 0 && !prm.use_initial_guess) {
                 for (int k = 0; k < nr; k++) WL_CUDA(cudaMemsetAsync(q64.block(0, k), 0, q64.pbytes, st));
+                xmy_norm64(vec(r64, 0), vec(bhat, 0), vec(q64, 0), g, nr,
+                           red.args(slot(5), FIN_STORE, d_res + 2 * nr, nullptr), grid_cap, st);
+            } else if (use32) {
+                convert(P_F32, vec(x32, 0), P_F64, vec(x, 0), g, nr, st);
+                schur_apply(*g32, P_F32, vec(q32, 0), vec(x32, 0), vec(t32, 1), nr, kappa, 0, nullptr, nullptr, 0,
+                            0, st);
+                hops += 2;
+                outer_f32++;
+                xmy_norm(P_F32, vec(r64, 0), vec(bhat, 0), vec(q32, 0), g, nr,
+                         red.args(slot(5), FIN_STORE, d_res + 2 * nr, nullptr), grid_cap, st);
             } else {
                 schur_apply(g64, P_F64, vec(q64, 0), vec(x, 0), vec(t64, 1), nr, kappa, 0, nullptr, nullptr, 0, 0,
                             st);
                 hops += 2;
+                xmy_norm64(vec(r64, 0), vec(bhat, 0), vec(q64, 0), g, nr,
+                           red.args(slot(5), FIN_STORE, d_res + 2 * nr, nullptr), grid_cap, st);
             }
-            xmy_norm64(vec(r64, 0), vec(bhat, 0), vec(q64, 0), g, nr,
-                       red.args(slot(5), FIN_STORE, d_res + 2 * nr, nullptr), grid_cap, st);
             WL_CUDA(cudaMemcpyAsync(h_res + 2 * nr, d_res + 2 * nr, nr * sizeof(double), cudaMemcpyDeviceToHost,
                                     st));
             WL_CUDA(cudaStreamSynchronize(st));
             std::vector<double> rnorm(nr, 0.0);
+            // an FP32 residual at or below its target decides nothing: recompute in
+            // FP64; one that has not halved has reached the FP32 noise floor
+            if (use32) {
+                for (int k = 0; k < nr; k++) {
+                    if (finished[k]) continue;
+                    const double r32 = std::sqrt(h_res[2 * nr + k]);
+                    if (r32 <= target[k]) force64 = true;
+                    if (!(r32 <= 0.5 * last_rnorm[k])) f32_off = true;
+                }
+                if (force64) continue;
+            }
             bool all_done = true;
             const bool budget = outer < prm.max_restarts;
             for (int k = 0; k < nr; k++) {
                 if (finished[k]) continue;
                 rnorm[k] = std::sqrt(h_res[2 * nr + k]);
+                last_rnorm[k] = rnorm[k];
                 if (!std::isfinite(rnorm[k])) {
                     finished[k] = 1;
                     stats[k].status = 6;
@@ -462,6 +506,7 @@ std::vector<SolveStats> cg_solve_prepared(SpinorField& x, const SpinorField& b, 
         s.hop_applications = hops;
         s.seconds = secs;
         s.inner_seconds = inner_ms * 1e-3;
+        s.outer_f32 = outer_f32;
         if (s.status == 0 && !(s.true_rel_resid <= prm.tol)) s.status = std::isfinite(s.true_rel_resid) ? 4 : 6;
     }
     return stats;
@@ -485,6 +530,19 @@ std::vector<SolveStats> cg_solve(double* xc, const double* gauge_canon, const do
         pack_gauge(glo, gauge_canon, st);
         inner_gauge = &glo;
     }
+    // FP32 links for the FP32 outer residuals: the inner links when they are FP32
+    GaugeField g32f;
+    const GaugeField* g32 = nullptr;
+    if (prm.inner == P_F32) {
+        g32 = inner_gauge;
+    } else if (prm.inner != P_F64 && prm.tol < 1e-7) {
+        g32f.prec = P_F32;
+        g32f.recon = 12;
+        g32f.g = g;
+        g32f.buf.alloc(gauge_bytes(P_F32, 12, g.stride));
+        pack_gauge(g32f, gauge_canon, st);
+        g32 = &g32f;
+    }
     SpinorField b, x;
     b.alloc(P_F64, 2, nrhs, g);
     x.alloc(P_F64, 2, nrhs, g);
@@ -493,7 +551,7 @@ std::vector<SolveStats> cg_solve(double* xc, const double* gauge_canon, const do
         pack_spinor(b, k, bc + per * k, st);
         if (prm.use_initial_guess) pack_spinor(x, k, xc + per * k, st);
     }
-    std::vector<SolveStats> stats = cg_solve_prepared(x, b, g64, *inner_gauge, kappa, prm, st);
+    std::vector<SolveStats> stats = cg_solve_prepared(x, b, g64, *inner_gauge, kappa, prm, st, g32);
     for (int k = 0; k < nrhs; k++) unpack_spinor(x, k, xc + per * k, st);
     WL_CUDA(cudaStreamSynchronize(st));
     return stats;

@@ -39,6 +39,18 @@ inline double default_delta(Prec ip) {
 // bounds an inner solve whose delta is below what its precision can reach.
 constexpr int kInnerCap = 1000;
 
+// FP32 outer residuals: while every unfinished right-hand side's expected
+// residual (its last one times the inner reduction delta) is above this
+// fraction of |bhat|, the outer residual r = bhat - Mhat x is computed with
+// FP32 fields and links.  Its error is about 1e-7 |Mhat| |x| (the FP32
+// rounding of x and of the operator), so cond(Mhat) 1e-7 |bhat|: a few
+// percent of |r| at cond = 100, which the defect correction absorbs.  Below
+// the threshold, and for every convergence decision, the residual is FP64;
+// an FP32 residual that has not fallen below half the previous one (its
+// noise floor reached) ends the FP32 residuals of the solve.  Used when the
+// target is below 1e-7 (else every residual is FP64).
+constexpr double kF32ResidualRel = 1e-4;
+
 // A right-hand side whose FP64 residual grows past this factor times the
 // smallest one it has had is diverging (an inner precision too coarse for its
 // delta): it stops with WILSON_ERR_NOCONV instead of spending maxiter.
@@ -52,6 +64,7 @@ struct SolveStats {
     double true_rel_resid = 0.0;
     double seconds = 0.0;
     double inner_seconds = 0.0;  // device time of the inner CG iterations (graph replays)
+    int outer_f32 = 0;           // FP64 corrections whose residual was computed in FP32
 };
 
 // Mhat (dag = 0) or Mhat^dag (dag = 1) on even blocks of nrhs right-hand
@@ -69,7 +82,8 @@ void schur_tune(const GaugeField& gf, Prec sp, Vec out, Vec in, Vec tmp, int nrh
 // right-hand side (outer_iters, hop_applications and seconds are shared).
 std::vector<SolveStats> cg_solve_prepared(SpinorField& x, const SpinorField& b, const GaugeField& g64,
                                           const GaugeField& glo, double kappa, const SolveParams& prm,
-                                          cudaStream_t st);
+                                          cudaStream_t st,
+                                          const GaugeField* g32 = nullptr);
 
 // The same on canonical complex128 device fields (nrhs fields back to back).
 std::vector<SolveStats> cg_solve(double* x, const double* gauge_canon, const double* b, int nrhs, const Geom& g,

@@ -44,7 +44,7 @@ class wilson_solver_params(ctypes.Structure):
 class wilson_solve_stats(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int), ("outer_iters", ctypes.c_int), ("inner_iters", ctypes.c_int),
                 ("hop_applications", ctypes.c_int), ("true_rel_resid", ctypes.c_double),
-                ("seconds", ctypes.c_double), ("inner_seconds", ctypes.c_double)]
+                ("seconds", ctypes.c_double), ("inner_seconds", ctypes.c_double), ("outer_f32", ctypes.c_int)]
 
 
 class wilson_problem(ctypes.Structure):

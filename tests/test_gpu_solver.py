@@ -227,3 +227,35 @@ def test_kappa_zero_is_identity(w, inner):
     x, st = solve(w, U, b, dims, 0.0, w.PREC[inner])
     assert st["rc"] == 0 and st["true_rel_resid"] <= 1e-10
     assert rel_l2(x, b) <= 1e-10
+
+
+@pytest.mark.parametrize("inner", ["f16", "bf16", "f32"])
+def test_fp32_outer_residuals(w, oracle_mod, inner):
+    """The early corrections of an F16/BF16 solve compute their residual with
+    FP32 fields and links (expected residual above 1e-4 |bhat|); an F32 solve
+    (inner reduction 1e-4) has none.  Every solve still reaches the 1e-10
+    true residual by the oracle's FP64 M, also in the lockstep multi-RHS
+    form.  A target at or above 1e-7 uses only FP64 residuals."""
+    dims = (8, 6, 4, 10)
+    kappa = 0.1350
+    U = inputs.gauge_field(dims, "weak", eps=0.3, seed=161)
+    b = inputs.gaussian_spinor(dims, seed=162)
+    x, st = solve(w, U, b, dims, kappa, w.PREC[inner])
+    assert st["rc"] == 0
+    if inner == "f32":
+        assert st["outer_f32"] == 0
+    else:
+        assert st["outer_f32"] >= 1
+        assert st["outer_f32"] < st["outer_iters"]  # the last corrections are FP64
+    assert true_resid(oracle_mod, U, x, b, dims, kappa) <= 1.1e-10
+    x, st = solve(w, U, b, dims, kappa, w.PREC[inner], tol=1e-6)
+    assert st["rc"] == 0 and st["outer_f32"] == 0
+    assert true_resid(oracle_mod, U, x, b, dims, kappa) <= 1.1e-6
+    bs = inputs.gaussian_spinor(dims, seed=163, nrhs=3)
+    bs[1] *= 1e-4  # a right-hand side of another scale: its own |bhat| sets its threshold
+    xs = dev(np.zeros_like(bs))
+    rc, sts = w.wilson_cg_solve_multi(xs, dev(U), dev(bs), 3, w.lattice(dims), kappa, w.solver_defaults(w.PREC[inner]))
+    assert rc == 0 and (sts[0]["outer_f32"] >= 1) == (inner != "f32")
+    xh = host(xs)
+    for k in range(3):
+        assert true_resid(oracle_mod, U, xh[k], bs[k], dims, kappa) <= 1.1e-10
