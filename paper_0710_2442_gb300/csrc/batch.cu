@@ -118,9 +118,11 @@ __global__ void __launch_bounds__(256) bp_kernel(const BatchArgs A, const BOp op
     WL_TILE_LOOP_END
 }
 
-// x_e += xin (FP64 += FP32)   (OUTER)
+// x_e += xin (FP64 += FP32), and an FP32 copy of x_e when the problem's
+// residual is FP32 this correction   (OUTER)
 __global__ void __launch_bounds__(256) baxpy_kernel(const BatchArgs A, const BOp op) {
     WL_TILE_LOOP_BEGIN
+    const bool x32 = __ldcg(&A.state[pid].use32) != 0;  // set by the previous finisher
     for (int j = threadIdx.x; j < A.tile; j += blockDim.x) {
         const int h = h0 + j;
         if (h >= g.Vh) break;
@@ -134,20 +136,34 @@ __global__ void __launch_bounds__(256) baxpy_kernel(const BatchArgs A, const BOp
             xv[k].im += (double)ev[k].im;
         }
         SpinorFmt<P_F64>::store(Pr.f[BF_X], g.stride, h, xv);
+        if (x32) {
+            cpx<float> xf[12];
+#pragma unroll
+            for (int k = 0; k < 12; k++) xf[k] = {(float)xv[k].re, (float)xv[k].im};
+            SpinorFmt<P_F32>::store(Pr.f[BF_X32], g.stride, h, xf);
+        }
     }
     WL_TILE_LOOP_END
 }
 
-// r64 = bhat - q64, |r64|^2   (OUTER)
+// r64 = bhat - q, |r64|^2, q = Mhat x in FP64 (q64) or FP32 (q32)   (OUTER)
 __global__ void __launch_bounds__(256) bxmy_kernel(const BatchArgs A, const BOp op) {
     WL_TILE_LOOP_BEGIN
+    const bool q32 = __ldcg(&A.state[pid].use32) != 0;
     double nrm = 0.0;
     for (int j = threadIdx.x; j < A.tile; j += blockDim.x) {
         const int h = h0 + j;
         if (h >= g.Vh) break;
         cpx<double> bv[12], qv[12];
         SpinorFmt<P_F64>::load(Pr.f[BF_BHAT], g.stride, h, bv);
-        SpinorFmt<P_F64>::load(Pr.f[BF_Q64], g.stride, h, qv);
+        if (q32) {
+            cpx<float> qf[12];
+            SpinorFmt<P_F32>::load(Pr.f[BF_Q32], g.stride, h, qf);
+#pragma unroll
+            for (int k = 0; k < 12; k++) qv[k] = {(double)qf[k].re, (double)qf[k].im};
+        } else {
+            SpinorFmt<P_F64>::load(Pr.f[BF_Q64], g.stride, h, qv);
+        }
 #pragma unroll
         for (int k = 0; k < 12; k++) {
             bv[k] = csub(bv[k], qv[k]);
@@ -276,9 +292,10 @@ __global__ void bfinal_kernel(BatchGlobal* G) { G->t_end = globaltimer(); }
 // ---------------------------------------------------------------------------
 struct HostProb {
     Geom g;
-    GaugeField g64, glo;
+    GaugeField g64, glo, g32;
     SpinorField f[BF_N];
     double kappa;
+    bool res32_ok = false;  // FP32 residuals for the early corrections
 };
 
 template <class F>
@@ -302,7 +319,7 @@ struct BatchRun {
     DevBuf probs, state, tile_prob, global, partials, counters, ids;
     BatchArgs A{};
     int grid = 1;
-    LaunchConfig hop_lo{128, 1}, hop_64{128, 0};
+    LaunchConfig hop_lo{128, 1}, hop_64{128, 0}, hop_32{128, 3};
     cudaGraphConditionalHandle handle{};
     BatchGlobal* G() const { return global.as<BatchGlobal>(); }
 
@@ -318,6 +335,7 @@ struct BatchRun {
         o.phase = phase;
         o.skip_done = skip_done;
         o.fin = fin;
+        o.res32 = -1;
         o.zero_first = 0;
         o.partials = partials.as<double>() + (size_t)rslot * ntiles;
         o.counters = counters.as<unsigned int>() + (size_t)rslot * nprob;
@@ -329,8 +347,10 @@ struct BatchRun {
         launch_bhop<SP, GP>(A, o, dag, c.variant, c.block, grid, st);
     }
     void hop(const BOp& o, int dag, cudaStream_t st) const {
-        if (o.use64) {
+        if (o.use64 == 1) {
             hop_t<P_F64, P_F64>(o, dag, hop_64, st);
+        } else if (o.use64 == 2) {
+            hop_t<P_F32, P_F32>(o, dag, hop_32, st);
         } else {
             dispatch_low(ip, [&](auto I) { hop_t<decltype(I)::value, decltype(I)::value>(o, dag, hop_lo, st); });
         }
@@ -366,6 +386,22 @@ void build_problem(HostProb& P, const wilson_problem& in, Prec ip, const SolvePa
     P.f[BF_Q].alloc(ip, 0, 1, P.g);
     P.f[BF_R].alloc(ip, 0, 1, P.g);
     P.f[BF_T].alloc(ip, 1, 1, P.g);
+    // FP32 residuals of the early corrections (solver.h, kF32ResidualRel):
+    // FP32 links (the inner ones when the inner solve is FP32) and fields
+    P.res32_ok = prm.tol < 1e-7 && ip != P_F64;
+    if (P.res32_ok) {
+        if (ip != P_F32) {
+            P.g32.prec = P_F32;
+            P.g32.recon = 12;
+            P.g32.g = P.g;
+            P.g32.buf.alloc(gauge_bytes(P_F32, 12, P.g.stride));
+            pack_gauge(P.g32, in.gauge, st);
+        }
+        P.f[BF_X32].alloc(P_F32, 0, 1, P.g);
+        P.f[BF_Q32].alloc(P_F32, 0, 1, P.g);
+        P.f[BF_T32].alloc(P_F32, 1, 1, P.g);
+        WL_CUDA(cudaMemsetAsync(P.f[BF_X32].buf.p, 0, P.f[BF_X32].buf.bytes, st));  // read by tuning launches
+    }
     pack_spinor(P.f[BF_B], 0, in.b, st);
     if (prm.use_initial_guess) pack_spinor(P.f[BF_X], 0, in.x, st);
 }
@@ -393,6 +429,8 @@ std::unique_ptr<BatchRun> make_run(const std::vector<HostProb>& hp, const std::v
         }
         D.g64 = P.g64.buf.as<const char>();
         D.glo = P.glo.buf.as<const char>();
+        D.g32 = !P.res32_ok ? nullptr : P.glo.prec == P_F32 ? D.glo : P.g32.buf.as<const char>();
+        D.res32_ok = P.res32_ok && !small;
         D.kappa = P.kappa;
         D.tol = prm.tol;
         D.delta = prm.delta > 0 ? prm.delta : default_delta(R->ip);
@@ -557,6 +595,14 @@ void batch_solve(int n, const wilson_problem* probs, const SolveParams& prm, wil
         const BOp o64 = R->op(BF_Q64, BF_T64, BF_X, 0, 1, 2, -1, 0, BF_NONE, 0);
         R->hop_64 = tune_launch(key, cands64, LaunchConfig{128, 0}, st,
                                 [&](const LaunchConfig& c) { Rp->hop_t<P_F64, P_F64>(o64, 0, c, st); });
+        bool any32 = false;
+        for (int i : R->members) any32 = any32 || hp[i].res32_ok;
+        if (any32) {
+            snprintf(key, sizeof(key), "bhop:f32res:n%d:t%d", R->nprob, R->ntiles);
+            const BOp o32 = R->op(BF_Q32, BF_T32, BF_X32, 0, 2, 2, -1, 0, BF_NONE, 0);
+            R->hop_32 = tune_launch(key, cands, LaunchConfig{128, 3}, st,
+                                    [&](const LaunchConfig& c) { Rp->hop_t<P_F32, P_F32>(o32, 0, c, st); });
+        }
     }
 
     cudaStream_t st2 = nullptr, st3 = nullptr;
@@ -605,8 +651,16 @@ void batch_solve(int n, const wilson_problem* probs, const SolveParams& prm, wil
         BOp t64 = R.op(BF_T64, BF_X, -1, 1, 1, 0, PH_OUTER, 0, BF_NONE, 1);
         BOp q64 = R.op(BF_Q64, BF_T64, BF_X, 0, 1, 2, PH_OUTER, 0, BF_NONE, 1);
         t64.zero_first = q64.zero_first = prm.use_initial_guess ? 0 : 1;
+        t64.res32 = q64.res32 = 0;
         R.hop(t64, 0, s);
         R.hop(q64, 0, s);
+        // the problems whose residual is FP32 this correction: the same two hops
+        // on the FP32 copy of x with FP32 links
+        BOp t32 = R.op(BF_T32, BF_X32, -1, 1, 2, 0, PH_OUTER, 0, BF_NONE, 1);
+        BOp q32 = R.op(BF_Q32, BF_T32, BF_X32, 0, 2, 2, PH_OUTER, 0, BF_NONE, 1);
+        t32.res32 = q32.res32 = 1;
+        R.hop(t32, 0, s);
+        R.hop(q32, 0, s);
         blas(R, bxmy_kernel, R.op(0, 0, -1, 0, 0, 0, PH_OUTER, 0, BFIN_OUTER, 1), s);
         dispatch_low(ip, [&](auto I) {
             bprep_kernel<decltype(I)::value><<<R.grid, 256, 0, s>>>(R.A, R.op(0, 0, -1, 0, 0, 0, PH_OUTER, 0,
@@ -821,7 +875,7 @@ void batch_solve(int n, const wilson_problem* probs, const SolveParams& prm, wil
             o.hop_applications = 4 * S.sc.iter + 4 * (S.outer + 1) + (prm.use_initial_guess ? 4 : 2);
             o.seconds = S.phase == PH_DONE && S.t_done >= t_first ? (double)(S.t_done - t_first) * 1e-9 : -1.0;
             o.inner_seconds = 0.0;
-            o.outer_f32 = 0;
+            o.outer_f32 = S.n32;
             int status = S.status;
             if (status == 0 && S.phase != PH_DONE) status = hg[r].timed_out ? WILSON_ERR_TIMEOUT : WILSON_ERR_NOCONV;
             if (status == 0 && !(o.true_rel_resid <= prm.tol)) status = WILSON_ERR_NOCONV;

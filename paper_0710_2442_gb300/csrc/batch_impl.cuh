@@ -16,7 +16,8 @@ namespace bt {
 
 constexpr int kTile = 256;  // default half-lattice sites per tile (the run's tile is tuned: 128, 256, 512)
 
-enum BField { BF_B, BF_X, BF_BHAT, BF_R64, BF_Q64, BF_T64, BF_XIN, BF_S, BF_SLOW, BF_P, BF_Q, BF_R, BF_T, BF_N };
+enum BField { BF_B, BF_X, BF_BHAT, BF_R64, BF_Q64, BF_T64, BF_XIN, BF_S, BF_SLOW, BF_P, BF_Q, BF_R, BF_T,
+              BF_X32, BF_Q32, BF_T32, BF_N };
 enum Phase { PH_OUTER = 0, PH_INNER = 1, PH_DONE = 2 };
 enum BFin { BF_NONE = -1, BFIN_ALPHA, BFIN_RES, BFIN_BETA, BFIN_START, BFIN_OUTER, BFIN_BNORM, BFIN_TRUE };
 
@@ -26,11 +27,13 @@ struct BatchProb {
     long long fp[BF_N];   // parity step of full fields, 0 for half fields
     const char* g64;      // FP64 18-real links
     const char* glo;      // inner links
+    const char* g32;      // FP32 12-real links of the FP32 residuals (null: none)
     double kappa, tol, delta;
     int tile0, ntiles;
     int maxiter, max_outer;
     int small;            // 1: solved by one CTA (small_solve_kernel), no tiles
     int keep_x;           // 1: x holds an initial guess
+    int res32_ok;         // 1: early corrections may compute their residual in FP32
 };
 
 struct BatchState {
@@ -45,6 +48,10 @@ struct BatchState {
     double best2;  // smallest |r|^2 of the FP64 corrections so far
     double res2;
     unsigned long long t_done;
+    int use32;    // the next correction computes its residual with FP32 fields and links
+    int f32_off;  // an FP32 residual stopped halving: no more of them
+    int n32;      // corrections whose residual was FP32
+    int pad2;
 };
 
 struct BatchGlobal {
@@ -65,11 +72,12 @@ struct BatchArgs {
 struct BOp {
     int f_out, f_in, f_x;   // field ids (f_x < 0: no xpay)
     int out_parity;
-    int use64;              // links: FP64 (1) or inner (0)
+    int use64;              // links: FP64 (1), inner (0), or the FP32 residual links (2)
     int coef;               // a = 1, kappa, -kappa^2, -kappa
     int phase;              // only problems in this phase (-1: all)
     int skip_done;          // also skip problems whose inner CG is done
     int fin;                // BFin of the fused reduction (BF_NONE: none)
+    int res32;              // only problems whose next residual is FP32 (1), FP64 (0), or all (-1)
     int zero_first;         // the FP64 correction hops: while a problem's iterate is still zero
                             // (its first correction), the hop term is zero and is not computed
     double* partials;       // [ntiles]
@@ -122,13 +130,23 @@ __device__ inline void batch_finish(int op, const BatchProb& P, BatchState& S, d
             S.first = 0;
             break;
         case BFIN_OUTER: {
+            // the correction's residual was FP32 (use32) or FP64; an FP32 one
+            // decides no convergence (the inner solve it starts stops at once
+            // and the next residual is FP64), and one that has not halved has
+            // reached the FP32 noise floor (kF32ResidualRel, solver.h)
+            const bool was32 = S.use32 != 0;
+            const double prev2 = S.rnorm2;
             S.rnorm2 = sum;
             if (S.outer == 0 || sum < S.best2) S.best2 = sum;
             const double target2 = P.tol * P.tol * S.bnorm2;
+            if (was32) {
+                S.n32 += 1;
+                if (!(sum <= 0.25 * prev2)) S.f32_off = 1;
+            }
             if (!isfinite(sum)) {
                 S.status = WILSON_ERR_NUMERIC;
                 S.next_phase = PH_DONE;
-            } else if (sum <= target2) {
+            } else if (sum <= target2 && !was32) {
                 S.next_phase = PH_DONE;
             } else if (S.outer >= P.max_outer || sc.iter >= P.maxiter ||
                        (S.outer > 0 && sum > kDivergence * kDivergence * S.best2)) {
@@ -142,6 +160,10 @@ __device__ inline void batch_finish(int op, const BatchProb& P, BatchState& S, d
                 sc.snorm2 = sum;
                 sc.done = 0;
                 sc.maxiter = min(P.maxiter, sc.iter + kInnerCap);  // iter counts the whole solve
+                // the next residual in FP32 while the expected one (this one
+                // times delta) is above kF32ResidualRel |b|
+                S.use32 = P.res32_ok && !S.f32_off &&
+                          P.delta * P.delta * sum > kF32ResidualRel * kF32ResidualRel * S.bnorm2;
             }
             if (S.next_phase == PH_DONE) S.t_done = globaltimer();
             break;
@@ -161,6 +183,7 @@ __device__ __forceinline__ bool tile_active(const BatchArgs& A, const BOp& op, i
         int act = 1;
         if (op.phase >= 0 && __ldcg(&S.phase) != op.phase) act = 0;
         if (act && op.skip_done && __ldcg(&S.sc.done)) act = 0;
+        if (act && op.res32 >= 0 && __ldcg(&S.use32) != op.res32) act = 0;
         s_act = act;
     }
     __syncthreads();
@@ -204,7 +227,7 @@ __global__ void __launch_bounds__(256, MINB) bhop_kernel(const BatchArgs A, cons
         const BatchProb& Pr = A.probs[pid];
         HopParams P;
         P.g = Pr.g;
-        P.gauge = op.use64 ? Pr.g64 : Pr.glo;
+        P.gauge = op.use64 == 1 ? Pr.g64 : op.use64 == 2 ? Pr.g32 : Pr.glo;
         const int p = op.out_parity;
         char* out = Pr.f[op.f_out] + p * Pr.fp[op.f_out];
         const char* in = Pr.f[op.f_in] + (1 - p) * Pr.fp[op.f_in];
@@ -265,7 +288,7 @@ __global__ void __launch_bounds__(256, MINB) bhop_kernel_p(const BatchArgs A, co
         const BatchProb& Pr = A.probs[pid];
         HopParams P;
         P.g = Pr.g;
-        P.gauge = Pr.glo;
+        P.gauge = op.use64 == 2 ? Pr.g32 : Pr.glo;
         const int p = op.out_parity;
         char* out = Pr.f[op.f_out] + p * Pr.fp[op.f_out];
         const char* in = Pr.f[op.f_in] + (1 - p) * Pr.fp[op.f_in];

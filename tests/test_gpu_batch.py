@@ -217,3 +217,25 @@ def test_small_path_block_and_cluster(w, oracle_mod, monkeypatch, cluster, inner
     for q, (dims, U, b, kappa), s in zip(probs, hf, st):
         assert s["status"] == 0
         assert true_resid(oracle_mod, U, host(q["x"]), b, dims, kappa) <= 1.1e-10
+
+
+@pytest.mark.parametrize("inner", ["f16", "bf16"])
+def test_batch_fp32_outer_residuals(w, oracle_mod, monkeypatch, inner):
+    """The early corrections of the device-loop problems compute their
+    residual with FP32 fields and links; every problem still reaches the
+    1e-10 true residual by the oracle's FP64 M.  A target of 1e-6 uses only
+    FP64 residuals."""
+    monkeypatch.setenv("WILSON_BATCH_SMALL_VH", "0")
+    probs, hf = make_batch(w, MIX, seed0=500)
+    rc, st, info = w.wilson_batch_solve(probs, w.solver_defaults(w.PREC[inner]))
+    assert rc == 0 and not info["timed_out"]
+    assert all(s["outer_f32"] >= 1 and s["outer_f32"] < s["outer_iters"] for s in st)
+    for q, (dims, U, b, kappa), s in zip(probs, hf, st):
+        assert true_resid(oracle_mod, U, host(q["x"]), b, dims, kappa) <= 1.1e-10
+    probs, hf = make_batch(w, MIX, seed0=500)
+    p = w.solver_defaults(w.PREC[inner])
+    p.tol = 1e-6
+    rc, st, info = w.wilson_batch_solve(probs, p)
+    assert rc == 0 and all(s["outer_f32"] == 0 for s in st)
+    for q, (dims, U, b, kappa), s in zip(probs, hf, st):
+        assert true_resid(oracle_mod, U, host(q["x"]), b, dims, kappa) <= 1.1e-6
