@@ -542,9 +542,12 @@ void batch_solve(int n, const wilson_problem* probs, const SolveParams& prm, wil
             loops.push_back(make_run(hp, c, false, prm, st, tile_pin));
             continue;
         }
-        // 256 first: the tuner resolves near-ties (within 1 %) to the earlier
-        // candidate, and an isolated hop does not see how the classes share
-        // the GPU inside the graph
+        // 256 first, and another tile only if its hop is more than 5 % faster:
+        // an isolated hop does not see what more tiles cost inside the graph
+        // (more blocks for every phase-filtered kernel of the class, sharing
+        // the GPU with the other classes).  Measured on the 64-problem batch:
+        // 128-site tiles for the 16^3 x 32 class, picked on a 0.5 % faster
+        // hop, made the whole batch 5.6 % slower (0.266 against 0.252 s).
         std::unique_ptr<BatchRun> cand[3];
         const int tiles[3] = {256, 128, 512};
         long long vh = 0;
@@ -561,7 +564,8 @@ void batch_solve(int n, const wilson_problem* probs, const SolveParams& prm, wil
                 dispatch_low(ip, [&](auto I) {
                     Rt.hop_t<decltype(I)::value, decltype(I)::value>(o, 0, LaunchConfig{128, 4}, st);
                 });
-            });
+            },
+            0.05);
         loops.push_back(std::move(cand[pick.block == 256 ? 0 : pick.block == 128 ? 1 : 2]));
     }
     std::unique_ptr<BatchRun> smallrun;

@@ -112,9 +112,12 @@ struct LaunchConfig {
 // candidate is timed by running `run` on the stream with CUDA events, and the
 // fastest is cached (in memory, and in the file named by WILSON_TUNE_CACHE if
 // set).  `run` must be idempotent: it is executed several times.
+// margin: a later candidate replaces the best one so far only when it is
+// faster by more than this fraction (so that near-ties resolve to the
+// earlier candidate).
 LaunchConfig tune_launch(const std::string& key, const std::vector<LaunchConfig>& candidates,
                          const LaunchConfig& fallback, cudaStream_t st,
-                         const std::function<void(const LaunchConfig&)>& run);
+                         const std::function<void(const LaunchConfig&)>& run, double margin = 0.01);
 // The decision for `key` if one is cached (in memory or in the cache file)
 // and among `candidates`, else `fallback`; never times anything and never
 // synchronises.

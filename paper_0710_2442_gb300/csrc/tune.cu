@@ -5,8 +5,8 @@
 // on the caller's stream with CUDA events (per candidate: a warm-up launch,
 // one timed launch, then two timed bursts of four back-to-back launches
 // unless the single launch took longer than 300 us; the best time per launch
-// counts), and the fastest is kept: a later candidate must be more than 1 %
-// faster to replace an earlier one.  Tuning synchronises the stream, so the
+// counts), and the fastest is kept: a later candidate must be faster by more
+// than a margin (1 %; the batch's tile size asks 5 %) to replace an earlier one.  Tuning synchronises the stream, so the
 // first call for a new key is slower; it is skipped while the stream is being
 // captured into a graph (the fallback is used and the key is not stored).
 // A decision from the cache file that is not among the current candidates
@@ -132,7 +132,7 @@ LaunchConfig tune_lookup(const std::string& key0, const std::vector<LaunchConfig
 
 LaunchConfig tune_launch(const std::string& key0, const std::vector<LaunchConfig>& candidates,
                          const LaunchConfig& fallback, cudaStream_t st,
-                         const std::function<void(const LaunchConfig&)>& run) {
+                         const std::function<void(const LaunchConfig&)>& run, double margin) {
     const std::string key = device_tag() + "|" + key0;
     {
         LaunchConfig c;
@@ -151,9 +151,9 @@ LaunchConfig tune_launch(const std::string& key0, const std::vector<LaunchConfig
     // longer than 300 us (its launch gap is then negligible and bursts would
     // make tuning slow), twice as a burst of kBurst back-to-back launches, the
     // way operators run; the best time per launch counts.  A later candidate
-    // replaces the best one only when it is more than 1 % faster, so candidates
-    // within timing noise of each other resolve to the same (earlier) choice
-    // in every process.
+    // replaces the best one only when it is faster by more than the margin,
+    // so candidates within timing noise of each other resolve to the same
+    // (earlier) choice in every process.
     constexpr int kBurst = 4;
     Entry best{fallback, 1e30f};
     for (const LaunchConfig& c : candidates) {
@@ -176,7 +176,7 @@ LaunchConfig tune_launch(const std::string& key0, const std::vector<LaunchConfig
         const float us = ms_best * 1e3f;
         if (env_flag("WILSON_TUNE_VERBOSE", false))
             fprintf(stderr, "[wilson tune]   %s block %d variant %d: %.2f us\n", key.c_str(), c.block, c.variant, us);
-        if (us < 0.99f * best.us) best = Entry{c, us};
+        if (us < (float)(1.0 - margin) * best.us) best = Entry{c, us};
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
