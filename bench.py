@@ -483,12 +483,31 @@ def run_dd_block(w, torch, dev, stream, fields, single_us, n=2):
     def hop():
         for r in range(n):
             w.wilson_dd_hop(outs[r], gauges[r], ins[r], recv_next[r], recv_prev[r], 0, sp.first(r), sp.last(r),
-                            stream)
+                            w.WILSON_DD_ALL, stream)
 
     def apply():
         pack()
         exchange_loopback(sp, send_prev, send_next, recv_next, recv_prev)
         hop()
+
+    side = torch.cuda.Stream(dev)
+    packed, moved = torch.cuda.Event(), torch.cuda.Event()
+
+    def apply_overlapped():
+        # the face copies on a second stream while the interior t-slices are applied
+        pack()
+        packed.record(stream)
+        side.wait_event(packed)
+        with torch.cuda.stream(side):
+            exchange_loopback(sp, send_prev, send_next, recv_next, recv_prev)
+        moved.record(side)
+        for r in range(n):
+            w.wilson_dd_hop(outs[r], gauges[r], ins[r], None, None, 0, sp.first(r), sp.last(r),
+                            w.WILSON_DD_INTERIOR, stream)
+        stream.wait_event(moved)
+        for r in range(n):
+            w.wilson_dd_hop(outs[r], gauges[r], ins[r], recv_next[r], recv_prev[r], 0, sp.first(r), sp.last(r),
+                            w.WILSON_DD_FACES, stream)
 
     apply()
     parts = []
@@ -499,7 +518,8 @@ def run_dd_block(w, torch, dev, stream, fields, single_us, n=2):
     DD_OUTPUT[0] = sp.gather_half(parts)
     reps = 20
     res = {}
-    for name, fn in (("pack_exchange_hop", apply), ("hop_only", hop), ("pack_only", pack)):
+    for name, fn in (("pack_exchange_hop", apply), ("overlapped", apply_overlapped), ("hop_only", hop),
+                     ("pack_only", pack)):
         for _ in range(3):
             fn()
         torch.cuda.synchronize(dev)
@@ -516,7 +536,9 @@ def run_dd_block(w, torch, dev, stream, fields, single_us, n=2):
     out = {"workload": "dslash_eo_f32_32^3x64 split along t", "subdomains": n, "local_dims": list(sp.local_dims),
            "exchange": "loopback device copies on one GPU",
            "face_bytes_per_application": 2 * n * 48 * sp.Vs // 2,
-           "us_per_application": round(res["pack_exchange_hop"], 2),
+           "us_per_application": round(res["overlapped"], 2),
+           "us_serial_pack_exchange_hop": round(res["pack_exchange_hop"], 2),
+           "overlap": "face copies on a second stream during the interior t-slices' hop",
            "us_hops_only": round(res["hop_only"], 2), "us_pack_only": round(res["pack_only"], 2),
            "single_lattice_us": single_us,
            "hop_frac_of_hbm": round(byts / (res["hop_only"] * 1e-6) / 1e9 / peak, 4)}

@@ -324,15 +324,26 @@ long long wilson_dd_halo_bytes(const wilson_lattice* L, int prec);
 int wilson_dd_pack(void* send_prev, void* send_next, const wilson_gauge* g, const wilson_spinor* in,
                    int dagger, void* stream);
 
-/* out (parity p) = D_{p,1-p} in on this sub-lattice, the t-hops across its
- * two faces taken from recv_next (the next sub-lattice's send_prev) and
- * recv_prev (the previous one's send_next).  t_first / t_last: the sub-
- * lattice holds the lattice's first / last t-slice, so that the boundary
- * phase of t (g's lattice) applies on that face.  A single sub-lattice
- * (t_first = t_last = 1, its own buffers) is the undecomposed operator.
- * Asynchronous on the stream. */
+/* Parts of the sub-lattice hop (the part argument of wilson_dd_hop). */
+typedef enum {
+    WILSON_DD_ALL = 0,       /* every site                                                  */
+    WILSON_DD_INTERIOR = 1,  /* t-slices 1 .. Lr-2: needs no face buffer, so it can run while  */
+                             /* the buffers are still being exchanged                          */
+    WILSON_DD_FACES = 2      /* t-slices 0 and Lr-1 (the sites whose t-hops cross a face)    */
+} wilson_dd_part;
+
+/* out (parity p) = D_{p,1-p} in on this sub-lattice (or on one part of its
+ * sites: INTERIOR and FACES together are ALL), the t-hops across its two
+ * faces taken from recv_next (the next sub-lattice's send_prev) and
+ * recv_prev (the previous one's send_next); INTERIOR reads neither (they
+ * may be NULL).  t_first / t_last: the sub-lattice holds the lattice's
+ * first / last t-slice, so that the boundary phase of t (g's lattice)
+ * applies on that face.  A single sub-lattice (t_first = t_last = 1, its
+ * own buffers) is the undecomposed operator.  The first ALL call of a
+ * lattice times its launch configurations (synchronising once); the
+ * parts use that choice.  Asynchronous on the stream. */
 int wilson_dd_hop(wilson_spinor* out, const wilson_gauge* g, const wilson_spinor* in, const void* recv_next,
-                  const void* recv_prev, int dagger, int t_first, int t_last, void* stream);
+                  const void* recv_prev, int dagger, int t_first, int t_last, int part, void* stream);
 
 /* ---------------------------------------------------------------------- */
 /* No-allocation variant (the paper has no counterpart; this is a service  */

@@ -22,6 +22,7 @@ WILSON_F64, WILSON_F32, WILSON_F16, WILSON_BF16 = range(4)
 WILSON_OP_HOP, WILSON_OP_M, WILSON_OP_SCHUR, WILSON_OP_SCHUR_DAG = range(4)
 WILSON_EVEN, WILSON_ODD, WILSON_FULL = range(3)
 WILSON_PROBE_FMA_F64, WILSON_PROBE_FMA_F32, WILSON_PROBE_FMA_F32X2 = range(3)
+WILSON_DD_ALL, WILSON_DD_INTERIOR, WILSON_DD_FACES = range(3)
 PREC = {"f64": WILSON_F64, "f32": WILSON_F32, "f16": WILSON_F16, "bf16": WILSON_BF16}
 
 
@@ -88,7 +89,7 @@ def _declare(lib):
         "wilson_probe_fma_peak": (I, [I, P(D), VP]),
         "wilson_dd_halo_bytes": (ctypes.c_longlong, [P(wilson_lattice), I]),
         "wilson_dd_pack": (I, [VP, VP, VP, VP, I, VP]),
-        "wilson_dd_hop": (I, [VP, VP, VP, VP, VP, I, I, I, VP]),
+        "wilson_dd_hop": (I, [VP, VP, VP, VP, VP, I, I, I, I, VP]),
         "wilson_last_error": (ctypes.c_char_p, []),
         "wilson_version": (I, []),
     }
@@ -292,9 +293,9 @@ def wilson_dd_pack(send_prev, send_next, gauge: "Gauge", inp: "Spinor", dagger: 
 
 
 def wilson_dd_hop(out: "Spinor", gauge: "Gauge", inp: "Spinor", recv_next, recv_prev, dagger: int = 0,
-                  t_first: int = 1, t_last: int = 1, stream=None):
+                  t_first: int = 1, t_last: int = 1, part: int = 0, stream=None):
     _check(lib().wilson_dd_hop(out.h, gauge.h, inp.h, _ptr(recv_next), _ptr(recv_prev), int(dagger),
-                               int(t_first), int(t_last), _stream(stream)))
+                               int(t_first), int(t_last), int(part), _stream(stream)))
 
 
 def wilson_probe_fma_peak(kind: int, stream=None) -> float:

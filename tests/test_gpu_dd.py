@@ -25,7 +25,9 @@ def w():
     return wilson
 
 
-def dd_apply(w, U, src, dims, n, prec, recon, out_parity, dagger, phases):
+def dd_apply(w, U, src, dims, n, prec, recon, out_parity, dagger, phases, split=False):
+    """split: the interior t-slices are applied before the exchange (with no
+    face buffers), the two face slices after it."""
     import torch
     sp = TSplit(dims, n)
     L = w.lattice(sp.local_dims, phases)
@@ -41,9 +43,14 @@ def dd_apply(w, U, src, dims, n, prec, recon, out_parity, dagger, phases):
     send_prev, send_next, recv_next, recv_prev = buf(), buf(), buf(), buf()
     for r in range(n):
         w.wilson_dd_pack(send_prev[r], send_next[r], gauges[r], ins[r], dagger)
+    if split:
+        for r in range(n):
+            w.wilson_dd_hop(outs[r], gauges[r], ins[r], None, None, dagger, sp.first(r), sp.last(r),
+                            w.WILSON_DD_INTERIOR)
     exchange_loopback(sp, send_prev, send_next, recv_next, recv_prev)
     for r in range(n):
-        w.wilson_dd_hop(outs[r], gauges[r], ins[r], recv_next[r], recv_prev[r], dagger, sp.first(r), sp.last(r))
+        w.wilson_dd_hop(outs[r], gauges[r], ins[r], recv_next[r], recv_prev[r], dagger, sp.first(r), sp.last(r),
+                        w.WILSON_DD_FACES if split else w.WILSON_DD_ALL)
     parts = []
     for o in outs:
         t = torch.full((sp.Lr * sp.Vs // 2, 4, 3), float("nan"), dtype=torch.complex128, device="cuda")
@@ -78,6 +85,20 @@ def test_dd_hop_dagger(w, oracle_mod, n, prec):
     assert_parity(got, want, TOL[prec])
 
 
+@pytest.mark.parametrize("n", [1, 2, 4])
+@pytest.mark.parametrize("prec,recon", [("f64", 18), ("f32", 12)])
+def test_dd_interior_then_faces(w, oracle_mod, n, prec, recon):
+    """The interior t-slices (no face buffers) before the exchange and the
+    face slices after it give the whole operator; with Lr = 2 (n = 4) the
+    interior is empty."""
+    dims = (4, 6, 4, 8)
+    U = inputs.gauge_field(dims, "random", seed=406)
+    src = inputs.gaussian_spinor(inputs.volume(dims) // 2, seed=407)
+    for out_parity in (0, 1):
+        got = dd_apply(w, U, src, dims, n, prec, recon, out_parity, 0, PHASES, split=True)
+        assert_parity(got, oracle_mod.dslash_eo(U, src, dims, out_parity, PHASES), TOL[prec])
+
+
 def test_dd_halo_bytes_and_argument_checks(w):
     import torch
     L = w.lattice((4, 4, 4, 4))
@@ -95,5 +116,11 @@ def test_dd_halo_bytes_and_argument_checks(w):
         w.wilson_dd_hop(b, g, a, buf, buf2)
     with pytest.raises(w.WilsonError):  # one buffer for both faces
         w.wilson_dd_pack(buf, buf, g, a)
+    c = w.Spinor(L, 1, w.WILSON_F32)
+    with pytest.raises(w.WilsonError):  # the faces need their buffers
+        w.wilson_dd_hop(c, g, a, None, None, 0, 1, 1, w.WILSON_DD_FACES)
+    with pytest.raises(w.WilsonError):  # unknown part
+        w.wilson_dd_hop(c, g, a, buf, buf2, 0, 1, 1, 3)
+    c.close()
     for h in (g, a, b):
         h.close()
