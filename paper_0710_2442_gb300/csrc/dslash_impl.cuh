@@ -298,6 +298,44 @@ __device__ __forceinline__ void project_p(const PSpinor& q, PHalf& h) {
     }
 }
 
+// (1 - S g_mu) psi of one stored F16 site, projected on packed halves and
+// converted to the paired-FP32 half spinor (same equations as project_p).
+template <int MU, int S>
+__device__ __forceinline__ void project_f16_packed(const uint4 (&d)[3], PHalf& h) {
+    // +-1 as F16 bit patterns: 0x3C00 = 1.0, 0xBC00 = -1.0
+    constexpr uint32_t P1 = 0x3C00u, M1 = 0xBC00u;
+    constexpr uint32_t sp = S > 0 ? P1 : M1;   // +S
+    constexpr uint32_t sm = S > 0 ? M1 : P1;   // -S
+    auto c2 = [](uint32_t lo, uint32_t hi) {
+        const uint32_t u = lo | (hi << 16);
+        return *reinterpret_cast<const __half2*>(&u);
+    };
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+        const uint32_t ux = d[c].x, uy = d[c].y, uz = d[c].z, uw = d[c].w;
+        const __half2 x = *reinterpret_cast<const __half2*>(&ux);
+        const __half2 y = *reinterpret_cast<const __half2*>(&uy);
+        const __half2 z = *reinterpret_cast<const __half2*>(&uz);
+        const __half2 w = *reinterpret_cast<const __half2*>(&uw);
+        __half2 r, i;
+        if (MU == 0) {  // h0 = p0 - S i p3, h1 = p1 - S i p2
+            r = __hfma2(c2(sp, sp), __lowhigh2highlow(w), x);
+            i = __hfma2(c2(sm, sm), __lowhigh2highlow(z), y);
+        } else if (MU == 1) {  // h0 = p0 + S p3, h1 = p1 - S p2
+            r = __hfma2(c2(sp, sm), __lowhigh2highlow(z), x);
+            i = __hfma2(c2(sp, sm), __lowhigh2highlow(w), y);
+        } else if (MU == 2) {  // h0 = p0 - S i p2, h1 = p1 + S i p3
+            r = __hfma2(c2(sp, sm), w, x);
+            i = __hfma2(c2(sm, sp), z, y);
+        } else {  // h0 = p0 - S p2, h1 = p1 - S p3
+            r = __hfma2(c2(sm, sm), z, x);
+            i = __hfma2(c2(sm, sm), w, y);
+        }
+        h.re[c] = __half22float2(r);
+        h.im[c] = __half22float2(i);
+    }
+}
+
 // w = U h (ADJ = false) or U^dag h (ADJ = true), both half-spin rows at once.
 template <bool ADJ>
 __device__ __forceinline__ void su3_mul_p(const cpx<float> U[3][3], const PHalf& h, PHalf& w) {
@@ -498,7 +536,27 @@ __device__ __forceinline__ void apply_phase_p(PHalf& hh, float er, float ei) {
     }
 }
 
-template <int SP, int GP, int R, bool DAG, int MU, bool FIRST, int NB>
+// The neighbour's projected half spinor and storage scale: loaded and
+// projected in FP32 (HP = false), or (F16, HP = true) projected on the stored
+// packed halves and then converted (project_f16_packed).
+template <int SP, int MU, int S, bool HP>
+__device__ __forceinline__ void load_project(const char* in, int stride, int hn, PHalf& hh, float& sc) {
+    using SF = SpinorFmt<SP>;
+    if constexpr (HP) {
+        uint4 d[3];
+        const uint4* b = reinterpret_cast<const uint4*>(in) + hn;
+#pragma unroll
+        for (int cc = 0; cc < 3; cc++) d[cc] = __ldg(b + (size_t)cc * stride);
+        sc = SF::load_scale(in, stride, hn);
+        project_f16_packed<MU, S>(d, hh);
+    } else {
+        PSpinor q;
+        SF::load_packed(in, stride, hn, q, sc);
+        project_p<MU, S>(q, hh);
+    }
+}
+
+template <int SP, int GP, int R, bool DAG, int MU, bool FIRST, int NB, bool HP = false>
 __device__ __forceinline__ void hop_dir_pm(PSpinor (&acc)[NB], const HopParams& P, const char* in, int p, int h,
                                            const int c[4], int s) {
     using SF = SpinorFmt<SP>;
@@ -514,11 +572,9 @@ __device__ __forceinline__ void hop_dir_pm(PSpinor (&acc)[NB], const HopParams& 
         GF::load(P.gauge, g.stride, p * 4 + MU, h, U);
 #pragma unroll
         for (int r = 0; r < NB; r++) {
-            PSpinor q;
             PHalf hh, w;
             float sc;
-            SF::load_packed(in + r * P.in_rstep, g.stride, hn, q, sc);
-            project_p<MU, SF_>(q, hh);
+            load_project<SP, MU, SF_, HP>(in + r * P.in_rstep, g.stride, hn, hh, sc);
             if (wrap) apply_phase_p(hh, (float)g.ph[MU][0], (float)g.ph[MU][1]);
             su3_mul_p<false>(U, hh, w);
             expand_p<MU, SF_, FIRST>(acc[r], w, sc);
@@ -531,11 +587,9 @@ __device__ __forceinline__ void hop_dir_pm(PSpinor (&acc)[NB], const HopParams& 
         GF::load(P.gauge, g.stride, (1 - p) * 4 + MU, hn, U);
 #pragma unroll
         for (int r = 0; r < NB; r++) {
-            PSpinor q;
             PHalf hh, w;
             float sc;
-            SF::load_packed(in + r * P.in_rstep, g.stride, hn, q, sc);
-            project_p<MU, -SF_>(q, hh);
+            load_project<SP, MU, -SF_, HP>(in + r * P.in_rstep, g.stride, hn, hh, sc);
             if (wrap) apply_phase_p(hh, (float)g.ph[MU][0], -(float)g.ph[MU][1]);
             su3_mul_p<true>(U, hh, w);
             expand_p<MU, -SF_, false>(acc[r], w, sc);
@@ -543,7 +597,7 @@ __device__ __forceinline__ void hop_dir_pm(PSpinor (&acc)[NB], const HopParams& 
     }
 }
 
-template <int SP, int GP, int R, bool DAG, int MINB, int NB>
+template <int SP, int GP, int R, bool DAG, int MINB, int NB, bool HP = false>
 __global__ void __launch_bounds__(256, MINB) hop_kernel_pm(const HopParams P) {
     using SF = SpinorFmt<SP>;
     const int ng = P.nrhs / NB;
@@ -573,10 +627,10 @@ __global__ void __launch_bounds__(256, MINB) hop_kernel_pm(const HopParams P) {
         int c[4], s;
         site_of_half(h, p, g, c, s);
         PSpinor acc[NB];
-        hop_dir_pm<SP, GP, R, DAG, 0, true, NB>(acc, P, in, p, h, c, s);
-        hop_dir_pm<SP, GP, R, DAG, 1, false, NB>(acc, P, in, p, h, c, s);
-        hop_dir_pm<SP, GP, R, DAG, 2, false, NB>(acc, P, in, p, h, c, s);
-        hop_dir_pm<SP, GP, R, DAG, 3, false, NB>(acc, P, in, p, h, c, s);
+        hop_dir_pm<SP, GP, R, DAG, 0, true, NB, HP>(acc, P, in, p, h, c, s);
+        hop_dir_pm<SP, GP, R, DAG, 1, false, NB, HP>(acc, P, in, p, h, c, s);
+        hop_dir_pm<SP, GP, R, DAG, 2, false, NB, HP>(acc, P, in, p, h, c, s);
+        hop_dir_pm<SP, GP, R, DAG, 3, false, NB, HP>(acc, P, in, p, h, c, s);
 #pragma unroll
         for (int r = 0; r < NB; r++) {
             PSpinor& A = acc[r];
@@ -757,32 +811,39 @@ __global__ void __launch_bounds__(256, MINB) hop_kernel_rl(const HopParams P) {
 // registers, 13: SPT 2 at 255, 14: SPT 4 at 255; at 85 registers two sites
 // spill about 1 KB) and, F16 only, the packed-half projection with one site
 // per thread (15, 16, 17: 128, 85, 64 registers).
-constexpr int kHopVariants = 18;
+// v = 18, 19: the register-blocked kernel (NB = 2) with the F16 packed
+// projection at 128 and 255 registers (at 85 it spills 1.2 KB).
+constexpr int kHopVariants = 20;
 constexpr int kHopBaseVariants = 6;
 constexpr int kHopStagedVariant = 10;  // hop_kernel_rl (128 registers)
 constexpr int kHopMmaVariant = 11;     // hop_kernel_mma (128 registers)
 constexpr int kHopSptVariant = 12;     // first hop_kernel_ps variant
+constexpr int kHopSptLast = 17;      // last hop_kernel_ps variant
+constexpr bool hop_variant_is_ps(int v) { return v >= kHopSptVariant && v <= kHopSptLast; }
 constexpr int hop_variant_nb(int v) {
-    return v < kHopBaseVariants || v >= kHopStagedVariant ? 1 : v == 6 || v == 7 ? 2 : v == 8 ? 3 : 4;
+    return v == 18 || v == 19 ? 2
+           : v < kHopBaseVariants || v >= kHopStagedVariant ? 1 : v == 6 || v == 7 ? 2 : v == 8 ? 3 : 4;
 }
 constexpr int hop_variant_spt(int v) { return v == 12 || v == 13 ? 2 : v == 14 ? 4 : 1; }
-constexpr bool hop_variant_hproj(int v) { return v >= 15 && v <= 17; }
+constexpr bool hop_variant_hproj(int v) { return (v >= 15 && v <= 17) || v == 18 || v == 19; }
 // FP64 operands take two registers per real: their budgets start at 255
 // registers.
 constexpr bool wide_regs(int sp) { return sp == P_F64; }
 constexpr bool float_storage(int sp) { return sp == P_F32 || sp == P_F16 || sp == P_BF16; }
 constexpr int hop_variant_minb(int v, int sp) {
     return v < kHopBaseVariants ? (wide_regs(sp) ? 1 : 2) + v % 3
-           : v == 13 || v == 14 ? 1
+           : v == 13 || v == 14 || v == 19 ? 1
            : v == 16 ? 3
            : v == 17 ? 4
+           : v == 18 ? 2
            : v >= kHopStagedVariant ? 2
            : v == 7 ? 2 : 1;
 }
 inline bool hop_variant_valid(int v, Prec sp, int recon, int nrhs) {
     if (v < 0 || v >= kHopVariants) return false;
     if (v < kHopBaseVariants) return true;
-    if (v >= kHopSptVariant && v < kHopVariants) return hop_variant_hproj(v) ? sp == P_F16 : float_storage(sp);
+    if (hop_variant_is_ps(v)) return hop_variant_hproj(v) ? sp == P_F16 : float_storage(sp);
+    if (v == 18 || v == 19) return sp == P_F16 && recon == 12 && nrhs >= 2 && nrhs % 2 == 0;
     if (v == kHopMmaVariant) return (sp == P_F16 || sp == P_BF16) && recon == 12 && nrhs > 1;
     if (v >= kHopStagedVariant) return float_storage(sp) && recon == 12 && nrhs > 1;
     const int nb = hop_variant_nb(v);
@@ -823,9 +884,10 @@ void launch_hop_rl_v(const HopParams& P, int block, int site_blocks, int ny, boo
 template <int SP, int GP, int R, int V>
 void launch_hop_mrhs_v(const HopParams& P, int block, int site_blocks, int ny, bool dag, cudaStream_t st) {
     constexpr int NB = hop_variant_nb(V), MINB = hop_variant_minb(V, SP);
+    constexpr bool HP = hop_variant_hproj(V) && SP == P_F16;
     const dim3 grid(site_blocks * (P.nrhs / NB), ny);
-    if (dag) launch_dep(hop_kernel_pm<SP, GP, R, true, MINB, NB>, grid, dim3(block), st, P);
-    else launch_dep(hop_kernel_pm<SP, GP, R, false, MINB, NB>, grid, dim3(block), st, P);
+    if (dag) launch_dep(hop_kernel_pm<SP, GP, R, true, MINB, NB, HP>, grid, dim3(block), st, P);
+    else launch_dep(hop_kernel_pm<SP, GP, R, false, MINB, NB, HP>, grid, dim3(block), st, P);
 }
 
 template <int SP, int GP, int R, int V>
@@ -845,7 +907,7 @@ void launch_hop_v(const HopParams& P, dim3 grid, int block, bool dag, cudaStream
 template <int SP, int GP, int R>
 void launch_hop_prec(const HopParams& P, int block, int site_blocks, int ny, bool dag, int variant,
                      cudaStream_t st) {
-    if (variant >= kHopSptVariant) {
+    if (hop_variant_is_ps(variant)) {
         if constexpr (float_storage(SP)) {
             launch_hop_ps<SP, GP, R>(P, block, site_blocks, ny, dag, variant, st);
             return;

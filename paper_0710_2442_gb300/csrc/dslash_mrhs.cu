@@ -14,6 +14,14 @@ void launch_hop_mrhs(const HopParams& P, int block, int site_blocks, int ny, boo
         case 8: launch_hop_mrhs_v<SP, GP, R, 8>(P, block, site_blocks, ny, dag, st); break;
         case 9: launch_hop_mrhs_v<SP, GP, R, 9>(P, block, site_blocks, ny, dag, st); break;
         case 10: launch_hop_rl_v<SP, GP, R, 10>(P, block, site_blocks, ny, dag, st); break;
+        case 18:
+        case 19:
+            if constexpr (SP == P_F16) {
+                if (variant == 18) launch_hop_mrhs_v<SP, GP, R, 18>(P, block, site_blocks, ny, dag, st);
+                else launch_hop_mrhs_v<SP, GP, R, 19>(P, block, site_blocks, ny, dag, st);
+                break;
+            }
+            throw Error(7, "the packed-projection multi-RHS variants need F16 spinors");
         case kHopMmaVariant:
             if constexpr ((SP == P_F16 || SP == P_BF16) && GP == SP && R == 12) {
                 launch_hop_mma<SP>(P, block, site_blocks, ny, dag, st);

@@ -29,44 +29,6 @@ namespace wl {
 
 namespace {
 
-// (1 - S g_mu) psi of one stored F16 site, projected on packed halves and
-// converted to the paired-FP32 half spinor (same equations as project_p).
-template <int MU, int S>
-__device__ __forceinline__ void project_f16_packed(const uint4 (&d)[3], PHalf& h) {
-    // +-1 as F16 bit patterns: 0x3C00 = 1.0, 0xBC00 = -1.0
-    constexpr uint32_t P1 = 0x3C00u, M1 = 0xBC00u;
-    constexpr uint32_t sp = S > 0 ? P1 : M1;   // +S
-    constexpr uint32_t sm = S > 0 ? M1 : P1;   // -S
-    auto c2 = [](uint32_t lo, uint32_t hi) {
-        const uint32_t u = lo | (hi << 16);
-        return *reinterpret_cast<const __half2*>(&u);
-    };
-#pragma unroll
-    for (int c = 0; c < 3; c++) {
-        const uint32_t ux = d[c].x, uy = d[c].y, uz = d[c].z, uw = d[c].w;
-        const __half2 x = *reinterpret_cast<const __half2*>(&ux);
-        const __half2 y = *reinterpret_cast<const __half2*>(&uy);
-        const __half2 z = *reinterpret_cast<const __half2*>(&uz);
-        const __half2 w = *reinterpret_cast<const __half2*>(&uw);
-        __half2 r, i;
-        if (MU == 0) {  // h0 = p0 - S i p3, h1 = p1 - S i p2
-            r = __hfma2(c2(sp, sp), __lowhigh2highlow(w), x);
-            i = __hfma2(c2(sm, sm), __lowhigh2highlow(z), y);
-        } else if (MU == 1) {  // h0 = p0 + S p3, h1 = p1 - S p2
-            r = __hfma2(c2(sp, sm), __lowhigh2highlow(z), x);
-            i = __hfma2(c2(sp, sm), __lowhigh2highlow(w), y);
-        } else if (MU == 2) {  // h0 = p0 - S i p2, h1 = p1 + S i p3
-            r = __hfma2(c2(sp, sm), w, x);
-            i = __hfma2(c2(sm, sp), z, y);
-        } else {  // h0 = p0 - S p2, h1 = p1 - S p3
-            r = __hfma2(c2(sm, sm), z, x);
-            i = __hfma2(c2(sm, sm), w, y);
-        }
-        h.re[c] = __half22float2(r);
-        h.im[c] = __half22float2(i);
-    }
-}
-
 // One direction mu of the stencil with the F16 packed projection; otherwise
 // the arithmetic of hop_dir_p.
 template <int GP, int R, bool DAG, int MU, bool FIRST>

@@ -255,10 +255,11 @@ def test_variant_solver(w, oracle_mod, monkeypatch, variant):
 
 
 # The register-blocked multi-RHS variants (NB = 2, 2, 3, 4 right-hand sides
-# per thread) and the link-staged one (10: links in shared memory, a loop over
-# the right-hand sides), pinned through WILSON_HOP_VARIANT, on 12 right-hand
+# per thread; 18, 19: NB = 2 with the F16 packed projection), the link-staged
+# one (10: links in shared memory, a loop over the right-hand sides), pinned
+# through WILSON_HOP_VARIANT, on 12 right-hand
 # sides (a multiple of every NB) over a lattice with a ragged last block.
-@pytest.mark.parametrize("variant", [6, 7, 8, 9, 10])
+@pytest.mark.parametrize("variant", [6, 7, 8, 9, 10, 18, 19])
 @pytest.mark.parametrize("prec", ["f32", "f16", "bf16"])
 def test_blocked_multi_rhs_variants(w, oracle_mod, monkeypatch, variant, prec):
     monkeypatch.setenv("WILSON_HOP_VARIANT", str(variant))
@@ -314,7 +315,7 @@ def test_tensor_core_multi_rhs_variant(w, oracle_mod, monkeypatch, nrhs, prec, b
         assert_parity(got[k], oracle_mod.wilson_m(U, psi[k], dims, 0.1350, CPLX_PHASES), TOL[prec], f"rhs {k}")
 
 
-@pytest.mark.parametrize("variant", [6, 8, 9, 10, 11])
+@pytest.mark.parametrize("variant", [6, 8, 9, 10, 11, 18])
 def test_blocked_variant_lockstep_solve(w, oracle_mod, monkeypatch, variant):
     """The lockstep multi-RHS solve on a blocked kernel: right-hand sides that
     finish early (a zero source at once) are skipped inside their group while
