@@ -46,7 +46,7 @@
  *   WILSON_TUNE=0                 no autotuning: default launch configurations
  *   WILSON_TUNE_CACHE=path        load tuning decisions from path, append new ones
  *   WILSON_TUNE_VERBOSE=1         report tuning candidates and decisions on stderr
- *   WILSON_HOP_VARIANT=v          pin the hop kernel variant (0..19) of every launch;
+ *   WILSON_HOP_VARIANT=v          pin the hop kernel variant (0..22) of every launch;
  *                                 a variant that does not fit a launch runs variant 3
  *   WILSON_HOP_BLOCK=n            block size with WILSON_HOP_VARIANT (64, 128, 256)
  *   WILSON_PDL=0                  hops without programmatic dependent launch (read

@@ -105,8 +105,8 @@ void launch_hop(const HopLaunch& L, cudaStream_t st) {
             if (!wide_regs(sp) || c.variant < 3) cands.push_back(c);
         // two sites per thread, and the F16 packed projection
         for (int block : {64, 128, 256})
-            for (int v = kHopSptVariant; v <= kHopSptLast; v++)
-                if (hop_variant_valid(v, sp, R, P.nrhs)) cands.push_back(LaunchConfig{block, v});
+            for (int v = kHopSptVariant; v < kHopVariants; v++)
+                if (hop_variant_is_ps(v) && hop_variant_valid(v, sp, R, P.nrhs)) cands.push_back(LaunchConfig{block, v});
         if (P.nrhs > 1)
             for (int block : {64, 128, 256})
                 for (int v = kHopBaseVariants; v < kHopVariants; v++)

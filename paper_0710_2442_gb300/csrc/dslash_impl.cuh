@@ -34,6 +34,8 @@
 //                        warp per site and 16 right-hand sides (dslash_mma.cu)
 //   hop_kernel_ps  12-17 the paired stencil with 2 or 4 sites per thread, and
 //                        for F16 the projection on packed halves (dslash_spt.cu)
+//   hop_kernel_pm  18-19 the register-blocked form with the F16 packed projection
+//   hop_kernel_f16pipe 20-22 F16 with the neighbour data copied ahead (dslash_spt.cu)
 // Multi-RHS launches of the first two run the right-hand sides of a site
 // tile as consecutive blocks.  Every kernel starts with the programmatic-
 // dependent-launch wait, so it can be launched with that attribute.
@@ -813,13 +815,16 @@ __global__ void __launch_bounds__(256, MINB) hop_kernel_rl(const HopParams P) {
 // per thread (15, 16, 17: 128, 85, 64 registers).
 // v = 18, 19: the register-blocked kernel (NB = 2) with the F16 packed
 // projection at 128 and 255 registers (at 85 it spills 1.2 KB).
-constexpr int kHopVariants = 20;
+// v = 20-22: the F16 kernel with its neighbour data copied ahead into shared
+// memory (cp.async), 2 / 3 / 3 hops ahead at 85 / 85 / 64 registers.
+constexpr int kHopVariants = 23;
 constexpr int kHopBaseVariants = 6;
 constexpr int kHopStagedVariant = 10;  // hop_kernel_rl (128 registers)
 constexpr int kHopMmaVariant = 11;     // hop_kernel_mma (128 registers)
 constexpr int kHopSptVariant = 12;     // first hop_kernel_ps variant
 constexpr int kHopSptLast = 17;      // last hop_kernel_ps variant
-constexpr bool hop_variant_is_ps(int v) { return v >= kHopSptVariant && v <= kHopSptLast; }
+constexpr bool hop_variant_is_pipe(int v) { return v >= 20 && v <= 22; }
+constexpr bool hop_variant_is_ps(int v) { return (v >= kHopSptVariant && v <= kHopSptLast) || hop_variant_is_pipe(v); }
 constexpr int hop_variant_nb(int v) {
     return v == 18 || v == 19 ? 2
            : v < kHopBaseVariants || v >= kHopStagedVariant ? 1 : v == 6 || v == 7 ? 2 : v == 8 ? 3 : 4;
@@ -833,8 +838,8 @@ constexpr bool float_storage(int sp) { return sp == P_F32 || sp == P_F16 || sp =
 constexpr int hop_variant_minb(int v, int sp) {
     return v < kHopBaseVariants ? (wide_regs(sp) ? 1 : 2) + v % 3
            : v == 13 || v == 14 || v == 19 ? 1
-           : v == 16 ? 3
-           : v == 17 ? 4
+           : v == 16 || v == 20 || v == 21 ? 3
+           : v == 17 || v == 22 ? 4
            : v == 18 ? 2
            : v >= kHopStagedVariant ? 2
            : v == 7 ? 2 : 1;
@@ -842,6 +847,7 @@ constexpr int hop_variant_minb(int v, int sp) {
 inline bool hop_variant_valid(int v, Prec sp, int recon, int nrhs) {
     if (v < 0 || v >= kHopVariants) return false;
     if (v < kHopBaseVariants) return true;
+    if (hop_variant_is_pipe(v)) return sp == P_F16 && recon == 12;
     if (hop_variant_is_ps(v)) return hop_variant_hproj(v) ? sp == P_F16 : float_storage(sp);
     if (v == 18 || v == 19) return sp == P_F16 && recon == 12 && nrhs >= 2 && nrhs % 2 == 0;
     if (v == kHopMmaVariant) return (sp == P_F16 || sp == P_BF16) && recon == 12 && nrhs > 1;

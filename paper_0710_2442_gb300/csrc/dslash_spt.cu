@@ -23,6 +23,8 @@
 //
 // Variants: 12 = SPT 2 at 128 registers, 13 = SPT 2 at 255, 14 = SPT 4 at
 // 255; 15, 16, 17 = the F16 projection at 128, 85 and 64 registers.
+#include <cuda_pipeline.h>
+
 #include "dslash_impl.cuh"
 
 namespace wl {
@@ -157,6 +159,167 @@ __global__ void __launch_bounds__(256, MINB) hop_kernel_ps(const HopParams P) {
     if (P.reduce) grid_reduce(nrm, P.red, k, nb * gridDim.y, sb + nb * blockIdx.y);
 }
 
+// ---------------------------------------------------------------------------
+// F16 hop with the neighbour data copied ahead into shared memory (variants
+// 20-22).  The F16 hop's exact loads alone run at 0.93 of the copy bandwidth,
+// the kernel itself at 0.6: its arithmetic waits on loads it cannot keep in
+// flight at the occupancy its registers allow.  Here each thread issues the
+// raw data of a hop (3 spinor chunks, the scale, 3 link chunks) with
+// asynchronous copies (cp.async) into its own shared-memory slots, D hops
+// ahead, so the loads in flight hold no registers.  Before computing hop j
+// the thread waits for that hop's copy group (a hardware wait, no spin);
+// after computing it, it reuses the slot for hop j + D.  Slots are laid out
+// [slot][chunk][thread] (conflict-free warp accesses); a thread reads only
+// what it copied, so no barrier is needed.  The arithmetic is that of the
+// packed-projection kernel.  A thread past the lattice's end runs site 0 and
+// stores nothing, so the pipeline never diverges.
+// ---------------------------------------------------------------------------
+template <bool DAG, int J>
+__device__ __forceinline__ void f16pipe_hop(PSpinor& acc, const uint4 (&d)[3], float sc, const cpx<float> (&U)[3][3],
+                                            unsigned wrap, const Geom& g) {
+    constexpr int MU = J >> 1;
+    constexpr bool FWD = (J & 1) == 0;
+    constexpr int SF_ = DAG ? -1 : 1;
+    constexpr int S = FWD ? SF_ : -SF_;
+    PHalf hh, w;
+    project_f16_packed<MU, S>(d, hh);
+    if (wrap >> J & 1u) apply_phase_p(hh, (float)g.ph[MU][0], FWD ? (float)g.ph[MU][1] : -(float)g.ph[MU][1]);
+    su3_mul_p<!FWD>(U, hh, w);
+    expand_p<MU, S, J == 0>(acc, w, sc);
+}
+
+template <bool DAG, int MINB, int D>
+__global__ void __launch_bounds__(256, MINB) hop_kernel_f16pipe(const HopParams P) {
+    using SF = SpinorFmt<P_F16>;
+    using GF = GaugeFmt<P_F16, 12>;
+    extern __shared__ __align__(16) unsigned char pipe_smem[];
+    const int T = blockDim.x, t = threadIdx.x;
+    uint4* sp = reinterpret_cast<uint4*>(pipe_smem);     // [D][3][T] spinor chunks
+    uint2* lk = reinterpret_cast<uint2*>(sp + D * 3 * T);  // [D][3][T] link chunks
+    float* scs = reinterpret_cast<float*>(lk + D * 3 * T); // [D][T] scales
+    const int k = blockIdx.x % P.nrhs;
+    const int sb = blockIdx.x / P.nrhs;
+    const int nb = gridDim.x / P.nrhs;
+    const int p = P.full ? (int)blockIdx.y : P.out_parity;
+    pdl_trigger();
+    pdl_wait();
+    if (P.skip && __ldcg(P.skip + (size_t)k * P.skip_stride)) return;
+    const int pin = 1 - p;
+    char* out = P.out + (P.full ? p * P.out_pstep : 0) + k * P.out_rstep;
+    const char* in = P.in + (P.full ? pin * P.in_pstep : 0) + k * P.in_rstep;
+    const char* x = P.x ? P.x + (P.full ? p * P.x_pstep : 0) + k * P.x_rstep : nullptr;
+    const Geom& g = P.g;
+    const float a = (float)P.a;
+    const float* gscale = reinterpret_cast<const float*>(in + 48LL * g.stride);
+    double nrm = 0.0;
+    for (int h0 = sb * T + t; h0 - t < g.Vh; h0 += nb * T) {
+        const bool ok = h0 < g.Vh;
+        const int h = ok ? h0 : 0;
+        int hn[8];
+        unsigned wrap = 0;
+        {
+            int c[4], s;
+            site_of_half(h, p, g, c, s);
+#pragma unroll
+            for (int mu = 0; mu < 4; mu++) {
+                const int L = g.L[mu];
+                const int smu = mu == 0 ? 1 : mu == 1 ? g.L[0] : mu == 2 ? g.L[0] * g.L[1] : g.L[0] * g.L[1] * g.L[2];
+                const bool wf = c[mu] == L - 1, wb = c[mu] == 0;
+                hn[2 * mu] = (wf ? s - (L - 1) * smu : s + smu) >> 1;
+                hn[2 * mu + 1] = (wb ? s + (L - 1) * smu : s - smu) >> 1;
+                wrap |= (unsigned)wf << (2 * mu) | (unsigned)wb << (2 * mu + 1);
+            }
+        }
+        // hop j's raw data into slot j % D: the neighbour's chunks and scale,
+        // the link of the site (forward) or of the neighbour (backward)
+        auto issue = [&](int j) {
+            const int slot = j % D;
+            const int n = hn[j];
+            const uint4* gs = reinterpret_cast<const uint4*>(in) + n;
+#pragma unroll
+            for (int kk = 0; kk < 3; kk++) __pipeline_memcpy_async(&sp[(slot * 3 + kk) * T + t], gs + (size_t)kk * g.stride, 16);
+            __pipeline_memcpy_async(&scs[slot * T + t], gscale + n, 4);
+            const int blk = ((j & 1) ? pin : p) * 4 + (j >> 1);
+            const uint2* gl = reinterpret_cast<const uint2*>(P.gauge) + (size_t)blk * 3 * g.stride + ((j & 1) ? n : h);
+#pragma unroll
+            for (int kk = 0; kk < 3; kk++) __pipeline_memcpy_async(&lk[(slot * 3 + kk) * T + t], gl + (size_t)kk * g.stride, 8);
+            __pipeline_commit();
+        };
+#pragma unroll
+        for (int j = 0; j < D; j++) issue(j);
+        PSpinor acc;
+#define WL_PIPE_HOP(J)                                                                      \
+        {                                                                                   \
+            __pipeline_wait_prior(D - 1);                                                   \
+            constexpr int slot = (J) % D;                                                   \
+            uint4 d[3];                                                                     \
+            _Pragma("unroll") for (int kk = 0; kk < 3; kk++) d[kk] = sp[(slot * 3 + kk) * T + t]; \
+            const float sc = scs[slot * T + t];                                             \
+            cpx<float> U[3][3];                                                             \
+            GF::decode(&lk[slot * 3 * T + t], T, U);                                        \
+            f16pipe_hop<DAG, (J)>(acc, d, sc, U, wrap, g);                                  \
+            if ((J) + D < 8) issue((J) + D);                                                \
+            else __pipeline_commit();                                                       \
+        }
+        WL_PIPE_HOP(0) WL_PIPE_HOP(1) WL_PIPE_HOP(2) WL_PIPE_HOP(3)
+        WL_PIPE_HOP(4) WL_PIPE_HOP(5) WL_PIPE_HOP(6) WL_PIPE_HOP(7)
+#undef WL_PIPE_HOP
+        if (!ok) continue;
+        if (P.xpay) {
+            PSpinor xq;
+            float xs;
+            SF::load_packed(x, g.stride, h, xq, xs);
+            const float2 Af = bc2(a), X = bc2(xs);
+#pragma unroll
+            for (int cc = 0; cc < 3; cc++) {
+                acc.re01[cc] = fma2(Af, acc.re01[cc], mul2(X, xq.re01[cc]));
+                acc.im01[cc] = fma2(Af, acc.im01[cc], mul2(X, xq.im01[cc]));
+                acc.re23[cc] = fma2(Af, acc.re23[cc], mul2(X, xq.re23[cc]));
+                acc.im23[cc] = fma2(Af, acc.im23[cc], mul2(X, xq.im23[cc]));
+            }
+        } else if (P.a != 1.0) {
+            const float2 Af = bc2(a);
+#pragma unroll
+            for (int cc = 0; cc < 3; cc++) {
+                acc.re01[cc] = mul2(Af, acc.re01[cc]);
+                acc.im01[cc] = mul2(Af, acc.im01[cc]);
+                acc.re23[cc] = mul2(Af, acc.re23[cc]);
+                acc.im23[cc] = mul2(Af, acc.im23[cc]);
+            }
+        }
+        if (P.reduce) {
+            float2 n2 = make_float2(0.f, 0.f);
+#pragma unroll
+            for (int cc = 0; cc < 3; cc++) {
+                n2 = fma2(acc.re01[cc], acc.re01[cc], n2);
+                n2 = fma2(acc.im01[cc], acc.im01[cc], n2);
+                n2 = fma2(acc.re23[cc], acc.re23[cc], n2);
+                n2 = fma2(acc.im23[cc], acc.im23[cc], n2);
+            }
+            nrm += (double)n2.x + (double)n2.y;
+        }
+        if (P.nrhs > 1) SF::template store_packed<true>(out, g.stride, h, acc);
+        else SF::store_packed(out, g.stride, h, acc);
+    }
+    if (P.reduce) grid_reduce(nrm, P.red, k, nb * gridDim.y, sb + nb * blockIdx.y);
+}
+
+template <bool DAG, int V>
+void launch_f16pipe_v(const HopParams& P, int block, int site_blocks, int ny, cudaStream_t st) {
+    constexpr int MINB = hop_variant_minb(V, P_F16), D = V == 20 ? 2 : 3;
+    constexpr size_t per_thread = (size_t)D * (3 * 16 + 3 * 8 + 4);
+    auto k = hop_kernel_f16pipe<DAG, MINB, D>;
+    static bool opted[64] = {};  // the larger dynamic shared memory, once per device
+    int dev = 0;
+    WL_CUDA(cudaGetDevice(&dev));
+    WL_REQUIRE(dev >= 0 && dev < 64, "device ordinal out of range");
+    if (!opted[dev]) {
+        WL_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(per_thread * 256)));
+        opted[dev] = true;
+    }
+    launch_dep_smem(k, dim3(site_blocks * P.nrhs, ny), dim3(block), per_thread * block, st, P);
+}
+
 template <int SP, int GP, int R, bool DAG, int V>
 void launch_ps_v(const HopParams& P, int block, int site_blocks, int ny, cudaStream_t st) {
     constexpr int MINB = hop_variant_minb(V, SP), SPT = hop_variant_spt(V);
@@ -178,6 +341,16 @@ void launch_ps_dag(const HopParams& P, int block, int site_blocks, int ny, int v
         case 15: launch_ps_v<SP, GP, R, DAG, 15>(P, block, site_blocks, ny, st); break;
         case 16: launch_ps_v<SP, GP, R, DAG, 16>(P, block, site_blocks, ny, st); break;
         case 17: launch_ps_v<SP, GP, R, DAG, 17>(P, block, site_blocks, ny, st); break;
+        case 20:
+        case 21:
+        case 22:
+            if constexpr (SP == P_F16 && GP == P_F16 && R == 12) {
+                if (variant == 20) launch_f16pipe_v<DAG, 20>(P, block, site_blocks, ny, st);
+                else if (variant == 21) launch_f16pipe_v<DAG, 21>(P, block, site_blocks, ny, st);
+                else launch_f16pipe_v<DAG, 22>(P, block, site_blocks, ny, st);
+                break;
+            }
+            throw Error(7, "the pipelined hop variants need F16 spinors and 12-real links");
         default: throw Error(7, "unknown sites-per-thread hop variant");
     }
 }
