@@ -273,6 +273,9 @@ def run_ours(args, ws, rank, local, fields):
     e2e = {"value": round(flops * apps * e2e_steps * ws / t_e2e / 1e9, 2), "unit": "GFlop/s",
            "h2d_bytes_per_step": int(host_in.numel() * 16), "d2h_bytes_per_step": int(host_out.numel() * 16),
            "steps": e2e_steps, "api": f"wilson_spinor_import(host) + {apps} x wilson_dslash_h + wilson_spinor_export(host)"}
+    # the hop's memory-access pattern with the arithmetic taken out, outside every timed
+    # region (overwrites odd with a checksum)
+    access = access_record(comp_bytes, w.wilson_probe_hop_access(odd, g, even, 50, stream), t_launch, peak)
     del src_dev
     for h in (even, odd, g):
         h.close()
@@ -301,7 +304,8 @@ def run_ours(args, ws, rank, local, fields):
                             "launch_us": round(t_launch * 1e6, 2),
                             "hbm": {"achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                                     "frac": round(achieved / peak, 4)}}
-    line.update({"clocks": clocks, "e2e": e2e, "gpu_launches": launches, "alu_peaks": alu})
+    line.update({"clocks": clocks, "e2e": e2e, "gpu_launches": launches, "alu_peaks": alu,
+                 "access_pattern": access})
     if rank == 0 and not args.no_solver:
         blocks = {b.strip() for b in args.blocks.split(",")}
         if "cg" in blocks:
@@ -313,6 +317,21 @@ def run_ours(args, ws, rank, local, fields):
         if "batch" in blocks:
             line["batch"] = run_batch_block(w, torch, dev, stream)
     return line
+
+
+def access_record(comp_bytes, t_access, t_hop, hbm_peak):
+    """The paper's benchmark of Eq. 3's memory-access pattern (Sec. 5, after
+    Table 1: within 20 % of the model's T_mem on the Cell) on this GPU:
+    wilson_probe_hop_access makes the hop's DRAM accesses with trivial
+    arithmetic.  T_mem here is the compulsory bytes at the measured copy
+    bandwidth; hop_over_access is how much the arithmetic adds to the hop."""
+    t_mem = comp_bytes / (hbm_peak * 1e9)
+    return {"us": round(t_access * 1e6, 2), "frac": round(comp_bytes / t_access / 1e9 / hbm_peak, 4),
+            "t_mem_us": round(t_mem * 1e6, 2), "access_over_t_mem": round(t_access / t_mem, 3),
+            "hop_us": round(t_hop * 1e6, 2), "hop_over_access": round(t_hop / t_access, 3),
+            "how": "wilson_probe_hop_access: the hop's loads and stores, XOR/add of the loaded words, best "
+                   "of block sizes 64/128/256 x four register budgets, mean of back-to-back CUDA-event-timed "
+                   "launches"}
 
 
 def run_solver_block(w, torch, dev, stream, precs, hbm_peak):
@@ -400,6 +419,9 @@ def run_multirhs_block(w, torch, dev, stream, fields, nrhs=12):
                 "GBs_compulsory": round(byts / t / 1e9, 1), "bytes_per_site_rhs": round(bps / n, 1),
                 "frac": round(byts / t / 1e9 / hbm_peak, 4),
                 "TFlops": round(model.FLOPS_PER_SITE * Vh * n / t / 1e12, 3)}
+            if n == 1:  # the same accesses without the arithmetic (overwrites b)
+                out[f"{prefix}hop_nrhs1"]["access_pattern"] = access_record(
+                    byts, w.wilson_probe_hop_access(b, g, a, reps, stream), t, hbm_peak)
             a.close()
             b.close()
         g.close()

@@ -46,7 +46,7 @@
  *   WILSON_TUNE=0                 no autotuning: default launch configurations
  *   WILSON_TUNE_CACHE=path        load tuning decisions from path, append new ones
  *   WILSON_TUNE_VERBOSE=1         report tuning candidates and decisions on stderr
- *   WILSON_HOP_VARIANT=v          pin the hop kernel variant (0..22) of every launch;
+ *   WILSON_HOP_VARIANT=v          pin the hop kernel variant (0..25) of every launch;
  *                                 a variant that does not fit a launch runs variant 3
  *   WILSON_HOP_BLOCK=n            block size with WILSON_HOP_VARIANT (64, 128, 256)
  *   WILSON_PDL=0                  hops without programmatic dependent launch (read
@@ -388,6 +388,23 @@ typedef enum {
  * *gflops: 2 flops per FMA (per lane).  Allocates a small result buffer and
  * synchronises the stream.  WILSON_ERR_ARG for an unknown kind. */
 int wilson_probe_fma_peak(int kind, double* gflops, void* stream);
+
+/* The memory-access pattern of the even-odd hop with the arithmetic taken
+ * out (Sec. 5, after Table 1: the paper benchmarked the access pattern of
+ * Eq. 3 and compared its time with the model's memory time T_mem).  A kernel
+ * makes exactly the DRAM accesses of wilson_dslash_h(out, g, in, 0,
+ * WILSON_OP_HOP): for each site of out's parity p it reads the eight
+ * neighbours' spinors of in (parity 1 - p, periodic wrap) and the eight links,
+ * and writes the site's rows of out; each loaded word is folded into an
+ * integer checksum, which is stored in place of the spinor, so out's contents
+ * afterwards are NOT a spinor field.  One RHS; in and out of the gauge's
+ * lattice and precision, of opposite parities.  Times reps back-to-back
+ * launches at each block size of 64, 128 and 256 threads and each of four
+ * register budgets with CUDA events on the stream (after three warm-up
+ * launches) and returns the best mean time per launch in *seconds.  Synchronises the stream; allocates nothing.
+ * WILSON_ERR_ARG for mismatched handles or reps outside [1, 100000]. */
+int wilson_probe_hop_access(wilson_spinor* out, const wilson_gauge* g, const wilson_spinor* in, int reps,
+                            double* seconds, void* stream);
 
 /* ---------------------------------------------------------------------- */
 /* Errors and version                                                      */

@@ -541,4 +541,40 @@ struct GaugeFmt<P_F16, 18> : GaugeLow18<P_F16> {};
 template <>
 struct GaugeFmt<P_BF16, 18> : GaugeLow18<P_BF16> {};
 
+// L2 prefetches of one link or one spinor of a stored field: a request per
+// row of the site's SoA rows, which holds no register and waits for nothing.
+// The hop variants that issue them when a thread takes its site start the
+// streamed link loads of all eight hops at once (GB300 keeps more of the
+// link stream in flight this way than the per-hop loads, which wait for
+// registers).
+__device__ __forceinline__ void prefetch_l2(const void* p) { asm volatile("prefetch.global.L2 [%0];" ::"l"(p)); }
+template <int NR, int RB>
+__device__ __forceinline__ void prefetch_rows(const char* b, long long stride, int i) {
+#pragma unroll
+    for (int r = 0; r < NR; r++) prefetch_l2(b + (long long)r * RB * stride + (long long)i * RB);
+}
+// Link blk of site i in GaugeFmt<P, R>'s layout (blocks of nchunk rows; the
+// 18-real F16/BF16 format has rows of 16, 16 and 4 bytes).
+template <int P, int R>
+__device__ __forceinline__ void prefetch_link(const void* base, int stride, int blk, int i) {
+    using GF = GaugeFmt<P, R>;
+    const char* b = static_cast<const char*>(base);
+    if constexpr ((P == P_F16 || P == P_BF16) && R == 18) {
+        const char* lb = b + (long long)blk * 36 * stride;
+        prefetch_rows<2, 16>(lb, stride, i);
+        prefetch_l2(lb + 32LL * stride + (long long)i * 4);
+    } else {
+        prefetch_rows<GF::nchunk, GF::chunk_bytes>(b + (long long)blk * GF::nchunk * GF::chunk_bytes * stride,
+                                                   stride, i);
+    }
+}
+// Spinor i in SpinorFmt<P>'s layout (the scale row after the chunks).
+template <int P>
+__device__ __forceinline__ void prefetch_spinor(const void* base, int stride, int i) {
+    using SF = SpinorFmt<P>;
+    const char* b = static_cast<const char*>(base);
+    prefetch_rows<SF::nchunk, SF::chunk_bytes>(b, stride, i);
+    if constexpr (SF::scaled) prefetch_l2(b + (long long)SF::nchunk * SF::chunk_bytes * stride + (long long)i * 4);
+}
+
 }  // namespace wl

@@ -103,14 +103,16 @@ void launch_hop(const HopLaunch& L, cudaStream_t st) {
         std::vector<LaunchConfig> cands;
         for (const LaunchConfig& c : hop_candidates())  // FP64 has three register budgets, not six
             if (!wide_regs(sp) || c.variant < 3) cands.push_back(c);
-        // two sites per thread, and the F16 packed projection
+        // two sites per thread, the F16 packed projection and pipeline, and
+        // the prefetching variants
         for (int block : {64, 128, 256})
             for (int v = kHopSptVariant; v < kHopVariants; v++)
-                if (hop_variant_is_ps(v) && hop_variant_valid(v, sp, R, P.nrhs)) cands.push_back(LaunchConfig{block, v});
+                if ((hop_variant_is_ps(v) || hop_variant_is_pf(v)) && hop_variant_valid(v, sp, R, P.nrhs))
+                    cands.push_back(LaunchConfig{block, v});
         if (P.nrhs > 1)
             for (int block : {64, 128, 256})
                 for (int v = kHopBaseVariants; v < kHopVariants; v++)
-                    if (!hop_variant_is_ps(v) && hop_variant_valid(v, sp, R, P.nrhs))
+                    if (!hop_variant_is_ps(v) && !hop_variant_is_pf(v) && hop_variant_valid(v, sp, R, P.nrhs))
                         cands.push_back(LaunchConfig{block, v});
         if (L.no_tune)
             cfg = tune_lookup(key, cands, LaunchConfig{});

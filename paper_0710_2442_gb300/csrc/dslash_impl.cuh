@@ -36,6 +36,8 @@
 //                        for F16 the projection on packed halves (dslash_spt.cu)
 //   hop_kernel_pm  18-19 the register-blocked form with the F16 packed projection
 //   hop_kernel_f16pipe 20-22 F16 with the neighbour data copied ahead (dslash_spt.cu)
+//   hop_kernel / hop_kernel_p 23-25 with L2 prefetches of the site's links
+//                        (and neighbour spinors) when a thread takes its site
 // Multi-RHS launches of the first two run the right-hand sides of a site
 // tile as consecutive blocks.  Every kernel starts with the programmatic-
 // dependent-launch wait, so it can be launched with that attribute.
@@ -202,11 +204,39 @@ __device__ __forceinline__ void hop_dir(cpx<typename SpinorFmt<SP>::real> acc[12
     }
 }
 
+// The prefetching variants (PF = 1: the site's eight links; PF = 2: also its
+// eight neighbour spinors) issue L2 prefetches for all of them when a thread
+// takes its site, before the first hop.  On the F32 hop with 12-real links
+// (384 of 576 bytes per site are links, each read once) the link stream then
+// keeps up with the copy bandwidth; reading the links from cache instead
+// takes a fifth off the time, while reading the neighbour spinors from the
+// site's own (coalesced) rows changes nothing.
+template <int SP, int GP, int R, int PF>
+__device__ __forceinline__ void hop_prefetch(const HopParams& P, const char* in, int p, int h, const int c[4],
+                                             int s) {
+    if constexpr (PF > 0) {
+        const Geom& g = P.g;
+#pragma unroll
+        for (int mu = 0; mu < 4; mu++) {
+            const int L = g.L[mu];
+            const int smu = mu == 0 ? 1 : mu == 1 ? g.L[0] : mu == 2 ? g.L[0] * g.L[1] : g.L[0] * g.L[1] * g.L[2];
+            const int hb = (c[mu] == 0 ? s + (L - 1) * smu : s - smu) >> 1;
+            prefetch_link<GP, R>(P.gauge, g.stride, p * 4 + mu, h);
+            prefetch_link<GP, R>(P.gauge, g.stride, (1 - p) * 4 + mu, hb);
+            if constexpr (PF > 1) {
+                const int hf = (c[mu] == L - 1 ? s - (L - 1) * smu : s + smu) >> 1;
+                prefetch_spinor<SP>(in, g.stride, hf);
+                prefetch_spinor<SP>(in, g.stride, hb);
+            }
+        }
+    }
+}
+
 // Grid: blockIdx.x = site_block * nrhs + rhs (right-hand sides fastest, so
 // the blocks of all right-hand sides of one site tile run back to back and
 // share the tile's link loads through L2); blockIdx.y = output parity for
 // full-lattice launches.
-template <int SP, int GP, int R, bool DAG, int MINB>
+template <int SP, int GP, int R, bool DAG, int MINB, int PF = 0>
 __global__ void __launch_bounds__(256, MINB) hop_kernel(const HopParams P) {
     using SF = SpinorFmt<SP>;
     using T = typename SF::real;
@@ -231,6 +261,7 @@ __global__ void __launch_bounds__(256, MINB) hop_kernel(const HopParams P) {
         if (h >= g.Vh) continue;
         int c[4], s;
         site_of_half(h, p, g, c, s);
+        hop_prefetch<SP, GP, R, PF>(P, in, p, h, c, s);
         cpx<T> acc[12];
         hop_dir<SP, GP, R, DAG, 0, true>(acc, P, in, p, h, c, s);
         hop_dir<SP, GP, R, DAG, 1, false>(acc, P, in, p, h, c, s);
@@ -453,7 +484,7 @@ __device__ __forceinline__ void hop_dir_p(PSpinor& acc, const HopParams& P, cons
     }
 }
 
-template <int SP, int GP, int R, bool DAG, int MINB>
+template <int SP, int GP, int R, bool DAG, int MINB, int PF = 0>
 __global__ void __launch_bounds__(256, MINB) hop_kernel_p(const HopParams P) {
     using SF = SpinorFmt<SP>;
     const int k = blockIdx.x % P.nrhs;
@@ -474,6 +505,7 @@ __global__ void __launch_bounds__(256, MINB) hop_kernel_p(const HopParams P) {
         if (h >= g.Vh) continue;
         int c[4], s;
         site_of_half(h, p, g, c, s);
+        hop_prefetch<SP, GP, R, PF>(P, in, p, h, c, s);
         PSpinor acc;
         hop_dir_p<SP, GP, R, DAG, 0, true>(acc, P, in, p, h, c, s);
         hop_dir_p<SP, GP, R, DAG, 1, false>(acc, P, in, p, h, c, s);
@@ -817,13 +849,19 @@ __global__ void __launch_bounds__(256, MINB) hop_kernel_rl(const HopParams P) {
 // projection at 128 and 255 registers (at 85 it spills 1.2 KB).
 // v = 20-22: the F16 kernel with its neighbour data copied ahead into shared
 // memory (cp.async), 2 / 3 / 3 hops ahead at 85 / 85 / 64 registers.
-constexpr int kHopVariants = 23;
+// v = 23-25: the kernels of v = 0 and 3 at 128 registers with L2 prefetches
+// of the site's links at its start (23: scalar, 24: paired) and of its links
+// and neighbour spinors (25: paired); single and reduced precision.
+constexpr int kHopVariants = 26;
+constexpr int kHopPrefetchVariant = 23;  // first prefetching variant
 constexpr int kHopBaseVariants = 6;
 constexpr int kHopStagedVariant = 10;  // hop_kernel_rl (128 registers)
 constexpr int kHopMmaVariant = 11;     // hop_kernel_mma (128 registers)
 constexpr int kHopSptVariant = 12;     // first hop_kernel_ps variant
 constexpr int kHopSptLast = 17;      // last hop_kernel_ps variant
 constexpr bool hop_variant_is_pipe(int v) { return v >= 20 && v <= 22; }
+constexpr bool hop_variant_is_pf(int v) { return v >= kHopPrefetchVariant && v <= kHopPrefetchVariant + 2; }
+constexpr int hop_variant_pf(int v) { return !hop_variant_is_pf(v) ? 0 : v == kHopPrefetchVariant + 2 ? 2 : 1; }
 constexpr bool hop_variant_is_ps(int v) { return (v >= kHopSptVariant && v <= kHopSptLast) || hop_variant_is_pipe(v); }
 constexpr int hop_variant_nb(int v) {
     return v == 18 || v == 19 ? 2
@@ -840,13 +878,14 @@ constexpr int hop_variant_minb(int v, int sp) {
            : v == 13 || v == 14 || v == 19 ? 1
            : v == 16 || v == 20 || v == 21 ? 3
            : v == 17 || v == 22 ? 4
-           : v == 18 ? 2
+           : v == 18 || hop_variant_is_pf(v) ? 2
            : v >= kHopStagedVariant ? 2
            : v == 7 ? 2 : 1;
 }
 inline bool hop_variant_valid(int v, Prec sp, int recon, int nrhs) {
     if (v < 0 || v >= kHopVariants) return false;
     if (v < kHopBaseVariants) return true;
+    if (hop_variant_is_pf(v)) return float_storage(sp);
     if (hop_variant_is_pipe(v)) return sp == P_F16 && recon == 12;
     if (hop_variant_is_ps(v)) return hop_variant_hproj(v) ? sp == P_F16 : float_storage(sp);
     if (v == 18 || v == 19) return sp == P_F16 && recon == 12 && nrhs >= 2 && nrhs % 2 == 0;
@@ -898,13 +937,14 @@ void launch_hop_mrhs_v(const HopParams& P, int block, int site_blocks, int ny, b
 
 template <int SP, int GP, int R, int V>
 void launch_hop_v(const HopParams& P, dim3 grid, int block, bool dag, cudaStream_t st) {
-    constexpr int MINB = hop_variant_minb(V, SP);
-    if constexpr (V >= 3 && float_storage(SP)) {
-        if (dag) launch_dep(hop_kernel_p<SP, GP, R, true, MINB>, grid, dim3(block), st, P);
-        else launch_dep(hop_kernel_p<SP, GP, R, false, MINB>, grid, dim3(block), st, P);
+    constexpr int MINB = hop_variant_minb(V, SP), PF = hop_variant_pf(V);
+    constexpr bool paired = PF ? V > kHopPrefetchVariant : V >= 3;
+    if constexpr (paired && float_storage(SP)) {
+        if (dag) launch_dep(hop_kernel_p<SP, GP, R, true, MINB, PF>, grid, dim3(block), st, P);
+        else launch_dep(hop_kernel_p<SP, GP, R, false, MINB, PF>, grid, dim3(block), st, P);
     } else {
-        if (dag) launch_dep(hop_kernel<SP, GP, R, true, MINB>, grid, dim3(block), st, P);
-        else launch_dep(hop_kernel<SP, GP, R, false, MINB>, grid, dim3(block), st, P);
+        if (dag) launch_dep(hop_kernel<SP, GP, R, true, MINB, PF>, grid, dim3(block), st, P);
+        else launch_dep(hop_kernel<SP, GP, R, false, MINB, PF>, grid, dim3(block), st, P);
     }
 }
 
@@ -920,6 +960,17 @@ void launch_hop_prec(const HopParams& P, int block, int site_blocks, int ny, boo
         }
         throw Error(7, "the sites-per-thread hop variants need F32/F16/BF16 spinors");
     }
+    const dim3 grid(site_blocks * P.nrhs, ny);
+    if (hop_variant_is_pf(variant)) {
+        if constexpr (float_storage(SP)) {
+            if (variant == kHopPrefetchVariant) launch_hop_v<SP, GP, R, kHopPrefetchVariant>(P, grid, block, dag, st);
+            else if (variant == kHopPrefetchVariant + 1)
+                launch_hop_v<SP, GP, R, kHopPrefetchVariant + 1>(P, grid, block, dag, st);
+            else launch_hop_v<SP, GP, R, kHopPrefetchVariant + 2>(P, grid, block, dag, st);
+            return;
+        }
+        throw Error(7, "the prefetching hop variants need F32/F16/BF16 spinors");
+    }
     if (variant >= kHopBaseVariants) {
         if constexpr (float_storage(SP) && R == 12) {
             launch_hop_mrhs<SP, GP, R>(P, block, site_blocks, ny, dag, variant, st);
@@ -927,7 +978,6 @@ void launch_hop_prec(const HopParams& P, int block, int site_blocks, int ny, boo
         }
         throw Error(7, "register-blocked hop variant needs F32/F16/BF16 spinors and 12-real links");
     }
-    const dim3 grid(site_blocks * P.nrhs, ny);
     if (wide_regs(SP)) variant %= 3;
     switch (variant) {
         case 1: launch_hop_v<SP, GP, R, 1>(P, grid, block, dag, st); break;

@@ -87,6 +87,7 @@ def _declare(lib):
         "wilson_spinor_export": (I, [VP, VP, VP]),
         "wilson_dslash_h": (I, [VP, VP, VP, D, I, VP]),
         "wilson_probe_fma_peak": (I, [I, P(D), VP]),
+        "wilson_probe_hop_access": (I, [VP, VP, VP, I, P(D), VP]),
         "wilson_dd_halo_bytes": (ctypes.c_longlong, [P(wilson_lattice), I]),
         "wilson_dd_pack": (I, [VP, VP, VP, VP, I, VP]),
         "wilson_dd_hop": (I, [VP, VP, VP, VP, VP, I, I, I, I, VP]),
@@ -302,6 +303,14 @@ def wilson_probe_fma_peak(kind: int, stream=None) -> float:
     """Measured peak GFLOP/s of one FMA kind (WILSON_PROBE_FMA_*)."""
     v = ctypes.c_double(0.0)
     _check(lib().wilson_probe_fma_peak(int(kind), ctypes.byref(v), _stream(stream)))
+    return v.value
+
+
+def wilson_probe_hop_access(out: "Spinor", gauge: "Gauge", inp: "Spinor", reps: int = 50, stream=None) -> float:
+    """Seconds per launch of the even-odd hop's memory accesses with trivial
+    arithmetic (overwrites out with a checksum, not a spinor)."""
+    v = ctypes.c_double(0.0)
+    _check(lib().wilson_probe_hop_access(out.h, gauge.h, inp.h, int(reps), ctypes.byref(v), _stream(stream)))
     return v.value
 
 

@@ -73,6 +73,16 @@ def test_bad_phase_null_and_alias_rejected(w):
         == w.WILSON_ERR_ARG
 
 
+def test_probe_arguments_rejected(w):
+    """The probes check their arguments before any device call."""
+    import ctypes
+    v = ctypes.c_double(0.0)
+    lib = w.lib()
+    assert lib.wilson_probe_hop_access(None, None, None, 3, ctypes.byref(v), None) == w.WILSON_ERR_ARG
+    assert lib.wilson_probe_fma_peak(7, ctypes.byref(v), None) == w.WILSON_ERR_ARG
+    assert lib.wilson_probe_fma_peak(w.WILSON_PROBE_FMA_F64, None, None) == w.WILSON_ERR_ARG
+
+
 def test_last_error_message(w):
     buf = np.zeros(64, dtype=np.complex128)
     L = w.lattice((4, 4, 3, 4))

@@ -217,10 +217,12 @@ def test_handle_schur(w, oracle_mod, prec, recon, dag):
 # Every kernel variant (register budgets 0-2 of the scalar stencil, 3-5 of the
 # paired-FP32 stencil, 12-14 two or four sites per thread, 15-17 the F16
 # projection on packed halves, 20-22 F16 with the neighbour data copied ahead
-# into shared memory; a variant that does not fit a precision runs variant 3)
+# into shared memory, 23-25 the scalar and paired stencils with L2 prefetches
+# of the site's links and neighbours; a variant that does not fit a precision
+# runs variant 3)
 # against the oracle, pinned through WILSON_HOP_VARIANT so that the
 # autotuner's choice does not decide which code is tested.
-@pytest.mark.parametrize("variant", [0, 1, 2, 3, 4, 5, 12, 13, 14, 15, 16, 17, 20, 21, 22])
+@pytest.mark.parametrize("variant", [0, 1, 2, 3, 4, 5, 12, 13, 14, 15, 16, 17, 20, 21, 22, 23, 24, 25])
 @pytest.mark.parametrize("prec,recon", [("f32", 12), ("f16", 12), ("bf16", 12), ("f32", 18), ("f16", 18)])
 def test_every_variant_eo_and_schur(w, oracle_mod, monkeypatch, variant, prec, recon):
     monkeypatch.setenv("WILSON_HOP_VARIANT", str(variant))
@@ -241,7 +243,7 @@ def test_every_variant_eo_and_schur(w, oracle_mod, monkeypatch, variant, prec, r
     assert_parity(got, oracle_mod.wilson_m(U, psi, dims, 0.1350, CPLX_PHASES), TOL[prec])
 
 
-@pytest.mark.parametrize("variant", [0, 3, 12, 14, 16, 21])
+@pytest.mark.parametrize("variant", [0, 3, 12, 14, 16, 21, 23, 25])
 def test_variant_solver(w, oracle_mod, monkeypatch, variant):
     """The mixed-precision solve on each stencil family."""
     monkeypatch.setenv("WILSON_HOP_VARIANT", str(variant))
