@@ -46,9 +46,13 @@
  *   WILSON_TUNE=0                 no autotuning: default launch configurations
  *   WILSON_TUNE_CACHE=path        load tuning decisions from path, append new ones
  *   WILSON_TUNE_VERBOSE=1         report tuning candidates and decisions on stderr
- *   WILSON_HOP_VARIANT=v          pin the hop kernel variant (0..25) of every launch;
+ *   WILSON_HOP_VARIANT=v          pin the hop kernel variant (0..26) of every launch;
  *                                 a variant that does not fit a launch runs variant 3
  *   WILSON_HOP_BLOCK=n            block size with WILSON_HOP_VARIANT (64, 128, 256)
+ *   WILSON_TEST_STAGE_TIMEOUT=1   failure-detection test only: the t-slab hop's
+ *                                 staged slices never complete, so its bounded
+ *                                 waits give up (NaN outputs, counted by
+ *                                 wilson_stage_timeouts)
  *   WILSON_PDL=0                  hops without programmatic dependent launch (read
  *                                 once per process)
  *   WILSON_BATCH_SMALL_VH=n       batched solves: lattices with at most n sites per
@@ -405,6 +409,14 @@ int wilson_probe_fma_peak(int kind, double* gflops, void* stream);
  * WILSON_ERR_ARG for mismatched handles or reps outside [1, 100000]. */
 int wilson_probe_hop_access(wilson_spinor* out, const wilson_gauge* g, const wilson_spinor* in, int reps,
                             double* seconds, void* stream);
+
+/* Failure detection: *count = how many bounded waits in the library's
+ * kernels have given up since the library was loaded in this process (the
+ * t-slab hop waits for its staged slices with an iteration limit of about a
+ * second; a wait that runs out stores NaN at its site, ends that block's
+ * sweep and returns, so a solver reports WILSON_ERR_NUMERIC).  A healthy run
+ * reads 0.  Synchronises the stream. */
+int wilson_stage_timeouts(unsigned long long* count, void* stream);
 
 /* ---------------------------------------------------------------------- */
 /* Errors and version                                                      */

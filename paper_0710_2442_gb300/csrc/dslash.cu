@@ -80,6 +80,8 @@ void launch_hop(const HopLaunch& L, cudaStream_t st) {
     const bool dag = L.dagger != 0;
     const Prec sp = L.sprec, gp = gf.prec;
     const int R = gf.recon;
+    // the t-slab kernel takes one parity and one RHS, in tiles that divide the slice
+    auto slab_ok = [&](int block) { return P.nrhs == 1 && !L.full && hop_slab_fits(P.g, block); };
 
     LaunchConfig cfg;
     const char* forced = std::getenv("WILSON_HOP_VARIANT");  // pins the kernel (tests of each variant)
@@ -93,6 +95,7 @@ void launch_hop(const HopLaunch& L, cudaStream_t st) {
         WL_REQUIRE(cfg.variant >= 0 && cfg.variant < kHopVariants, "WILSON_HOP_VARIANT out of range");
         // a blocked variant that does not fit this launch falls back to variant 3
         if (!hop_variant_valid(cfg.variant, sp, R, P.nrhs)) cfg.variant = 3;
+        if (cfg.variant == kHopSlabVariant && !slab_ok(cfg.block)) cfg.variant = 3;
         WL_REQUIRE(cfg.block == 64 || cfg.block == 128 || cfg.block == 256, "WILSON_HOP_BLOCK must be 64, 128 or 256");
     } else {
         char key[160];
@@ -103,16 +106,18 @@ void launch_hop(const HopLaunch& L, cudaStream_t st) {
         std::vector<LaunchConfig> cands;
         for (const LaunchConfig& c : hop_candidates())  // FP64 has three register budgets, not six
             if (!wide_regs(sp) || c.variant < 3) cands.push_back(c);
-        // two sites per thread, the F16 packed projection and pipeline, and
-        // the prefetching variants
+        // two sites per thread, the F16 packed projection and pipeline, the
+        // prefetching variants and the t-slab kernel where its tiles fit
         for (int block : {64, 128, 256})
             for (int v = kHopSptVariant; v < kHopVariants; v++)
-                if ((hop_variant_is_ps(v) || hop_variant_is_pf(v)) && hop_variant_valid(v, sp, R, P.nrhs))
+                if ((hop_variant_is_ps(v) || hop_variant_is_pf(v) || (v == kHopSlabVariant && slab_ok(block))) &&
+                    hop_variant_valid(v, sp, R, P.nrhs))
                     cands.push_back(LaunchConfig{block, v});
         if (P.nrhs > 1)
             for (int block : {64, 128, 256})
                 for (int v = kHopBaseVariants; v < kHopVariants; v++)
-                    if (!hop_variant_is_ps(v) && !hop_variant_is_pf(v) && hop_variant_valid(v, sp, R, P.nrhs))
+                    if (!hop_variant_is_ps(v) && !hop_variant_is_pf(v) && v != kHopSlabVariant &&
+                        hop_variant_valid(v, sp, R, P.nrhs))
                         cands.push_back(LaunchConfig{block, v});
         if (L.no_tune)
             cfg = tune_lookup(key, cands, LaunchConfig{});
@@ -125,7 +130,8 @@ void launch_hop(const HopLaunch& L, cudaStream_t st) {
     WL_REQUIRE(hop_variant_valid(cfg.variant, sp, R, P.nrhs), "hop variant does not fit this launch");
     // the link-staged and tensor-core kernels have no fused reduction:
     // reducing launches take the paired kernel with the same block
-    if (L.red && (cfg.variant == kHopStagedVariant || cfg.variant == kHopMmaVariant)) cfg.variant = 3;
+    if (L.red && (cfg.variant == kHopStagedVariant || cfg.variant == kHopMmaVariant || cfg.variant == kHopSlabVariant))
+        cfg.variant = 3;
     if (L.tune_only) return;
     if (L.red) {
         P.reduce = 1;

@@ -38,6 +38,8 @@
 //   hop_kernel_f16pipe 20-22 F16 with the neighbour data copied ahead (dslash_spt.cu)
 //   hop_kernel / hop_kernel_p 23-25 with L2 prefetches of the site's links
 //                        (and neighbour spinors) when a thread takes its site
+//   hop_kernel_slab 26   t-slab streaming: neighbouring slices of a tile staged
+//                        in shared memory by bulk copies (dslash_slab.cu)
 // Multi-RHS launches of the first two run the right-hand sides of a site
 // tile as consecutive blocks.  Every kernel starts with the programmatic-
 // dependent-launch wait, so it can be launched with that attribute.
@@ -852,8 +854,13 @@ __global__ void __launch_bounds__(256, MINB) hop_kernel_rl(const HopParams P) {
 // v = 23-25: the kernels of v = 0 and 3 at 128 registers with L2 prefetches
 // of the site's links at its start (23: scalar, 24: paired) and of its links
 // and neighbour spinors (25: paired); single and reduced precision.
-constexpr int kHopVariants = 26;
+// v = 26: the t-slab streaming kernel (dslash_slab.cu): tiles of a 3-d slice
+// swept along t, the neighbouring input slices staged in shared memory by
+// bulk asynchronous copies; one parity, one RHS, non-reducing launches, tiles
+// that divide the slice.
+constexpr int kHopVariants = 27;
 constexpr int kHopPrefetchVariant = 23;  // first prefetching variant
+constexpr int kHopSlabVariant = 26;      // hop_kernel_slab
 constexpr int kHopBaseVariants = 6;
 constexpr int kHopStagedVariant = 10;  // hop_kernel_rl (128 registers)
 constexpr int kHopMmaVariant = 11;     // hop_kernel_mma (128 registers)
@@ -878,7 +885,7 @@ constexpr int hop_variant_minb(int v, int sp) {
            : v == 13 || v == 14 || v == 19 ? 1
            : v == 16 || v == 20 || v == 21 ? 3
            : v == 17 || v == 22 ? 4
-           : v == 18 || hop_variant_is_pf(v) ? 2
+           : v == 18 || hop_variant_is_pf(v) || v == kHopSlabVariant ? 2
            : v >= kHopStagedVariant ? 2
            : v == 7 ? 2 : 1;
 }
@@ -886,6 +893,7 @@ inline bool hop_variant_valid(int v, Prec sp, int recon, int nrhs) {
     if (v < 0 || v >= kHopVariants) return false;
     if (v < kHopBaseVariants) return true;
     if (hop_variant_is_pf(v)) return float_storage(sp);
+    if (v == kHopSlabVariant) return float_storage(sp) && nrhs == 1;
     if (hop_variant_is_pipe(v)) return sp == P_F16 && recon == 12;
     if (hop_variant_is_ps(v)) return hop_variant_hproj(v) ? sp == P_F16 : float_storage(sp);
     if (v == 18 || v == 19) return sp == P_F16 && recon == 12 && nrhs >= 2 && nrhs % 2 == 0;
@@ -902,6 +910,14 @@ void launch_hop_mrhs(const HopParams& P, int block, int site_blocks, int ny, boo
 // The tensor-core kernel (dslash_mma.cu; F16 and BF16 storage, 12-real links).
 template <int SP>
 void launch_hop_mma(const HopParams& P, int block, int site_blocks, int ny, bool dag, cudaStream_t st);
+// The t-slab streaming kernel (dslash_slab.cu; F32/F16/BF16, one parity and
+// one RHS, non-reducing): hop_slab_fits says whether a block size tiles the
+// lattice's 3-d slices; stage_timeouts reads how many of its bounded waits
+// have given up since the library was loaded (synchronises the stream).
+template <int SP, int GP, int R>
+void launch_hop_slab(const HopParams& P, int block, bool dag, cudaStream_t st);
+bool hop_slab_fits(const Geom& g, int block);
+unsigned long long stage_timeouts(cudaStream_t st);
 // Sites per thread and the F16 packed projection (dslash_spt.cu; F32/F16/BF16).
 template <int SP, int GP, int R>
 void launch_hop_ps(const HopParams& P, int block, int site_blocks, int ny, bool dag, int variant, cudaStream_t st);
@@ -961,6 +977,13 @@ void launch_hop_prec(const HopParams& P, int block, int site_blocks, int ny, boo
         throw Error(7, "the sites-per-thread hop variants need F32/F16/BF16 spinors");
     }
     const dim3 grid(site_blocks * P.nrhs, ny);
+    if (variant == kHopSlabVariant) {
+        if constexpr (float_storage(SP)) {
+            launch_hop_slab<SP, GP, R>(P, block, dag, st);
+            return;
+        }
+        throw Error(7, "the slab hop variant needs F32/F16/BF16 spinors");
+    }
     if (hop_variant_is_pf(variant)) {
         if constexpr (float_storage(SP)) {
             if (variant == kHopPrefetchVariant) launch_hop_v<SP, GP, R, kHopPrefetchVariant>(P, grid, block, dag, st);

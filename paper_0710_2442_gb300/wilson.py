@@ -88,6 +88,7 @@ def _declare(lib):
         "wilson_dslash_h": (I, [VP, VP, VP, D, I, VP]),
         "wilson_probe_fma_peak": (I, [I, P(D), VP]),
         "wilson_probe_hop_access": (I, [VP, VP, VP, I, P(D), VP]),
+        "wilson_stage_timeouts": (I, [P(ctypes.c_ulonglong), VP]),
         "wilson_dd_halo_bytes": (ctypes.c_longlong, [P(wilson_lattice), I]),
         "wilson_dd_pack": (I, [VP, VP, VP, VP, I, VP]),
         "wilson_dd_hop": (I, [VP, VP, VP, VP, VP, I, I, I, I, VP]),
@@ -311,6 +312,13 @@ def wilson_probe_hop_access(out: "Spinor", gauge: "Gauge", inp: "Spinor", reps: 
     arithmetic (overwrites out with a checksum, not a spinor)."""
     v = ctypes.c_double(0.0)
     _check(lib().wilson_probe_hop_access(out.h, gauge.h, inp.h, int(reps), ctypes.byref(v), _stream(stream)))
+    return v.value
+
+
+def wilson_stage_timeouts(stream=None) -> int:
+    """Bounded waits in the library's kernels that gave up (0 when healthy)."""
+    v = ctypes.c_ulonglong(0)
+    _check(lib().wilson_stage_timeouts(ctypes.byref(v), _stream(stream)))
     return v.value
 
 

@@ -81,6 +81,7 @@ def test_probe_arguments_rejected(w):
     assert lib.wilson_probe_hop_access(None, None, None, 3, ctypes.byref(v), None) == w.WILSON_ERR_ARG
     assert lib.wilson_probe_fma_peak(7, ctypes.byref(v), None) == w.WILSON_ERR_ARG
     assert lib.wilson_probe_fma_peak(w.WILSON_PROBE_FMA_F64, None, None) == w.WILSON_ERR_ARG
+    assert lib.wilson_stage_timeouts(None, None) == w.WILSON_ERR_ARG
 
 
 def test_last_error_message(w):

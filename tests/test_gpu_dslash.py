@@ -256,6 +256,66 @@ def test_variant_solver(w, oracle_mod, monkeypatch, variant):
     assert np.linalg.norm(r) / np.linalg.norm(b) <= 1.1e-10
 
 
+# The t-slab streaming kernel (variant 26): tiles of a 3-d slice swept along
+# t, the neighbouring input slices staged in shared memory by bulk copies, on
+# lattices whose slices the tile divides: one and several tiles and t-chunks,
+# Lt = 2 (the ring of slices wraps around the lattice), 64/128/256-site
+# tiles.  No bounded wait may give up.
+SLAB_CASES = [((8, 4, 4, 6), 64), ((8, 8, 4, 16), 64), ((4, 4, 8, 2), 64), ((16, 8, 8, 10), 128),
+              ((16, 8, 8, 10), 256), ((8, 8, 8, 8), 256)]
+
+
+@pytest.mark.parametrize("dims,block", SLAB_CASES)
+@pytest.mark.parametrize("prec,recon", [("f32", 12), ("f16", 12), ("bf16", 12), ("f32", 18), ("f16", 18)])
+def test_slab_variant(w, oracle_mod, monkeypatch, dims, block, prec, recon):
+    monkeypatch.setenv("WILSON_HOP_VARIANT", "26")
+    monkeypatch.setenv("WILSON_HOP_BLOCK", str(block))
+    before = w.wilson_stage_timeouts()
+    U = inputs.gauge_field(dims, "weak", eps=0.3, seed=131)
+    src = inputs.gaussian_spinor(inputs.volume(dims) // 2, seed=132)
+    for out_parity in (0, 1):
+        got = handle_hop(w, U, src, dims, CPLX_PHASES, w.PREC[prec], recon, 1 - out_parity, out_parity,
+                         w.WILSON_OP_HOP)
+        assert_parity(got, oracle_mod.dslash_eo(U, src, dims, out_parity, CPLX_PHASES), TOL[prec])
+    got = handle_hop(w, U, src, dims, CPLX_PHASES, w.PREC[prec], recon, 0, 0, w.WILSON_OP_SCHUR_DAG, 0.1350)
+    assert_parity(got, oracle_mod.schur(U, src, dims, 0.1350, 0, True, CPLX_PHASES), TOL[prec])
+    assert w.wilson_stage_timeouts() == before
+
+
+def test_slab_solver(w, oracle_mod, monkeypatch):
+    """The mixed-precision solve with its non-reducing hops on the t-slab kernel."""
+    monkeypatch.setenv("WILSON_HOP_VARIANT", "26")
+    monkeypatch.setenv("WILSON_HOP_BLOCK", "64")
+    dims = (8, 4, 4, 8)
+    U = inputs.gauge_field(dims, "weak", eps=0.3, seed=133)
+    b = inputs.gaussian_spinor(dims, seed=134)
+    x = dev(np.zeros_like(b))
+    w.wilson_cg_solve(x, dev(U), dev(b), w.lattice(dims), 0.135, w.solver_defaults(w.WILSON_F16))
+    r = b - oracle_mod.wilson_m(U, host(x), dims, 0.135)
+    assert np.linalg.norm(r) / np.linalg.norm(b) <= 1.1e-10
+
+
+def test_slab_wait_gives_up(w, oracle_mod, monkeypatch):
+    """Failure detection without a fault: with WILSON_TEST_STAGE_TIMEOUT=1 the
+    staged slices are armed but never copied, so the kernel's bounded waits
+    give up.  The kernel stores NaN at the sites it could not compute and
+    returns, the library counts the timeouts, and the next launch on the same
+    context computes the oracle's hop."""
+    monkeypatch.setenv("WILSON_HOP_VARIANT", "26")
+    monkeypatch.setenv("WILSON_HOP_BLOCK", "64")
+    dims = (4, 4, 8, 2)
+    U = inputs.gauge_field(dims, "weak", eps=0.3, seed=135)
+    src = inputs.gaussian_spinor(inputs.volume(dims) // 2, seed=136)
+    before = w.wilson_stage_timeouts()
+    monkeypatch.setenv("WILSON_TEST_STAGE_TIMEOUT", "1")
+    got = handle_hop(w, U, src, dims, CPLX_PHASES, w.WILSON_F32, 12, 1, 0, w.WILSON_OP_HOP)
+    assert np.isnan(got).any()
+    assert w.wilson_stage_timeouts() > before
+    monkeypatch.delenv("WILSON_TEST_STAGE_TIMEOUT")
+    got = handle_hop(w, U, src, dims, CPLX_PHASES, w.WILSON_F32, 12, 1, 0, w.WILSON_OP_HOP)
+    assert_parity(got, oracle_mod.dslash_eo(U, src, dims, 0, CPLX_PHASES), TOL["f32"])
+
+
 # The register-blocked multi-RHS variants (NB = 2, 2, 3, 4 right-hand sides
 # per thread; 18, 19: NB = 2 with the F16 packed projection), the link-staged
 # one (10: links in shared memory, a loop over the right-hand sides), pinned
