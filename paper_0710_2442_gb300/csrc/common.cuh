@@ -22,7 +22,12 @@ namespace wl {
 // kernel has completed and its memory operations are visible, so a kernel
 // calls it before it reads or writes anything an earlier kernel touches.
 // pdl_trigger() lets the next such kernel be scheduled once every block of
-// this one has started.  Both are no-ops for a plain launch.
+// this one has called it or exited.  The hop kernels call it when a block has
+// finished its sites: calling it at the start, so that the next hop's blocks
+// wait resident through the whole launch, gained nothing on the tuned hops
+// and slowed a chain of hops sharply whenever a kernel of another stream ran
+// alongside (the host-buffer loop with its export on a second stream: 11.9
+// against 14.5 TFlop/s).  Both are no-ops for a plain launch.
 __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 __device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 

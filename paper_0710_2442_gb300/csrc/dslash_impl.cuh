@@ -246,7 +246,6 @@ __global__ void __launch_bounds__(256, MINB) hop_kernel(const HopParams P) {
     const int sb = blockIdx.x / P.nrhs;
     const int nb = gridDim.x / P.nrhs;
     const int p = P.full ? (int)blockIdx.y : P.out_parity;
-    pdl_trigger();
     pdl_wait();
     if (P.skip && __ldcg(P.skip + (size_t)k * P.skip_stride)) return;
     const int pin = 1 - p;
@@ -290,6 +289,7 @@ __global__ void __launch_bounds__(256, MINB) hop_kernel(const HopParams P) {
         if (P.nrhs > 1) SF::template store<true>(out, g.stride, h, acc);
         else SF::store(out, g.stride, h, acc);
     }
+    pdl_trigger();
     if (P.reduce) grid_reduce(nrm, P.red, k, nb * gridDim.y, sb + nb * blockIdx.y);
 }
 
@@ -493,7 +493,6 @@ __global__ void __launch_bounds__(256, MINB) hop_kernel_p(const HopParams P) {
     const int sb = blockIdx.x / P.nrhs;
     const int nb = gridDim.x / P.nrhs;
     const int p = P.full ? (int)blockIdx.y : P.out_parity;
-    pdl_trigger();
     pdl_wait();
     if (P.skip && __ldcg(P.skip + (size_t)k * P.skip_stride)) return;
     const int pin = 1 - p;
@@ -549,6 +548,7 @@ __global__ void __launch_bounds__(256, MINB) hop_kernel_p(const HopParams P) {
         if (P.nrhs > 1) SF::template store_packed<true>(out, g.stride, h, acc);
         else SF::store_packed(out, g.stride, h, acc);
     }
+    pdl_trigger();
     if (P.reduce) grid_reduce(nrm, P.red, k, nb * gridDim.y, sb + nb * blockIdx.y);
 }
 
@@ -641,7 +641,6 @@ __global__ void __launch_bounds__(256, MINB) hop_kernel_pm(const HopParams P) {
     const int sb = blockIdx.x / ng;
     const int nb = gridDim.x / ng;
     const int k0 = grp * NB;
-    pdl_trigger();
     pdl_wait();
     unsigned act = 0;
 #pragma unroll
@@ -706,6 +705,7 @@ __global__ void __launch_bounds__(256, MINB) hop_kernel_pm(const HopParams P) {
             if (act >> r & 1u) SF::template store_packed<true>(out + r * P.out_rstep, g.stride, h, A);
         }
     }
+    pdl_trigger();
     if (P.reduce) {
 #pragma unroll
         for (int r = 0; r < NB; r++)
@@ -770,7 +770,6 @@ __global__ void __launch_bounds__(256, MINB) hop_kernel_rl(const HopParams P) {
     const int T = blockDim.x, t = threadIdx.x;
     const CT* lsm = reinterpret_cast<const CT*>(rl_smem) + t;
     const int sb = blockIdx.x, nb = gridDim.x;
-    pdl_trigger();
     pdl_wait();
     const int p = P.full ? (int)blockIdx.y : P.out_parity;
     const int pin = 1 - p;
@@ -833,6 +832,7 @@ __global__ void __launch_bounds__(256, MINB) hop_kernel_rl(const HopParams P) {
             SF::template store_packed<true>(out, g.stride, h, A);
         }
     }
+    pdl_trigger();
 }
 
 // Kernel variants: v = 0..5: v % 3 is the register budget (blocks of 256

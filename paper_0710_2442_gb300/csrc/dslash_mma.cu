@@ -216,7 +216,6 @@ __global__ void __launch_bounds__(256, MINB) hop_kernel_mma(const HopParams P) {
     const int sb = blockIdx.x / ngrp, nb = gridDim.x / ngrp;
     const int k0 = grp * kGroup;
     const int nk = min(kGroup, P.nrhs - k0);
-    pdl_trigger();
     pdl_wait();
     const int p = P.full ? (int)blockIdx.y : P.out_parity;
     const int pin = 1 - p;
@@ -346,6 +345,7 @@ __global__ void __launch_bounds__(256, MINB) hop_kernel_mma(const HopParams P) {
         }
         __syncwarp();  // the next tile's staging overwrites the slots
     }
+    pdl_trigger();
 }
 
 }  // namespace

@@ -185,7 +185,6 @@ __global__ void __launch_bounds__(256, 2) hop_kernel_slab(const HopParams P, int
     const int t0 = (blockIdx.x / tiles) * tt;
     const int p = P.out_parity;
     const unsigned slot_bytes = slot_bytes_per_site<SP>() * (unsigned)T;
-    pdl_trigger();
     pdl_wait();
     if (P.skip && __ldcg(P.skip)) return;  // a converged right-hand side (block-uniform)
     const char* in = P.in;
@@ -267,6 +266,7 @@ __global__ void __launch_bounds__(256, 2) hop_kernel_slab(const HopParams P, int
         if (abort_sweep) break;
         if (t == 0 && tc + 3 <= t0 + tt) issue(tc + 3);
     }
+    pdl_trigger();
     // copies still in flight (only after an abandoned sweep): wait for them,
     // bounded, before the block's shared memory is released
     if (t == 0)

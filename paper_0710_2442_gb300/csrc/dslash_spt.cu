@@ -83,7 +83,6 @@ __global__ void __launch_bounds__(256, MINB) hop_kernel_ps(const HopParams P) {
     const int sb = blockIdx.x / P.nrhs;
     const int nb = gridDim.x / P.nrhs;
     const int p = P.full ? (int)blockIdx.y : P.out_parity;
-    pdl_trigger();
     pdl_wait();
     if (P.skip && __ldcg(P.skip + (size_t)k * P.skip_stride)) return;
     const int pin = 1 - p;
@@ -156,6 +155,7 @@ __global__ void __launch_bounds__(256, MINB) hop_kernel_ps(const HopParams P) {
             else SF::store_packed(out, g.stride, h, A);
         }
     }
+    pdl_trigger();
     if (P.reduce) grid_reduce(nrm, P.red, k, nb * gridDim.y, sb + nb * blockIdx.y);
 }
 
@@ -201,7 +201,6 @@ __global__ void __launch_bounds__(256, MINB) hop_kernel_f16pipe(const HopParams 
     const int sb = blockIdx.x / P.nrhs;
     const int nb = gridDim.x / P.nrhs;
     const int p = P.full ? (int)blockIdx.y : P.out_parity;
-    pdl_trigger();
     pdl_wait();
     if (P.skip && __ldcg(P.skip + (size_t)k * P.skip_stride)) return;
     const int pin = 1 - p;
@@ -301,6 +300,7 @@ __global__ void __launch_bounds__(256, MINB) hop_kernel_f16pipe(const HopParams 
         if (P.nrhs > 1) SF::template store_packed<true>(out, g.stride, h, acc);
         else SF::store_packed(out, g.stride, h, acc);
     }
+    pdl_trigger();
     if (P.reduce) grid_reduce(nrm, P.red, k, nb * gridDim.y, sb + nb * blockIdx.y);
 }
 
