@@ -850,7 +850,7 @@ __global__ void __launch_bounds__(256, MINB) hop_kernel_rl(const HopParams P) {
 // v = 18, 19: the register-blocked kernel (NB = 2) with the F16 packed
 // projection at 128 and 255 registers (at 85 it spills 1.2 KB).
 // v = 20-22: the F16 kernel with its neighbour data copied ahead into shared
-// memory (cp.async), 2 / 3 / 3 hops ahead at 85 / 85 / 64 registers.
+// memory (cp.async), 2 / 3 / 3 hops ahead at 80 / 80 / 96 registers.
 // v = 23-25: the kernels of v = 0 and 3 at 128 registers with L2 prefetches
 // of the site's links at its start (23: scalar, 24: paired) and of its links
 // and neighbour spinors (25: paired); single and reduced precision.
@@ -884,8 +884,8 @@ constexpr int hop_variant_minb(int v, int sp) {
     return v < kHopBaseVariants ? (wide_regs(sp) ? 1 : 2) + v % 3
            : v == 13 || v == 14 || v == 19 ? 1
            : v == 16 || v == 20 || v == 21 ? 3
-           : v == 17 || v == 22 ? 4
-           : v == 18 || hop_variant_is_pf(v) || v == kHopSlabVariant ? 2
+           : v == 17 ? 4
+           : v == 18 || v == 22 || hop_variant_is_pf(v) || v == kHopSlabVariant ? 2
            : v >= kHopStagedVariant ? 2
            : v == 7 ? 2 : 1;
 }

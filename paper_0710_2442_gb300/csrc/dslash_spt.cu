@@ -188,12 +188,15 @@ __device__ __forceinline__ void f16pipe_hop(PSpinor& acc, const uint4 (&d)[3], f
     expand_p<MU, S, J == 0>(acc, w, sc);
 }
 
-template <bool DAG, int MINB, int D>
-__global__ void __launch_bounds__(256, MINB) hop_kernel_f16pipe(const HopParams P) {
+// TB: the block size (the launch's blockDim.x), a compile-time constant so
+// that every slot offset is an immediate; NREG: the register budget.
+template <bool DAG, int NREG, int D, int TB>
+__global__ void __launch_bounds__(TB) __maxnreg__(NREG) hop_kernel_f16pipe(const HopParams P) {
     using SF = SpinorFmt<P_F16>;
     using GF = GaugeFmt<P_F16, 12>;
     extern __shared__ __align__(16) unsigned char pipe_smem[];
-    const int T = blockDim.x, t = threadIdx.x;
+    constexpr int T = TB;
+    const int t = threadIdx.x;
     uint4* sp = reinterpret_cast<uint4*>(pipe_smem);     // [D][3][T] spinor chunks
     uint2* lk = reinterpret_cast<uint2*>(sp + D * 3 * T);  // [D][3][T] link chunks
     float* scs = reinterpret_cast<float*>(lk + D * 3 * T); // [D][T] scales
@@ -304,20 +307,27 @@ __global__ void __launch_bounds__(256, MINB) hop_kernel_f16pipe(const HopParams 
     if (P.reduce) grid_reduce(nrm, P.red, k, nb * gridDim.y, sb + nb * blockIdx.y);
 }
 
-template <bool DAG, int V>
-void launch_f16pipe_v(const HopParams& P, int block, int site_blocks, int ny, cudaStream_t st) {
-    constexpr int MINB = hop_variant_minb(V, P_F16), D = V == 20 ? 2 : 3;
+template <bool DAG, int V, int TB>
+void launch_f16pipe_tb(const HopParams& P, int site_blocks, int ny, cudaStream_t st) {
+    constexpr int NREG = V == 22 ? 96 : 80, D = V == 20 ? 2 : 3;
     constexpr size_t per_thread = (size_t)D * (3 * 16 + 3 * 8 + 4);
-    auto k = hop_kernel_f16pipe<DAG, MINB, D>;
+    auto k = hop_kernel_f16pipe<DAG, NREG, D, TB>;
     static bool opted[64] = {};  // the larger dynamic shared memory, once per device
     int dev = 0;
     WL_CUDA(cudaGetDevice(&dev));
     WL_REQUIRE(dev >= 0 && dev < 64, "device ordinal out of range");
     if (!opted[dev]) {
-        WL_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(per_thread * 256)));
+        WL_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(per_thread * TB)));
         opted[dev] = true;
     }
-    launch_dep_smem(k, dim3(site_blocks * P.nrhs, ny), dim3(block), per_thread * block, st, P);
+    launch_dep_smem(k, dim3(site_blocks * P.nrhs, ny), dim3(TB), per_thread * TB, st, P);
+}
+template <bool DAG, int V>
+void launch_f16pipe_v(const HopParams& P, int block, int site_blocks, int ny, cudaStream_t st) {
+    if (block == 64) launch_f16pipe_tb<DAG, V, 64>(P, site_blocks, ny, st);
+    else if (block == 128) launch_f16pipe_tb<DAG, V, 128>(P, site_blocks, ny, st);
+    else if (block == 256) launch_f16pipe_tb<DAG, V, 256>(P, site_blocks, ny, st);
+    else throw Error(WILSON_ERR_ARG, "the pipelined F16 hop takes blocks of 64, 128 or 256 threads");
 }
 
 template <int SP, int GP, int R, bool DAG, int V>
