@@ -120,8 +120,20 @@ __device__ inline void grid_reduce(double v, const RedArgs& r, int slot, unsigne
     __syncthreads();
     if (!s_last) return;
     __threadfence();
+    // Each thread adds its strided partials in index order; the loads are
+    // issued eight at a time so that their L2 latencies overlap (the order of
+    // the additions, and so the result, is that of the plain loop).
     double acc = 0.0;
-    for (unsigned int i = threadIdx.x; i < nblocks; i += blockDim.x) acc += __ldcg(part + i);
+    const unsigned int step = blockDim.x;
+    unsigned int i = threadIdx.x;
+    for (; i + 7 * step < nblocks; i += 8 * step) {
+        double v[8];
+#pragma unroll
+        for (int k = 0; k < 8; k++) v[k] = __ldcg(part + i + k * step);
+#pragma unroll
+        for (int k = 0; k < 8; k++) acc += v[k];
+    }
+    for (; i < nblocks; i += step) acc += __ldcg(part + i);
     const double total = block_sum(acc);
     if (threadIdx.x == 0) {
         run_finisher(r, slot, total);
