@@ -654,11 +654,79 @@ __global__ void __cluster_dims__(kSmallCluster, 1, 1) __launch_bounds__(kSmallTh
     small_solve_body<IP, kSmallCluster>(A, ids, G, budget_ns);
 }
 
+// The batched hop of F16 storage on the pipelined site (f16pipe_site): each
+// thread copies the next hops' raw data into its own shared-memory slots
+// (batch variant 22; TB threads per block, D hops ahead, NREG registers).
+template <bool DAG, int NREG, int D, int TB>
+__global__ void __launch_bounds__(TB) __maxnreg__(NREG) bhop_kernel_pipe(const BatchArgs A, const BOp op) {
+    using SF = SpinorFmt<P_F16>;
+    extern __shared__ __align__(16) unsigned char bpipe_smem[];
+    uint4* sp = reinterpret_cast<uint4*>(bpipe_smem);      // [D][3][TB] spinor chunks
+    uint2* lk = reinterpret_cast<uint2*>(sp + D * 3 * TB);  // [D][3][TB] link chunks
+    float* scs = reinterpret_cast<float*>(lk + D * 3 * TB); // [D][TB] scales
+    for (int t = blockIdx.x; t < A.ntiles; t += gridDim.x) {
+        const int pid = __ldg(A.tile_prob + t);
+        if (!tile_active(A, op, pid)) continue;
+        const BatchProb& Pr = A.probs[pid];
+        const Geom& g = Pr.g;
+        const int p = op.out_parity;
+        char* out = Pr.f[op.f_out] + p * Pr.fp[op.f_out];
+        const char* in = Pr.f[op.f_in] + (1 - p) * Pr.fp[op.f_in];
+        const char* x = op.f_x >= 0 ? Pr.f[op.f_x] + p * Pr.fp[op.f_x] : nullptr;
+        const float2 Af = bc2((float)coef_of(op.coef, Pr.kappa));
+        double nrm = 0.0;
+        const int h0 = (t - Pr.tile0) * A.tile;
+        for (int j = threadIdx.x; j < A.tile; j += TB) {
+            const int h = h0 + j;
+            if (h >= g.Vh) break;
+            PSpinor acc;
+            f16pipe_site<DAG, D, TB>(acc, in, Pr.glo, g, p, h, sp, lk, scs, threadIdx.x);
+            if (x) {
+                PSpinor xq;
+                float xs;
+                SF::load_packed(x, g.stride, h, xq, xs);
+                const float2 X = bc2(xs);
+#pragma unroll
+                for (int cc = 0; cc < 3; cc++) {
+                    acc.re01[cc] = fma2(Af, acc.re01[cc], mul2(X, xq.re01[cc]));
+                    acc.im01[cc] = fma2(Af, acc.im01[cc], mul2(X, xq.im01[cc]));
+                    acc.re23[cc] = fma2(Af, acc.re23[cc], mul2(X, xq.re23[cc]));
+                    acc.im23[cc] = fma2(Af, acc.im23[cc], mul2(X, xq.im23[cc]));
+                }
+            } else {
+#pragma unroll
+                for (int cc = 0; cc < 3; cc++) {
+                    acc.re01[cc] = mul2(Af, acc.re01[cc]);
+                    acc.im01[cc] = mul2(Af, acc.im01[cc]);
+                    acc.re23[cc] = mul2(Af, acc.re23[cc]);
+                    acc.im23[cc] = mul2(Af, acc.im23[cc]);
+                }
+            }
+            if (op.fin != BF_NONE) {
+                float2 n2 = make_float2(0.f, 0.f);
+#pragma unroll
+                for (int cc = 0; cc < 3; cc++) {
+                    n2 = fma2(acc.re01[cc], acc.re01[cc], n2);
+                    n2 = fma2(acc.im01[cc], acc.im01[cc], n2);
+                    n2 = fma2(acc.re23[cc], acc.re23[cc], n2);
+                    n2 = fma2(acc.im23[cc], acc.im23[cc], n2);
+                }
+                nrm += (double)n2.x + (double)n2.y;
+            }
+            SF::store_packed(out, g.stride, h, acc);
+        }
+        if (op.fin != BF_NONE) tile_reduce(nrm, A, op, t, pid);
+    }
+}
+
 // ---------------------------------------------------------------------------
 // launchers (instantiated in their own translation units)
 // ---------------------------------------------------------------------------
 // Batched hop: variants 0-2 the scalar stencil (register budgets), 3-5 the
-// paired-FP32 stencil (F32 / F16 / BF16 spinors only).
+// paired-FP32 stencil (F32 / F16 / BF16 spinors only), 22 the pipelined F16
+// stencil (64- or 128-thread blocks).
+constexpr int kBatchPipeVariant = 22;  // the pipelined F16 stencil (as hop variant 22)
+constexpr int kBatchPipeDepth = 3;     // hops copied ahead
 template <int SP, int GP>
 void launch_bhop(const BatchArgs& A, const BOp& o, int dag, int v, int block, int blocks, cudaStream_t st) {
     constexpr int R = wide_regs(SP) ? 18 : 12;
@@ -668,6 +736,20 @@ void launch_bhop(const BatchArgs& A, const BOp& o, int dag, int v, int block, in
 #define WL_BHOP_P(V)                                                                                      \
     if (dag) bhop_kernel_p<SP, GP, 12, true, hop_variant_minb(V, SP)><<<blocks, block, 0, st>>>(A, o);  \
     else bhop_kernel_p<SP, GP, 12, false, hop_variant_minb(V, SP)><<<blocks, block, 0, st>>>(A, o);
+    if constexpr (SP == P_F16 && GP == P_F16) {
+        if (v == kBatchPipeVariant) {
+            constexpr size_t per_thread = (size_t)kBatchPipeDepth * (3 * 16 + 3 * 8 + 4);
+            if (block == 64) {
+                if (dag) bhop_kernel_pipe<true, 96, kBatchPipeDepth, 64><<<blocks, 64, per_thread * 64, st>>>(A, o);
+                else bhop_kernel_pipe<false, 96, kBatchPipeDepth, 64><<<blocks, 64, per_thread * 64, st>>>(A, o);
+            } else {
+                WL_REQUIRE(block == 128, "the pipelined batch hop takes 64- or 128-thread blocks");
+                if (dag) bhop_kernel_pipe<true, 96, kBatchPipeDepth, 128><<<blocks, 128, per_thread * 128, st>>>(A, o);
+                else bhop_kernel_pipe<false, 96, kBatchPipeDepth, 128><<<blocks, 128, per_thread * 128, st>>>(A, o);
+            }
+            return;
+        }
+    }
     if constexpr (float_storage(SP)) {
         if (v == 3) { WL_BHOP_P(3) return; }
         if (v == 4) { WL_BHOP_P(4) return; }

@@ -45,6 +45,8 @@
 // dependent-launch wait, so it can be launched with that attribute.
 #pragma once
 
+#include <cuda_pipeline.h>
+
 #include "internal.h"
 
 namespace wl {
@@ -833,6 +835,83 @@ __global__ void __launch_bounds__(256, MINB) hop_kernel_rl(const HopParams P) {
         }
     }
     pdl_trigger();
+}
+
+// One output site of the pipelined F16 hop (hop_kernel_f16pipe, and the
+// batch's tile form): the eight hops of site h of parity p, each hop's raw
+// data -- the neighbour's three 16-byte chunks and scale, the link's three
+// 8-byte chunks -- copied with cp.async into this thread's own shared-memory
+// slots D hops ahead (sp [D][3][T], lk [D][3][T], scs [D][T]; T the block
+// size, t the thread).  Every copy group is waited for before the function
+// returns, so the slots are free for the next site.
+template <bool DAG, int J>
+__device__ __forceinline__ void f16pipe_hop(PSpinor& acc, const uint4 (&d)[3], float sc, const cpx<float> (&U)[3][3],
+                                            unsigned wrap, const Geom& g) {
+    constexpr int MU = J >> 1;
+    constexpr bool FWD = (J & 1) == 0;
+    constexpr int SF_ = DAG ? -1 : 1;
+    constexpr int S = FWD ? SF_ : -SF_;
+    PHalf hh, w;
+    project_f16_packed<MU, S>(d, hh);
+    if (wrap >> J & 1u) apply_phase_p(hh, (float)g.ph[MU][0], FWD ? (float)g.ph[MU][1] : -(float)g.ph[MU][1]);
+    su3_mul_p<!FWD>(U, hh, w);
+    expand_p<MU, S, J == 0>(acc, w, sc);
+}
+
+template <bool DAG, int D, int T>
+__device__ __forceinline__ void f16pipe_site(PSpinor& acc, const char* in, const char* gauge, const Geom& g, int p,
+                                             int h, uint4* sp, uint2* lk, float* scs, int t) {
+    using GF = GaugeFmt<P_F16, 12>;
+    const int pin = 1 - p;
+    const float* gscale = reinterpret_cast<const float*>(in + 48LL * g.stride);
+    int hn[8];
+    unsigned wrap = 0;
+    {
+        int c[4], s;
+        site_of_half(h, p, g, c, s);
+#pragma unroll
+        for (int mu = 0; mu < 4; mu++) {
+            const int L = g.L[mu];
+            const int smu = mu == 0 ? 1 : mu == 1 ? g.L[0] : mu == 2 ? g.L[0] * g.L[1] : g.L[0] * g.L[1] * g.L[2];
+            const bool wf = c[mu] == L - 1, wb = c[mu] == 0;
+            hn[2 * mu] = (wf ? s - (L - 1) * smu : s + smu) >> 1;
+            hn[2 * mu + 1] = (wb ? s + (L - 1) * smu : s - smu) >> 1;
+            wrap |= (unsigned)wf << (2 * mu) | (unsigned)wb << (2 * mu + 1);
+        }
+    }
+    // hop j's raw data into slot j % D: the neighbour's chunks and scale,
+    // the link of the site (forward) or of the neighbour (backward)
+    auto issue = [&](int j) {
+        const int slot = j % D;
+        const int n = hn[j];
+        const uint4* gs = reinterpret_cast<const uint4*>(in) + n;
+#pragma unroll
+        for (int kk = 0; kk < 3; kk++) __pipeline_memcpy_async(&sp[(slot * 3 + kk) * T + t], gs + (size_t)kk * g.stride, 16);
+        __pipeline_memcpy_async(&scs[slot * T + t], gscale + n, 4);
+        const int blk = ((j & 1) ? pin : p) * 4 + (j >> 1);
+        const uint2* gl = reinterpret_cast<const uint2*>(gauge) + (size_t)blk * 3 * g.stride + ((j & 1) ? n : h);
+#pragma unroll
+        for (int kk = 0; kk < 3; kk++) __pipeline_memcpy_async(&lk[(slot * 3 + kk) * T + t], gl + (size_t)kk * g.stride, 8);
+        __pipeline_commit();
+    };
+#pragma unroll
+    for (int j = 0; j < D; j++) issue(j);
+#define WL_PIPE_HOP(J)                                                                                        \
+    {                                                                                                         \
+        __pipeline_wait_prior(D - 1);                                                                         \
+        constexpr int slot = (J) % D;                                                                         \
+        uint4 d[3];                                                                                           \
+        _Pragma("unroll") for (int kk = 0; kk < 3; kk++) d[kk] = sp[(slot * 3 + kk) * T + t];                 \
+        const float sc = scs[slot * T + t];                                                                   \
+        cpx<float> U[3][3];                                                                                   \
+        GF::decode(&lk[slot * 3 * T + t], T, U);                                                              \
+        f16pipe_hop<DAG, (J)>(acc, d, sc, U, wrap, g);                                                        \
+        if ((J) + D < 8) issue((J) + D);                                                                      \
+        else __pipeline_commit();                                                                             \
+    }
+    WL_PIPE_HOP(0) WL_PIPE_HOP(1) WL_PIPE_HOP(2) WL_PIPE_HOP(3)
+    WL_PIPE_HOP(4) WL_PIPE_HOP(5) WL_PIPE_HOP(6) WL_PIPE_HOP(7)
+#undef WL_PIPE_HOP
 }
 
 // Kernel variants: v = 0..5: v % 3 is the register budget (blocks of 256

@@ -174,26 +174,11 @@ __global__ void __launch_bounds__(256, MINB) hop_kernel_ps(const HopParams P) {
 // packed-projection kernel.  A thread past the lattice's end runs site 0 and
 // stores nothing, so the pipeline never diverges.
 // ---------------------------------------------------------------------------
-template <bool DAG, int J>
-__device__ __forceinline__ void f16pipe_hop(PSpinor& acc, const uint4 (&d)[3], float sc, const cpx<float> (&U)[3][3],
-                                            unsigned wrap, const Geom& g) {
-    constexpr int MU = J >> 1;
-    constexpr bool FWD = (J & 1) == 0;
-    constexpr int SF_ = DAG ? -1 : 1;
-    constexpr int S = FWD ? SF_ : -SF_;
-    PHalf hh, w;
-    project_f16_packed<MU, S>(d, hh);
-    if (wrap >> J & 1u) apply_phase_p(hh, (float)g.ph[MU][0], FWD ? (float)g.ph[MU][1] : -(float)g.ph[MU][1]);
-    su3_mul_p<!FWD>(U, hh, w);
-    expand_p<MU, S, J == 0>(acc, w, sc);
-}
-
 // TB: the block size (the launch's blockDim.x), a compile-time constant so
 // that every slot offset is an immediate; NREG: the register budget.
 template <bool DAG, int NREG, int D, int TB>
 __global__ void __launch_bounds__(TB) __maxnreg__(NREG) hop_kernel_f16pipe(const HopParams P) {
     using SF = SpinorFmt<P_F16>;
-    using GF = GaugeFmt<P_F16, 12>;
     extern __shared__ __align__(16) unsigned char pipe_smem[];
     constexpr int T = TB;
     const int t = threadIdx.x;
@@ -212,60 +197,12 @@ __global__ void __launch_bounds__(TB) __maxnreg__(NREG) hop_kernel_f16pipe(const
     const char* x = P.x ? P.x + (P.full ? p * P.x_pstep : 0) + k * P.x_rstep : nullptr;
     const Geom& g = P.g;
     const float a = (float)P.a;
-    const float* gscale = reinterpret_cast<const float*>(in + 48LL * g.stride);
     double nrm = 0.0;
     for (int h0 = sb * T + t; h0 - t < g.Vh; h0 += nb * T) {
         const bool ok = h0 < g.Vh;
         const int h = ok ? h0 : 0;
-        int hn[8];
-        unsigned wrap = 0;
-        {
-            int c[4], s;
-            site_of_half(h, p, g, c, s);
-#pragma unroll
-            for (int mu = 0; mu < 4; mu++) {
-                const int L = g.L[mu];
-                const int smu = mu == 0 ? 1 : mu == 1 ? g.L[0] : mu == 2 ? g.L[0] * g.L[1] : g.L[0] * g.L[1] * g.L[2];
-                const bool wf = c[mu] == L - 1, wb = c[mu] == 0;
-                hn[2 * mu] = (wf ? s - (L - 1) * smu : s + smu) >> 1;
-                hn[2 * mu + 1] = (wb ? s + (L - 1) * smu : s - smu) >> 1;
-                wrap |= (unsigned)wf << (2 * mu) | (unsigned)wb << (2 * mu + 1);
-            }
-        }
-        // hop j's raw data into slot j % D: the neighbour's chunks and scale,
-        // the link of the site (forward) or of the neighbour (backward)
-        auto issue = [&](int j) {
-            const int slot = j % D;
-            const int n = hn[j];
-            const uint4* gs = reinterpret_cast<const uint4*>(in) + n;
-#pragma unroll
-            for (int kk = 0; kk < 3; kk++) __pipeline_memcpy_async(&sp[(slot * 3 + kk) * T + t], gs + (size_t)kk * g.stride, 16);
-            __pipeline_memcpy_async(&scs[slot * T + t], gscale + n, 4);
-            const int blk = ((j & 1) ? pin : p) * 4 + (j >> 1);
-            const uint2* gl = reinterpret_cast<const uint2*>(P.gauge) + (size_t)blk * 3 * g.stride + ((j & 1) ? n : h);
-#pragma unroll
-            for (int kk = 0; kk < 3; kk++) __pipeline_memcpy_async(&lk[(slot * 3 + kk) * T + t], gl + (size_t)kk * g.stride, 8);
-            __pipeline_commit();
-        };
-#pragma unroll
-        for (int j = 0; j < D; j++) issue(j);
         PSpinor acc;
-#define WL_PIPE_HOP(J)                                                                      \
-        {                                                                                   \
-            __pipeline_wait_prior(D - 1);                                                   \
-            constexpr int slot = (J) % D;                                                   \
-            uint4 d[3];                                                                     \
-            _Pragma("unroll") for (int kk = 0; kk < 3; kk++) d[kk] = sp[(slot * 3 + kk) * T + t]; \
-            const float sc = scs[slot * T + t];                                             \
-            cpx<float> U[3][3];                                                             \
-            GF::decode(&lk[slot * 3 * T + t], T, U);                                        \
-            f16pipe_hop<DAG, (J)>(acc, d, sc, U, wrap, g);                                  \
-            if ((J) + D < 8) issue((J) + D);                                                \
-            else __pipeline_commit();                                                       \
-        }
-        WL_PIPE_HOP(0) WL_PIPE_HOP(1) WL_PIPE_HOP(2) WL_PIPE_HOP(3)
-        WL_PIPE_HOP(4) WL_PIPE_HOP(5) WL_PIPE_HOP(6) WL_PIPE_HOP(7)
-#undef WL_PIPE_HOP
+        f16pipe_site<DAG, D, T>(acc, in, P.gauge, g, p, h, sp, lk, scs, t);
         if (!ok) continue;
         if (P.xpay) {
             PSpinor xq;

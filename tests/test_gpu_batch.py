@@ -56,6 +56,21 @@ def test_batch_matches_oracle(w, oracle_mod, monkeypatch, inner, small_vh):
         assert 0 <= s["seconds"] <= info["device_seconds"] + 1e-6
 
 
+# WILSON_BATCH_HOP pins the inner hop of the device loop: the pipelined F16
+# stencil (variant 22, 64- and 128-thread blocks, 256-site tiles walked by
+# 4 or 2 sites per thread) and the paired stencil, on MIX through the loop.
+@pytest.mark.parametrize("hop", ["22:64", "22:128", "4:128"])
+def test_batch_inner_hop_variants(w, oracle_mod, monkeypatch, hop):
+    monkeypatch.setenv("WILSON_BATCH_SMALL_VH", "0")
+    monkeypatch.setenv("WILSON_BATCH_HOP", hop)
+    probs, hf = make_batch(w, MIX)
+    rc, st, info = w.wilson_batch_solve(probs, w.solver_defaults(w.WILSON_F16))
+    assert rc == 0 and not info["timed_out"] and info["tiles"] > 0
+    for q, (dims, U, b, kappa), s in zip(probs, hf, st):
+        assert s["status"] == 0
+        assert true_resid(oracle_mod, U, host(q["x"]), b, dims, kappa) <= 1.1e-10
+
+
 # WILSON_BATCH_TILE pins the tile size of every class (the autotuner's
 # candidates): 128, 256 and 512 sites, on MIX (half volumes 32 to 512 sites:
 # single, partial and many tiles per problem) through the device loop.
