@@ -83,6 +83,21 @@ void launch_hop(const HopLaunch& L, cudaStream_t st) {
     // the t-slab kernel takes one parity and one RHS, in tiles that divide the slice
     auto slab_ok = [&](int block) { return P.nrhs == 1 && !L.full && hop_slab_fits(P.g, block); };
 
+    // The grid of a launch.  A reducing launch walks the lattice with a capped
+    // grid (one partial per block, summed by the last block in a fixed
+    // order): one resident wave of the block size, the blocks that the
+    // variant's register budget guarantees on every SM, so no tail wave.
+    auto grid_of = [&](const LaunchConfig& c) {
+        int cap = 0;
+        if (L.red) {
+            const int per_sm = std::max(1, hop_variant_minb(c.variant, sp) * 256 / c.block);
+            cap = std::min(L.grid_cap, device_sm_count() * per_sm);
+        }
+        return hop_grid_blocks(P.g, c.block * hop_variant_spt(c.variant), cap);
+    };
+    // the link-staged, tensor-core and t-slab kernels have no fused reduction
+    auto reduces = [](int v) { return v != kHopStagedVariant && v != kHopMmaVariant && v != kHopSlabVariant; };
+
     LaunchConfig cfg;
     const char* forced = std::getenv("WILSON_HOP_VARIANT");  // pins the kernel (tests of each variant)
     if (L.block > 0) {
@@ -98,10 +113,14 @@ void launch_hop(const HopLaunch& L, cudaStream_t st) {
         if (cfg.variant == kHopSlabVariant && !slab_ok(cfg.block)) cfg.variant = 3;
         WL_REQUIRE(cfg.block == 64 || cfg.block == 128 || cfg.block == 256, "WILSON_HOP_BLOCK must be 64, 128 or 256");
     } else {
-        char key[160];
-        snprintf(key, sizeof(key), "hop:s%d:g%d:r%d:d%d:f%d:x%d:n%d:%dx%dx%dx%d", (int)sp, (int)gp, R, (int)dag,
-                 L.full, L.xpay, P.nrhs, P.g.L[0], P.g.L[1], P.g.L[2], P.g.L[3]);
-        // tuning launches never reduce: the finishers are not idempotent
+        // Reducing launches are their own launch kind (key suffix ":red"):
+        // their grid is one capped wave, and the variant that streams best
+        // over the whole lattice need not walk it best in a wave.
+        char key[170];
+        snprintf(key, sizeof(key), "hop:s%d:g%d:r%d:d%d:f%d:x%d:n%d:%dx%dx%dx%d%s", (int)sp, (int)gp, R, (int)dag,
+                 L.full, L.xpay, P.nrhs, P.g.L[0], P.g.L[1], P.g.L[2], P.g.L[3], L.red ? ":red" : "");
+        // tuning launches never reduce (the finishers are not idempotent):
+        // a reducing launch is timed as its non-reducing copy on its own grid
         const HopParams Pt = P;
         std::vector<LaunchConfig> cands;
         for (const LaunchConfig& c : hop_candidates())  // FP64 has three register budgets, not six
@@ -119,35 +138,26 @@ void launch_hop(const HopLaunch& L, cudaStream_t st) {
                     if (!hop_variant_is_ps(v) && !hop_variant_is_pf(v) && v != kHopSlabVariant &&
                         hop_variant_valid(v, sp, R, P.nrhs))
                         cands.push_back(LaunchConfig{block, v});
+        if (L.red) cands.erase(std::remove_if(cands.begin(), cands.end(),
+                                              [&](const LaunchConfig& c) { return !reduces(c.variant); }),
+                               cands.end());
         if (L.no_tune)
             cfg = tune_lookup(key, cands, LaunchConfig{});
         else
             cfg = tune_launch(key, cands, LaunchConfig{}, st, [&](const LaunchConfig& c) {
-                dispatch(Pt, sp, gp, R, c.block, hop_grid_blocks(Pt.g, c.block * hop_variant_spt(c.variant), 0), ny,
-                         dag, c.variant, st);
+                dispatch(Pt, sp, gp, R, c.block, grid_of(c), ny, dag, c.variant, st);
             });
     }
     WL_REQUIRE(hop_variant_valid(cfg.variant, sp, R, P.nrhs), "hop variant does not fit this launch");
-    // the link-staged and tensor-core kernels have no fused reduction:
-    // reducing launches take the paired kernel with the same block
-    if (L.red && (cfg.variant == kHopStagedVariant || cfg.variant == kHopMmaVariant || cfg.variant == kHopSlabVariant))
-        cfg.variant = 3;
+    // a pinned variant without a fused reduction: the paired kernel, same block
+    if (L.red && !reduces(cfg.variant)) cfg.variant = 3;
     if (L.tune_only) return;
     if (L.red) {
         P.reduce = 1;
         P.red = *L.red;
         WL_REQUIRE(!L.full, "reducing hop launches are single-parity");
     }
-    // A reducing launch walks the lattice with a capped grid (one partial per
-    // block, summed by the last block in a fixed order).  It runs 256-thread
-    // blocks, one resident wave of them (the variant's guaranteed blocks per
-    // SM on every SM): no tail wave, and the finisher sums few partials.
-    int cap = 0;
-    if (L.red) {
-        cfg.block = 256;
-        cap = std::min(L.grid_cap, device_sm_count() * hop_variant_minb(cfg.variant, sp));
-    }
-    const int site_blocks = hop_grid_blocks(P.g, cfg.block * hop_variant_spt(cfg.variant), cap);
+    const int site_blocks = grid_of(cfg);
     WL_REQUIRE(!L.red || site_blocks <= L.red->slot_cap, "reduction capacity below the grid size");
     dispatch(P, sp, gp, R, cfg.block, site_blocks, ny, dag, cfg.variant, st);
     WL_LAUNCH_CHECK();

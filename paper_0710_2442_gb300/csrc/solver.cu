@@ -96,8 +96,9 @@ void schur_apply(const GaugeField& gf, Prec sp, Vec out, Vec in, Vec tmp, int nr
     schur_launch(gf, sp, out, in, tmp, nrhs, kappa, dag, red, skip, skip_stride, grid_cap, false, st);
 }
 
-void schur_tune(const GaugeField& gf, Prec sp, Vec out, Vec in, Vec tmp, int nrhs, int dag, cudaStream_t st) {
-    schur_launch(gf, sp, out, in, tmp, nrhs, 0.0, dag, nullptr, nullptr, 0, 0, true, st);
+void schur_tune(const GaugeField& gf, Prec sp, Vec out, Vec in, Vec tmp, int nrhs, int dag, const RedArgs* red,
+                int grid_cap, cudaStream_t st) {
+    schur_launch(gf, sp, out, in, tmp, nrhs, 0.0, dag, red, nullptr, 0, red ? grid_cap : 0, true, st);
 }
 
 namespace {
@@ -218,9 +219,16 @@ std::vector<SolveStats> cg_solve_prepared(SpinorField& x, const SpinorField& b, 
     // captured stream).  Tuning launches write only scratch fields; once the
     // configurations are known this launches nothing.
     for (int k = 0; k < nr; k++) WL_CUDA(cudaMemsetAsync(in.p.block(0, k), 0, in.p.pbytes, st));
-    for (int dag = 0; dag < 2; dag++)
-        schur_tune(glo, in.ip, vec(in.q, 0), vec(in.p, 0), vec(in.t, 1), nr, dag, st);
-    schur_tune(g64, P_F64, vec(q64, 0), vec(x, 0), vec(t64, 1), nr, 0, st);
+    {
+        // the inner operators as the iterations launch them (second hop
+        // reducing: its own launch kind) and without reductions
+        const RedArgs rt = red.args(slot(2), FIN_CG_ALPHA, nullptr, sc);
+        for (int dag = 0; dag < 2; dag++) {
+            schur_tune(glo, in.ip, vec(in.q, 0), vec(in.p, 0), vec(in.t, 1), nr, dag, &rt, grid_cap, st);
+            schur_tune(glo, in.ip, vec(in.q, 0), vec(in.p, 0), vec(in.t, 1), nr, dag, nullptr, 0, st);
+        }
+    }
+    schur_tune(g64, P_F64, vec(q64, 0), vec(x, 0), vec(t64, 1), nr, 0, nullptr, 0, st);
 
     auto iteration = [&](cudaStream_t s) {
         const int* skip = &sc->done;

@@ -74,7 +74,10 @@ void schur_apply(const GaugeField& gf, Prec sp, Vec out, Vec in, Vec tmp, int nr
                  const RedArgs* red, const int* skip, int skip_stride, int grid_cap, cudaStream_t st);
 // Tunes the launch configurations of schur_apply's two hops where they are
 // not known yet (the tuning launches write out and tmp); launches nothing else.
-void schur_tune(const GaugeField& gf, Prec sp, Vec out, Vec in, Vec tmp, int nrhs, int dag, cudaStream_t st);
+// red != nullptr tunes the reducing form of the second hop (grid_cap: its
+// reduction capacity); red itself is not written.
+void schur_tune(const GaugeField& gf, Prec sp, Vec out, Vec in, Vec tmp, int nrhs, int dag, const RedArgs* red,
+                int grid_cap, cudaStream_t st);
 
 // Solve M x_k = b_k for the nrhs right-hand sides of b (full F64 fields; x:
 // full F64, in/out) with independent CGs run in lockstep.  g64: FP64 links;
