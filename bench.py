@@ -47,7 +47,7 @@ SOLUTIONS = []
 # DRAM bytes (read + write) per launch of the tuned 32^3 x 64 even-odd kernel, read from one
 # ncu capture of that kernel (keyed by storage precision and link reals); a fixed figure, not
 # measured by this run.
-NCU_TRAFFIC = {("f32", 12): 581.4e6, ("f16", 12): 299.3e6, ("f64", 18): 1621.5e6}
+NCU_TRAFFIC = {("f32", 12): 581.6e6, ("f16", 12): 298.5e6, ("f64", 18): 1621.5e6}
 TRAFFIC_SOURCE = "ncu capture of the tuned kernel (dram__bytes_read.sum + dram__bytes_write.sum), fixed figure"
 WORKLOAD = "dslash_eo_f32_32^3x64"
 L2_NOTE = ("inputs larger than L2: each application streams 403 MB of links plus 2 x 101 MB of spinors "
