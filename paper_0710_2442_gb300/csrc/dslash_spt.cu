@@ -22,7 +22,8 @@
 // and the scale stay FP32 as in hop_kernel_p.
 //
 // Variants: 12 = SPT 2 at 128 registers, 13 = SPT 2 at 255, 14 = SPT 4 at
-// 255; 15, 16, 17 = the F16 projection at 128, 85 and 64 registers.
+// 255; 15, 16, 17 = the F16 projection at 128, 85 and 64 registers; 20-22
+// the pipelined F16 kernel below.
 #include <cuda_pipeline.h>
 
 #include "dslash_impl.cuh"
@@ -161,18 +162,20 @@ __global__ void __launch_bounds__(256, MINB) hop_kernel_ps(const HopParams P) {
 
 // ---------------------------------------------------------------------------
 // F16 hop with the neighbour data copied ahead into shared memory (variants
-// 20-22).  The F16 hop's exact loads alone run at 0.93 of the copy bandwidth,
-// the kernel itself at 0.6: its arithmetic waits on loads it cannot keep in
-// flight at the occupancy its registers allow.  Here each thread issues the
-// raw data of a hop (3 spinor chunks, the scale, 3 link chunks) with
-// asynchronous copies (cp.async) into its own shared-memory slots, D hops
-// ahead, so the loads in flight hold no registers.  Before computing hop j
-// the thread waits for that hop's copy group (a hardware wait, no spin);
-// after computing it, it reuses the slot for hop j + D.  Slots are laid out
-// [slot][chunk][thread] (conflict-free warp accesses); a thread reads only
-// what it copied, so no barrier is needed.  The arithmetic is that of the
-// packed-projection kernel.  A thread past the lattice's end runs site 0 and
-// stores nothing, so the pipeline never diverges.
+// 20-22: 2 / 3 / 3 hops ahead at 80 / 80 / 96 registers).  The F16 hop's
+// exact loads alone run at 0.93 of the copy bandwidth, the packed-projection
+// kernel at 0.6: its arithmetic waits on loads it cannot keep in flight at
+// the occupancy its registers allow.  Here each thread issues the raw data
+// of a hop (3 spinor chunks, the scale, 3 link chunks) with asynchronous
+// copies (cp.async) into its own shared-memory slots, D hops ahead, so the
+// loads in flight hold no registers (f16pipe_site, shared with the batch's
+// tile kernel).  Before computing hop j the thread waits for that hop's copy
+// group (a hardware wait, no spin); after computing it, it reuses the slot
+// for hop j + D.  Slots are laid out [slot][chunk][thread] (conflict-free
+// warp accesses); a thread reads only what it copied, so no barrier is
+// needed.  The arithmetic is that of the packed-projection kernel.  A thread
+// past the lattice's end runs site 0 and stores nothing, so the warp does
+// not diverge inside the pipeline.
 // ---------------------------------------------------------------------------
 // TB: the block size (the launch's blockDim.x), a compile-time constant so
 // that every slot offset is an immediate; NREG: the register budget.
