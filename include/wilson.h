@@ -46,7 +46,7 @@
  *   WILSON_TUNE=0                 no autotuning: default launch configurations
  *   WILSON_TUNE_CACHE=path        load tuning decisions from path, append new ones
  *   WILSON_TUNE_VERBOSE=1         report tuning candidates and decisions on stderr
- *   WILSON_HOP_VARIANT=v          pin the hop kernel variant (0..26) of every launch;
+ *   WILSON_HOP_VARIANT=v          pin the hop kernel variant (0..28) of every launch;
  *                                 a variant that does not fit a launch runs variant 3
  *   WILSON_HOP_BLOCK=n            block size with WILSON_HOP_VARIANT (64, 128, 256)
  *   WILSON_TEST_STAGE_TIMEOUT=1   failure-detection test only: the t-slab hop's

@@ -40,6 +40,8 @@
 //                        (and neighbour spinors) when a thread takes its site
 //   hop_kernel_slab 26   t-slab streaming: neighbouring slices of a tile staged
 //                        in shared memory by bulk copies (dslash_slab.cu)
+//   hop_kernel_f16pipe2 27-28 the F16 pipeline with two right-hand sides per
+//                        thread sharing each hop's link (dslash_spt.cu)
 // Multi-RHS launches of the first two run the right-hand sides of a site
 // tile as consecutive blocks.  Every kernel starts with the programmatic-
 // dependent-launch wait, so it can be launched with that attribute.
@@ -937,7 +939,11 @@ __device__ __forceinline__ void f16pipe_site(PSpinor& acc, const char* in, const
 // swept along t, the neighbouring input slices staged in shared memory by
 // bulk asynchronous copies; one parity, one RHS, non-reducing launches, tiles
 // that divide the slice.
-constexpr int kHopVariants = 27;
+// v = 27, 28: the pipelined F16 kernel with two right-hand sides per thread
+// (one link copy and decode per hop for both), 2 / 3 hops ahead at 128
+// registers; even nrhs.
+constexpr int kHopVariants = 29;
+constexpr int kHopPipe2Variant = 27;     // first two-RHS pipelined variant
 constexpr int kHopPrefetchVariant = 23;  // first prefetching variant
 constexpr int kHopSlabVariant = 26;      // hop_kernel_slab
 constexpr int kHopBaseVariants = 6;
@@ -946,11 +952,12 @@ constexpr int kHopMmaVariant = 11;     // hop_kernel_mma (128 registers)
 constexpr int kHopSptVariant = 12;     // first hop_kernel_ps variant
 constexpr int kHopSptLast = 17;      // last hop_kernel_ps variant
 constexpr bool hop_variant_is_pipe(int v) { return v >= 20 && v <= 22; }
+constexpr bool hop_variant_is_pipe2(int v) { return v == kHopPipe2Variant || v == kHopPipe2Variant + 1; }
 constexpr bool hop_variant_is_pf(int v) { return v >= kHopPrefetchVariant && v <= kHopPrefetchVariant + 2; }
 constexpr int hop_variant_pf(int v) { return !hop_variant_is_pf(v) ? 0 : v == kHopPrefetchVariant + 2 ? 2 : 1; }
 constexpr bool hop_variant_is_ps(int v) { return (v >= kHopSptVariant && v <= kHopSptLast) || hop_variant_is_pipe(v); }
 constexpr int hop_variant_nb(int v) {
-    return v == 18 || v == 19 ? 2
+    return v == 18 || v == 19 || hop_variant_is_pipe2(v) ? 2
            : v < kHopBaseVariants || v >= kHopStagedVariant ? 1 : v == 6 || v == 7 ? 2 : v == 8 ? 3 : 4;
 }
 constexpr int hop_variant_spt(int v) { return v == 12 || v == 13 ? 2 : v == 14 ? 4 : 1; }
@@ -964,7 +971,7 @@ constexpr int hop_variant_minb(int v, int sp) {
            : v == 13 || v == 14 || v == 19 ? 1
            : v == 16 || v == 20 || v == 21 ? 3
            : v == 17 ? 4
-           : v == 18 || v == 22 || hop_variant_is_pf(v) || v == kHopSlabVariant ? 2
+           : v == 18 || v == 22 || hop_variant_is_pf(v) || v == kHopSlabVariant || hop_variant_is_pipe2(v) ? 2
            : v >= kHopStagedVariant ? 2
            : v == 7 ? 2 : 1;
 }
@@ -973,6 +980,7 @@ inline bool hop_variant_valid(int v, Prec sp, int recon, int nrhs) {
     if (v < kHopBaseVariants) return true;
     if (hop_variant_is_pf(v)) return float_storage(sp);
     if (v == kHopSlabVariant) return float_storage(sp) && nrhs == 1;
+    if (hop_variant_is_pipe2(v)) return sp == P_F16 && recon == 12 && nrhs >= 2 && nrhs % 2 == 0;
     if (hop_variant_is_pipe(v)) return sp == P_F16 && recon == 12;
     if (hop_variant_is_ps(v)) return hop_variant_hproj(v) ? sp == P_F16 : float_storage(sp);
     if (v == 18 || v == 19) return sp == P_F16 && recon == 12 && nrhs >= 2 && nrhs % 2 == 0;
@@ -995,6 +1003,9 @@ void launch_hop_mma(const HopParams& P, int block, int site_blocks, int ny, bool
 // have given up since the library was loaded (synchronises the stream).
 template <int SP, int GP, int R>
 void launch_hop_slab(const HopParams& P, int block, bool dag, cudaStream_t st);
+// The two-RHS pipelined F16 kernel (dslash_spt.cu; F16-12, even nrhs).
+void launch_hop_f16pipe2(const HopParams& P, int block, int site_blocks, int ny, bool dag, int variant,
+                         cudaStream_t st);
 bool hop_slab_fits(const Geom& g, int block);
 unsigned long long stage_timeouts(cudaStream_t st);
 // Sites per thread and the F16 packed projection (dslash_spt.cu; F32/F16/BF16).
@@ -1062,6 +1073,13 @@ void launch_hop_prec(const HopParams& P, int block, int site_blocks, int ny, boo
             return;
         }
         throw Error(7, "the slab hop variant needs F32/F16/BF16 spinors");
+    }
+    if (hop_variant_is_pipe2(variant)) {
+        if constexpr (SP == P_F16 && GP == P_F16 && R == 12) {
+            launch_hop_f16pipe2(P, block, site_blocks, ny, dag, variant, st);
+            return;
+        }
+        throw Error(7, "the two-RHS pipelined hop variants need F16 spinors and 12-real links");
     }
     if (hop_variant_is_pf(variant)) {
         if constexpr (float_storage(SP)) {

@@ -270,6 +270,179 @@ void launch_f16pipe_v(const HopParams& P, int block, int site_blocks, int ny, cu
     else throw Error(WILSON_ERR_ARG, "the pipelined F16 hop takes blocks of 64, 128 or 256 threads");
 }
 
+// Two right-hand sides per thread on the pipelined F16 stencil (variants 27,
+// 28).  A thread computes one site for right-hand sides k0 and k0 + 1: per
+// hop it copies the link once and both neighbour spinors (chunks and scales)
+// into its slots, decodes the link once and applies it to both, so the link's
+// copy, conversion and third-row reconstruction are shared.  Slots: spinor
+// chunks [D][2][3][T], scales [D][2][T], link chunks [D][3][T].  Skip flags,
+// the epilogue and the per-RHS reductions as in hop_kernel_pm.
+template <bool DAG, int D, int T>
+__device__ __forceinline__ void f16pipe2_site(PSpinor (&acc)[2], const char* in0, long long rstep,
+                                              const char* gauge, const Geom& g, int p, int h, uint4* sp, uint2* lk,
+                                              float* scs, int t) {
+    using GF = GaugeFmt<P_F16, 12>;
+    const int pin = 1 - p;
+    int hn[8];
+    unsigned wrap = 0;
+    {
+        int c[4], s;
+        site_of_half(h, p, g, c, s);
+#pragma unroll
+        for (int mu = 0; mu < 4; mu++) {
+            const int L = g.L[mu];
+            const int smu = mu == 0 ? 1 : mu == 1 ? g.L[0] : mu == 2 ? g.L[0] * g.L[1] : g.L[0] * g.L[1] * g.L[2];
+            const bool wf = c[mu] == L - 1, wb = c[mu] == 0;
+            hn[2 * mu] = (wf ? s - (L - 1) * smu : s + smu) >> 1;
+            hn[2 * mu + 1] = (wb ? s + (L - 1) * smu : s - smu) >> 1;
+            wrap |= (unsigned)wf << (2 * mu) | (unsigned)wb << (2 * mu + 1);
+        }
+    }
+    auto issue = [&](int j) {
+        const int slot = j % D;
+        const int n = hn[j];
+#pragma unroll
+        for (int r = 0; r < 2; r++) {
+            const char* in = in0 + r * rstep;
+            const uint4* gs = reinterpret_cast<const uint4*>(in) + n;
+#pragma unroll
+            for (int kk = 0; kk < 3; kk++)
+                __pipeline_memcpy_async(&sp[((slot * 2 + r) * 3 + kk) * T + t], gs + (size_t)kk * g.stride, 16);
+            __pipeline_memcpy_async(&scs[(slot * 2 + r) * T + t],
+                                    reinterpret_cast<const float*>(in + 48LL * g.stride) + n, 4);
+        }
+        const int blk = ((j & 1) ? pin : p) * 4 + (j >> 1);
+        const uint2* gl = reinterpret_cast<const uint2*>(gauge) + (size_t)blk * 3 * g.stride + ((j & 1) ? n : h);
+#pragma unroll
+        for (int kk = 0; kk < 3; kk++)
+            __pipeline_memcpy_async(&lk[(slot * 3 + kk) * T + t], gl + (size_t)kk * g.stride, 8);
+        __pipeline_commit();
+    };
+#pragma unroll
+    for (int j = 0; j < D; j++) issue(j);
+#define WL_PIPE2_HOP(J)                                                                                         \
+    {                                                                                                           \
+        __pipeline_wait_prior(D - 1);                                                                           \
+        constexpr int slot = (J) % D;                                                                           \
+        cpx<float> U[3][3];                                                                                     \
+        GF::decode(&lk[slot * 3 * T + t], T, U);                                                                \
+        _Pragma("unroll") for (int r = 0; r < 2; r++) {                                                         \
+            uint4 d[3];                                                                                         \
+            _Pragma("unroll") for (int kk = 0; kk < 3; kk++) d[kk] = sp[((slot * 2 + r) * 3 + kk) * T + t];     \
+            f16pipe_hop<DAG, (J)>(acc[r], d, scs[(slot * 2 + r) * T + t], U, wrap, g);                          \
+        }                                                                                                       \
+        if ((J) + D < 8) issue((J) + D);                                                                        \
+        else __pipeline_commit();                                                                               \
+    }
+    WL_PIPE2_HOP(0) WL_PIPE2_HOP(1) WL_PIPE2_HOP(2) WL_PIPE2_HOP(3)
+    WL_PIPE2_HOP(4) WL_PIPE2_HOP(5) WL_PIPE2_HOP(6) WL_PIPE2_HOP(7)
+#undef WL_PIPE2_HOP
+}
+
+template <bool DAG, int NREG, int D, int TB>
+__global__ void __launch_bounds__(TB) __maxnreg__(NREG) hop_kernel_f16pipe2(const HopParams P) {
+    using SF = SpinorFmt<P_F16>;
+    extern __shared__ __align__(16) unsigned char pipe2_smem[];
+    constexpr int T = TB;
+    const int t = threadIdx.x;
+    uint4* sp = reinterpret_cast<uint4*>(pipe2_smem);       // [D][2][3][T] spinor chunks
+    uint2* lk = reinterpret_cast<uint2*>(sp + D * 6 * T);    // [D][3][T] link chunks
+    float* scs = reinterpret_cast<float*>(lk + D * 3 * T);   // [D][2][T] scales
+    const int ng = P.nrhs / 2;
+    const int grp = blockIdx.x % ng;
+    const int sb = blockIdx.x / ng;
+    const int nb = gridDim.x / ng;
+    const int k0 = grp * 2;
+    pdl_wait();
+    unsigned act = 0;
+#pragma unroll
+    for (int r = 0; r < 2; r++)
+        if (!P.skip || !__ldcg(P.skip + (size_t)(k0 + r) * P.skip_stride)) act |= 1u << r;
+    if (!act) return;
+    const int p = P.full ? (int)blockIdx.y : P.out_parity;
+    const int pin = 1 - p;
+    char* out = P.out + (P.full ? p * P.out_pstep : 0) + k0 * P.out_rstep;
+    const char* in = P.in + (P.full ? pin * P.in_pstep : 0) + k0 * P.in_rstep;
+    const char* x = P.x ? P.x + (P.full ? p * P.x_pstep : 0) + k0 * P.x_rstep : nullptr;
+    const Geom& g = P.g;
+    const float a = (float)P.a;
+    double nrm[2] = {0.0, 0.0};
+    for (int h0 = sb * T + t; h0 - t < g.Vh; h0 += nb * T) {
+        const bool ok = h0 < g.Vh;
+        const int h = ok ? h0 : 0;
+        PSpinor acc[2];
+        f16pipe2_site<DAG, D, T>(acc, in, P.in_rstep, P.gauge, g, p, h, sp, lk, scs, t);
+        if (!ok) continue;
+#pragma unroll
+        for (int r = 0; r < 2; r++) {
+            PSpinor& A = acc[r];
+            if (P.xpay) {
+                PSpinor xq;
+                float xs;
+                SF::load_packed(x + r * P.x_rstep, g.stride, h, xq, xs);
+                const float2 Af = bc2(a), X = bc2(xs);
+#pragma unroll
+                for (int cc = 0; cc < 3; cc++) {
+                    A.re01[cc] = fma2(Af, A.re01[cc], mul2(X, xq.re01[cc]));
+                    A.im01[cc] = fma2(Af, A.im01[cc], mul2(X, xq.im01[cc]));
+                    A.re23[cc] = fma2(Af, A.re23[cc], mul2(X, xq.re23[cc]));
+                    A.im23[cc] = fma2(Af, A.im23[cc], mul2(X, xq.im23[cc]));
+                }
+            } else if (P.a != 1.0) {
+                const float2 Af = bc2(a);
+#pragma unroll
+                for (int cc = 0; cc < 3; cc++) {
+                    A.re01[cc] = mul2(Af, A.re01[cc]);
+                    A.im01[cc] = mul2(Af, A.im01[cc]);
+                    A.re23[cc] = mul2(Af, A.re23[cc]);
+                    A.im23[cc] = mul2(Af, A.im23[cc]);
+                }
+            }
+            if (P.reduce) {
+                float2 n2 = make_float2(0.f, 0.f);
+#pragma unroll
+                for (int cc = 0; cc < 3; cc++) {
+                    n2 = fma2(A.re01[cc], A.re01[cc], n2);
+                    n2 = fma2(A.im01[cc], A.im01[cc], n2);
+                    n2 = fma2(A.re23[cc], A.re23[cc], n2);
+                    n2 = fma2(A.im23[cc], A.im23[cc], n2);
+                }
+                nrm[r] += (double)n2.x + (double)n2.y;
+            }
+            if (act >> r & 1u) SF::template store_packed<true>(out + r * P.out_rstep, g.stride, h, A);
+        }
+    }
+    pdl_trigger();
+    if (P.reduce) {
+#pragma unroll
+        for (int r = 0; r < 2; r++)
+            if (act >> r & 1u) grid_reduce(nrm[r], P.red, k0 + r, nb * gridDim.y, sb + nb * blockIdx.y);
+    }
+}
+
+template <bool DAG, int D, int TB>
+void launch_f16pipe2_tb(const HopParams& P, int site_blocks, int ny, cudaStream_t st) {
+    constexpr size_t per_thread = (size_t)D * (2 * (3 * 16 + 4) + 3 * 8);
+    auto k = hop_kernel_f16pipe2<DAG, 128, D, TB>;
+    static bool opted[64] = {};  // the larger dynamic shared memory, once per device
+    int dev = 0;
+    WL_CUDA(cudaGetDevice(&dev));
+    WL_REQUIRE(dev >= 0 && dev < 64, "device ordinal out of range");
+    if (!opted[dev]) {
+        WL_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(per_thread * TB)));
+        opted[dev] = true;
+    }
+    launch_dep_smem(k, dim3(site_blocks * (P.nrhs / 2), ny), dim3(TB), per_thread * TB, st, P);
+}
+template <bool DAG, int D>
+void launch_f16pipe2_d(const HopParams& P, int block, int site_blocks, int ny, cudaStream_t st) {
+    if (block == 64) launch_f16pipe2_tb<DAG, D, 64>(P, site_blocks, ny, st);
+    else if (block == 128) launch_f16pipe2_tb<DAG, D, 128>(P, site_blocks, ny, st);
+    else if (block == 256) launch_f16pipe2_tb<DAG, D, 256>(P, site_blocks, ny, st);
+    else throw Error(WILSON_ERR_ARG, "the pipelined F16 hop takes blocks of 64, 128 or 256 threads");
+}
+
+
 template <int SP, int GP, int R, bool DAG, int V>
 void launch_ps_v(const HopParams& P, int block, int site_blocks, int ny, cudaStream_t st) {
     constexpr int MINB = hop_variant_minb(V, SP), SPT = hop_variant_spt(V);
@@ -306,6 +479,16 @@ void launch_ps_dag(const HopParams& P, int block, int site_blocks, int ny, int v
 }
 
 }  // namespace
+
+void launch_hop_f16pipe2(const HopParams& P, int block, int site_blocks, int ny, bool dag, int variant,
+                         cudaStream_t st) {
+    WL_REQUIRE(P.nrhs >= 2 && P.nrhs % 2 == 0, "the two-RHS pipelined hop needs an even number of right-hand sides");
+    const bool d3 = variant == kHopPipe2Variant + 1;
+    if (dag) d3 ? launch_f16pipe2_d<true, 3>(P, block, site_blocks, ny, st)
+                : launch_f16pipe2_d<true, 2>(P, block, site_blocks, ny, st);
+    else d3 ? launch_f16pipe2_d<false, 3>(P, block, site_blocks, ny, st)
+            : launch_f16pipe2_d<false, 2>(P, block, site_blocks, ny, st);
+}
 
 template <int SP, int GP, int R>
 void launch_hop_ps(const HopParams& P, int block, int site_blocks, int ny, bool dag, int variant, cudaStream_t st) {

@@ -317,11 +317,12 @@ def test_slab_wait_gives_up(w, oracle_mod, monkeypatch):
 
 
 # The register-blocked multi-RHS variants (NB = 2, 2, 3, 4 right-hand sides
-# per thread; 18, 19: NB = 2 with the F16 packed projection), the link-staged
-# one (10: links in shared memory, a loop over the right-hand sides), pinned
+# per thread; 18, 19: NB = 2 with the F16 packed projection; 27, 28: the F16
+# pipeline with two right-hand sides per thread), the link-staged one (10:
+# links in shared memory, a loop over the right-hand sides), pinned
 # through WILSON_HOP_VARIANT, on 12 right-hand
 # sides (a multiple of every NB) over a lattice with a ragged last block.
-@pytest.mark.parametrize("variant", [6, 7, 8, 9, 10, 18, 19])
+@pytest.mark.parametrize("variant", [6, 7, 8, 9, 10, 18, 19, 27, 28])
 @pytest.mark.parametrize("prec", ["f32", "f16", "bf16"])
 def test_blocked_multi_rhs_variants(w, oracle_mod, monkeypatch, variant, prec):
     monkeypatch.setenv("WILSON_HOP_VARIANT", str(variant))
@@ -377,7 +378,7 @@ def test_tensor_core_multi_rhs_variant(w, oracle_mod, monkeypatch, nrhs, prec, b
         assert_parity(got[k], oracle_mod.wilson_m(U, psi[k], dims, 0.1350, CPLX_PHASES), TOL[prec], f"rhs {k}")
 
 
-@pytest.mark.parametrize("variant", [6, 8, 9, 10, 11, 18])
+@pytest.mark.parametrize("variant", [6, 8, 9, 10, 11, 18, 27])
 def test_blocked_variant_lockstep_solve(w, oracle_mod, monkeypatch, variant):
     """The lockstep multi-RHS solve on a blocked kernel: right-hand sides that
     finish early (a zero source at once) are skipped inside their group while
