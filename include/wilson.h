@@ -64,8 +64,8 @@
  *                                 (default: one block per tile)
  *   WILSON_BATCH_HOP=v:b          batched solves: the inner hop's kernel variant and
  *                                 block instead of the tuned one (0-5 with 64, 128 or
- *                                 256 threads; for F16 also 22, the pipelined
- *                                 stencil, with 64 or 128)
+ *                                 256 threads; for F16 and BF16 also 22, the
+ *                                 pipelined stencil, with 64 or 128)
  *   WILSON_BATCH_TILE=n           batch tile size (128, 256 or 512 sites) instead of
  *                                 the autotuned one
  *   WILSON_BATCH_HOST_LOOP=1      host-replayed graphs instead of device-side loops

@@ -588,12 +588,12 @@ void batch_solve(int n, const wilson_problem* probs, const SolveParams& prm, wil
         cands.push_back(c);
         if (c.variant < 3) cands64.push_back(c);
     }
-    // F16 inner hops: the pipelined stencil first, so that another candidate
+    // F16 / BF16 inner hops: the pipelined stencil first, so that another candidate
     // replaces it only when more than the tuner's margin faster (inside the
     // graph the pipelined hop wins by more than it does alone: the 64-problem
     // batch took 0.221 s with it on every class, 0.226 s on isolated choices)
     std::vector<LaunchConfig> cands_lo;
-    if (ip == P_F16)
+    if (ip == P_F16 || ip == P_BF16)
         for (int block : {64, 128}) cands_lo.push_back(LaunchConfig{block, kBatchPipeVariant});
     cands_lo.insert(cands_lo.end(), cands.begin(), cands.end());
     // WILSON_BATCH_HOP=v:block pins the inner hop's launch (one of cands_lo)

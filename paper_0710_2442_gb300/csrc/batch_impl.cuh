@@ -654,12 +654,12 @@ __global__ void __cluster_dims__(kSmallCluster, 1, 1) __launch_bounds__(kSmallTh
     small_solve_body<IP, kSmallCluster>(A, ids, G, budget_ns);
 }
 
-// The batched hop of F16 storage on the pipelined site (f16pipe_site): each
-// thread copies the next hops' raw data into its own shared-memory slots
+// The batched hop of F16 / BF16 storage on the pipelined site (pipe_site):
+// each thread copies the next hops' raw data into its own shared-memory slots
 // (batch variant 22; TB threads per block, D hops ahead, NREG registers).
-template <bool DAG, int NREG, int D, int TB>
+template <int SP, bool DAG, int NREG, int D, int TB>
 __global__ void __launch_bounds__(TB) __maxnreg__(NREG) bhop_kernel_pipe(const BatchArgs A, const BOp op) {
-    using SF = SpinorFmt<P_F16>;
+    using SF = SpinorFmt<SP>;
     extern __shared__ __align__(16) unsigned char bpipe_smem[];
     uint4* sp = reinterpret_cast<uint4*>(bpipe_smem);      // [D][3][TB] spinor chunks
     uint2* lk = reinterpret_cast<uint2*>(sp + D * 3 * TB);  // [D][3][TB] link chunks
@@ -680,7 +680,7 @@ __global__ void __launch_bounds__(TB) __maxnreg__(NREG) bhop_kernel_pipe(const B
             const int h = h0 + j;
             if (h >= g.Vh) break;
             PSpinor acc;
-            f16pipe_site<DAG, D, TB>(acc, in, Pr.glo, g, p, h, sp, lk, scs, threadIdx.x);
+            pipe_site<SP, DAG, D, TB>(acc, in, Pr.glo, g, p, h, sp, lk, scs, threadIdx.x);
             if (x) {
                 PSpinor xq;
                 float xs;
@@ -723,9 +723,9 @@ __global__ void __launch_bounds__(TB) __maxnreg__(NREG) bhop_kernel_pipe(const B
 // launchers (instantiated in their own translation units)
 // ---------------------------------------------------------------------------
 // Batched hop: variants 0-2 the scalar stencil (register budgets), 3-5 the
-// paired-FP32 stencil (F32 / F16 / BF16 spinors only), 22 the pipelined F16
-// stencil (64- or 128-thread blocks).
-constexpr int kBatchPipeVariant = 22;  // the pipelined F16 stencil (as hop variant 22)
+// paired-FP32 stencil (F32 / F16 / BF16 spinors only), 22 the pipelined
+// F16 / BF16 stencil (64- or 128-thread blocks).
+constexpr int kBatchPipeVariant = 22;  // the pipelined F16 / BF16 stencil (as hop variant 22)
 constexpr int kBatchPipeDepth = 3;     // hops copied ahead
 template <int SP, int GP>
 void launch_bhop(const BatchArgs& A, const BOp& o, int dag, int v, int block, int blocks, cudaStream_t st) {
@@ -736,16 +736,17 @@ void launch_bhop(const BatchArgs& A, const BOp& o, int dag, int v, int block, in
 #define WL_BHOP_P(V)                                                                                      \
     if (dag) bhop_kernel_p<SP, GP, 12, true, hop_variant_minb(V, SP)><<<blocks, block, 0, st>>>(A, o);  \
     else bhop_kernel_p<SP, GP, 12, false, hop_variant_minb(V, SP)><<<blocks, block, 0, st>>>(A, o);
-    if constexpr (SP == P_F16 && GP == P_F16) {
+    if constexpr ((SP == P_F16 || SP == P_BF16) && GP == SP) {
         if (v == kBatchPipeVariant) {
             constexpr size_t per_thread = (size_t)kBatchPipeDepth * (3 * 16 + 3 * 8 + 4);
+            constexpr int D = kBatchPipeDepth;
             if (block == 64) {
-                if (dag) bhop_kernel_pipe<true, 96, kBatchPipeDepth, 64><<<blocks, 64, per_thread * 64, st>>>(A, o);
-                else bhop_kernel_pipe<false, 96, kBatchPipeDepth, 64><<<blocks, 64, per_thread * 64, st>>>(A, o);
+                if (dag) bhop_kernel_pipe<SP, true, 96, D, 64><<<blocks, 64, per_thread * 64, st>>>(A, o);
+                else bhop_kernel_pipe<SP, false, 96, D, 64><<<blocks, 64, per_thread * 64, st>>>(A, o);
             } else {
                 WL_REQUIRE(block == 128, "the pipelined batch hop takes 64- or 128-thread blocks");
-                if (dag) bhop_kernel_pipe<true, 96, kBatchPipeDepth, 128><<<blocks, 128, per_thread * 128, st>>>(A, o);
-                else bhop_kernel_pipe<false, 96, kBatchPipeDepth, 128><<<blocks, 128, per_thread * 128, st>>>(A, o);
+                if (dag) bhop_kernel_pipe<SP, true, 96, D, 128><<<blocks, 128, per_thread * 128, st>>>(A, o);
+                else bhop_kernel_pipe<SP, false, 96, D, 128><<<blocks, 128, per_thread * 128, st>>>(A, o);
             }
             return;
         }

@@ -35,12 +35,12 @@
 //   hop_kernel_ps  12-17 the paired stencil with 2 or 4 sites per thread, and
 //                        for F16 the projection on packed halves (dslash_spt.cu)
 //   hop_kernel_pm  18-19 the register-blocked form with the F16 packed projection
-//   hop_kernel_f16pipe 20-22 F16 with the neighbour data copied ahead (dslash_spt.cu)
+//   hop_kernel_pipe 20-22 F16/BF16 with the neighbour data copied ahead (dslash_spt.cu)
 //   hop_kernel / hop_kernel_p 23-25 with L2 prefetches of the site's links
 //                        (and neighbour spinors) when a thread takes its site
 //   hop_kernel_slab 26   t-slab streaming: neighbouring slices of a tile staged
 //                        in shared memory by bulk copies (dslash_slab.cu)
-//   hop_kernel_f16pipe2 27-28 the F16 pipeline with two right-hand sides per
+//   hop_kernel_pipe2 27-28 the same pipeline with two right-hand sides per
 //                        thread sharing each hop's link (dslash_spt.cu)
 // Multi-RHS launches of the first two run the right-hand sides of a site
 // tile as consecutive blocks.  Every kernel starts with the programmatic-
@@ -839,31 +839,44 @@ __global__ void __launch_bounds__(256, MINB) hop_kernel_rl(const HopParams P) {
     pdl_trigger();
 }
 
-// One output site of the pipelined F16 hop (hop_kernel_f16pipe, and the
+// One output site of the pipelined F16 / BF16 hop (hop_kernel_pipe, and the
 // batch's tile form): the eight hops of site h of parity p, each hop's raw
 // data -- the neighbour's three 16-byte chunks and scale, the link's three
 // 8-byte chunks -- copied with cp.async into this thread's own shared-memory
 // slots D hops ahead (sp [D][3][T], lk [D][3][T], scs [D][T]; T the block
 // size, t the thread).  Every copy group is waited for before the function
 // returns, so the slots are free for the next site.
-template <bool DAG, int J>
-__device__ __forceinline__ void f16pipe_hop(PSpinor& acc, const uint4 (&d)[3], float sc, const cpx<float> (&U)[3][3],
-                                            unsigned wrap, const Geom& g) {
+template <int SP, bool DAG, int J>
+__device__ __forceinline__ void pipe_hop(PSpinor& acc, const uint4 (&d)[3], float sc, const cpx<float> (&U)[3][3],
+                                         unsigned wrap, const Geom& g) {
     constexpr int MU = J >> 1;
     constexpr bool FWD = (J & 1) == 0;
     constexpr int SF_ = DAG ? -1 : 1;
     constexpr int S = FWD ? SF_ : -SF_;
     PHalf hh, w;
-    project_f16_packed<MU, S>(d, hh);
+    if constexpr (SP == P_F16) {
+        project_f16_packed<MU, S>(d, hh);
+    } else {  // BF16: exact conversion to FP32, projection there
+        using LT = LowT<SP>;
+        PSpinor q;
+#pragma unroll
+        for (int c = 0; c < 3; c++) {
+            q.re01[c] = LT::to_f2(d[c].x);
+            q.im01[c] = LT::to_f2(d[c].y);
+            q.re23[c] = LT::to_f2(d[c].z);
+            q.im23[c] = LT::to_f2(d[c].w);
+        }
+        project_p<MU, S>(q, hh);
+    }
     if (wrap >> J & 1u) apply_phase_p(hh, (float)g.ph[MU][0], FWD ? (float)g.ph[MU][1] : -(float)g.ph[MU][1]);
     su3_mul_p<!FWD>(U, hh, w);
     expand_p<MU, S, J == 0>(acc, w, sc);
 }
 
-template <bool DAG, int D, int T>
-__device__ __forceinline__ void f16pipe_site(PSpinor& acc, const char* in, const char* gauge, const Geom& g, int p,
-                                             int h, uint4* sp, uint2* lk, float* scs, int t) {
-    using GF = GaugeFmt<P_F16, 12>;
+template <int SP, bool DAG, int D, int T>
+__device__ __forceinline__ void pipe_site(PSpinor& acc, const char* in, const char* gauge, const Geom& g, int p,
+                                          int h, uint4* sp, uint2* lk, float* scs, int t) {
+    using GF = GaugeFmt<SP, 12>;
     const int pin = 1 - p;
     const float* gscale = reinterpret_cast<const float*>(in + 48LL * g.stride);
     int hn[8];
@@ -907,7 +920,7 @@ __device__ __forceinline__ void f16pipe_site(PSpinor& acc, const char* in, const
         const float sc = scs[slot * T + t];                                                                   \
         cpx<float> U[3][3];                                                                                   \
         GF::decode(&lk[slot * 3 * T + t], T, U);                                                              \
-        f16pipe_hop<DAG, (J)>(acc, d, sc, U, wrap, g);                                                        \
+        pipe_hop<SP, DAG, (J)>(acc, d, sc, U, wrap, g);                                                       \
         if ((J) + D < 8) issue((J) + D);                                                                      \
         else __pipeline_commit();                                                                             \
     }
@@ -930,8 +943,8 @@ __device__ __forceinline__ void f16pipe_site(PSpinor& acc, const char* in, const
 // per thread (15, 16, 17: 128, 85, 64 registers).
 // v = 18, 19: the register-blocked kernel (NB = 2) with the F16 packed
 // projection at 128 and 255 registers (at 85 it spills 1.2 KB).
-// v = 20-22: the F16 kernel with its neighbour data copied ahead into shared
-// memory (cp.async), 2 / 3 / 3 hops ahead at 80 / 80 / 96 registers.
+// v = 20-22: the F16 / BF16 kernel with its neighbour data copied ahead into
+// shared memory (cp.async), 2 / 3 / 3 hops ahead at 80 / 80 / 96 registers.
 // v = 23-25: the kernels of v = 0 and 3 at 128 registers with L2 prefetches
 // of the site's links at its start (23: scalar, 24: paired) and of its links
 // and neighbour spinors (25: paired); single and reduced precision.
@@ -939,7 +952,7 @@ __device__ __forceinline__ void f16pipe_site(PSpinor& acc, const char* in, const
 // swept along t, the neighbouring input slices staged in shared memory by
 // bulk asynchronous copies; one parity, one RHS, non-reducing launches, tiles
 // that divide the slice.
-// v = 27, 28: the pipelined F16 kernel with two right-hand sides per thread
+// v = 27, 28: the pipelined F16 / BF16 kernel with two right-hand sides per thread
 // (one link copy and decode per hop for both), 2 / 3 hops ahead at 128
 // registers; even nrhs.
 constexpr int kHopVariants = 29;
@@ -980,8 +993,8 @@ inline bool hop_variant_valid(int v, Prec sp, int recon, int nrhs) {
     if (v < kHopBaseVariants) return true;
     if (hop_variant_is_pf(v)) return float_storage(sp);
     if (v == kHopSlabVariant) return float_storage(sp) && nrhs == 1;
-    if (hop_variant_is_pipe2(v)) return sp == P_F16 && recon == 12 && nrhs >= 2 && nrhs % 2 == 0;
-    if (hop_variant_is_pipe(v)) return sp == P_F16 && recon == 12;
+    if (hop_variant_is_pipe2(v)) return (sp == P_F16 || sp == P_BF16) && recon == 12 && nrhs >= 2 && nrhs % 2 == 0;
+    if (hop_variant_is_pipe(v)) return (sp == P_F16 || sp == P_BF16) && recon == 12;
     if (hop_variant_is_ps(v)) return hop_variant_hproj(v) ? sp == P_F16 : float_storage(sp);
     if (v == 18 || v == 19) return sp == P_F16 && recon == 12 && nrhs >= 2 && nrhs % 2 == 0;
     if (v == kHopMmaVariant) return (sp == P_F16 || sp == P_BF16) && recon == 12 && nrhs > 1;
@@ -1003,9 +1016,10 @@ void launch_hop_mma(const HopParams& P, int block, int site_blocks, int ny, bool
 // have given up since the library was loaded (synchronises the stream).
 template <int SP, int GP, int R>
 void launch_hop_slab(const HopParams& P, int block, bool dag, cudaStream_t st);
-// The two-RHS pipelined F16 kernel (dslash_spt.cu; F16-12, even nrhs).
-void launch_hop_f16pipe2(const HopParams& P, int block, int site_blocks, int ny, bool dag, int variant,
-                         cudaStream_t st);
+// The two-RHS pipelined kernel (dslash_spt.cu; F16-12 or BF16-12, even nrhs).
+template <int SP>
+void launch_hop_pipe2(const HopParams& P, int block, int site_blocks, int ny, bool dag, int variant,
+                      cudaStream_t st);
 bool hop_slab_fits(const Geom& g, int block);
 unsigned long long stage_timeouts(cudaStream_t st);
 // Sites per thread and the F16 packed projection (dslash_spt.cu; F32/F16/BF16).
@@ -1075,11 +1089,11 @@ void launch_hop_prec(const HopParams& P, int block, int site_blocks, int ny, boo
         throw Error(7, "the slab hop variant needs F32/F16/BF16 spinors");
     }
     if (hop_variant_is_pipe2(variant)) {
-        if constexpr (SP == P_F16 && GP == P_F16 && R == 12) {
-            launch_hop_f16pipe2(P, block, site_blocks, ny, dag, variant, st);
+        if constexpr ((SP == P_F16 || SP == P_BF16) && GP == SP && R == 12) {
+            launch_hop_pipe2<SP>(P, block, site_blocks, ny, dag, variant, st);
             return;
         }
-        throw Error(7, "the two-RHS pipelined hop variants need F16 spinors and 12-real links");
+        throw Error(7, "the two-RHS pipelined hop variants need F16/BF16 spinors and 12-real links");
     }
     if (hop_variant_is_pf(variant)) {
         if constexpr (float_storage(SP)) {

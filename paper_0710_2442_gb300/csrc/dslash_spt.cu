@@ -161,27 +161,28 @@ __global__ void __launch_bounds__(256, MINB) hop_kernel_ps(const HopParams P) {
 }
 
 // ---------------------------------------------------------------------------
-// F16 hop with the neighbour data copied ahead into shared memory (variants
-// 20-22: 2 / 3 / 3 hops ahead at 80 / 80 / 96 registers).  The F16 hop's
+// F16 / BF16 hop with the neighbour data copied ahead into shared memory
+// (variants 20-22: 2 / 3 / 3 hops ahead at 80 / 80 / 96 registers).  The F16 hop's
 // exact loads alone run at 0.93 of the copy bandwidth, the packed-projection
 // kernel at 0.6: its arithmetic waits on loads it cannot keep in flight at
 // the occupancy its registers allow.  Here each thread issues the raw data
 // of a hop (3 spinor chunks, the scale, 3 link chunks) with asynchronous
 // copies (cp.async) into its own shared-memory slots, D hops ahead, so the
-// loads in flight hold no registers (f16pipe_site, shared with the batch's
+// loads in flight hold no registers (pipe_site, shared with the batch's
 // tile kernel).  Before computing hop j the thread waits for that hop's copy
 // group (a hardware wait, no spin); after computing it, it reuses the slot
 // for hop j + D.  Slots are laid out [slot][chunk][thread] (conflict-free
 // warp accesses); a thread reads only what it copied, so no barrier is
-// needed.  The arithmetic is that of the packed-projection kernel.  A thread
+// needed.  The arithmetic is that of the packed-projection kernel for F16,
+// of the paired kernel for BF16 (exact conversion, projection in FP32).  A thread
 // past the lattice's end runs site 0 and stores nothing, so the warp does
 // not diverge inside the pipeline.
 // ---------------------------------------------------------------------------
 // TB: the block size (the launch's blockDim.x), a compile-time constant so
 // that every slot offset is an immediate; NREG: the register budget.
-template <bool DAG, int NREG, int D, int TB>
-__global__ void __launch_bounds__(TB) __maxnreg__(NREG) hop_kernel_f16pipe(const HopParams P) {
-    using SF = SpinorFmt<P_F16>;
+template <int SP, bool DAG, int NREG, int D, int TB>
+__global__ void __launch_bounds__(TB) __maxnreg__(NREG) hop_kernel_pipe(const HopParams P) {
+    using SF = SpinorFmt<SP>;
     extern __shared__ __align__(16) unsigned char pipe_smem[];
     constexpr int T = TB;
     const int t = threadIdx.x;
@@ -205,7 +206,7 @@ __global__ void __launch_bounds__(TB) __maxnreg__(NREG) hop_kernel_f16pipe(const
         const bool ok = h0 < g.Vh;
         const int h = ok ? h0 : 0;
         PSpinor acc;
-        f16pipe_site<DAG, D, T>(acc, in, P.gauge, g, p, h, sp, lk, scs, t);
+        pipe_site<SP, DAG, D, T>(acc, in, P.gauge, g, p, h, sp, lk, scs, t);
         if (!ok) continue;
         if (P.xpay) {
             PSpinor xq;
@@ -247,11 +248,11 @@ __global__ void __launch_bounds__(TB) __maxnreg__(NREG) hop_kernel_f16pipe(const
     if (P.reduce) grid_reduce(nrm, P.red, k, nb * gridDim.y, sb + nb * blockIdx.y);
 }
 
-template <bool DAG, int V, int TB>
-void launch_f16pipe_tb(const HopParams& P, int site_blocks, int ny, cudaStream_t st) {
+template <int SP, bool DAG, int V, int TB>
+void launch_pipe_tb(const HopParams& P, int site_blocks, int ny, cudaStream_t st) {
     constexpr int NREG = V == 22 ? 96 : 80, D = V == 20 ? 2 : 3;
     constexpr size_t per_thread = (size_t)D * (3 * 16 + 3 * 8 + 4);
-    auto k = hop_kernel_f16pipe<DAG, NREG, D, TB>;
+    auto k = hop_kernel_pipe<SP, DAG, NREG, D, TB>;
     static bool opted[64] = {};  // the larger dynamic shared memory, once per device
     int dev = 0;
     WL_CUDA(cudaGetDevice(&dev));
@@ -262,26 +263,26 @@ void launch_f16pipe_tb(const HopParams& P, int site_blocks, int ny, cudaStream_t
     }
     launch_dep_smem(k, dim3(site_blocks * P.nrhs, ny), dim3(TB), per_thread * TB, st, P);
 }
-template <bool DAG, int V>
-void launch_f16pipe_v(const HopParams& P, int block, int site_blocks, int ny, cudaStream_t st) {
-    if (block == 64) launch_f16pipe_tb<DAG, V, 64>(P, site_blocks, ny, st);
-    else if (block == 128) launch_f16pipe_tb<DAG, V, 128>(P, site_blocks, ny, st);
-    else if (block == 256) launch_f16pipe_tb<DAG, V, 256>(P, site_blocks, ny, st);
+template <int SP, bool DAG, int V>
+void launch_pipe_v(const HopParams& P, int block, int site_blocks, int ny, cudaStream_t st) {
+    if (block == 64) launch_pipe_tb<SP, DAG, V, 64>(P, site_blocks, ny, st);
+    else if (block == 128) launch_pipe_tb<SP, DAG, V, 128>(P, site_blocks, ny, st);
+    else if (block == 256) launch_pipe_tb<SP, DAG, V, 256>(P, site_blocks, ny, st);
     else throw Error(WILSON_ERR_ARG, "the pipelined F16 hop takes blocks of 64, 128 or 256 threads");
 }
 
-// Two right-hand sides per thread on the pipelined F16 stencil (variants 27,
-// 28).  A thread computes one site for right-hand sides k0 and k0 + 1: per
+// Two right-hand sides per thread on the pipelined F16 / BF16 stencil
+// (variants 27, 28).  A thread computes one site for right-hand sides k0 and k0 + 1: per
 // hop it copies the link once and both neighbour spinors (chunks and scales)
 // into its slots, decodes the link once and applies it to both, so the link's
 // copy, conversion and third-row reconstruction are shared.  Slots: spinor
 // chunks [D][2][3][T], scales [D][2][T], link chunks [D][3][T].  Skip flags,
 // the epilogue and the per-RHS reductions as in hop_kernel_pm.
-template <bool DAG, int D, int T>
-__device__ __forceinline__ void f16pipe2_site(PSpinor (&acc)[2], const char* in0, long long rstep,
+template <int SP, bool DAG, int D, int T>
+__device__ __forceinline__ void pipe2_site(PSpinor (&acc)[2], const char* in0, long long rstep,
                                               const char* gauge, const Geom& g, int p, int h, uint4* sp, uint2* lk,
                                               float* scs, int t) {
-    using GF = GaugeFmt<P_F16, 12>;
+    using GF = GaugeFmt<SP, 12>;
     const int pin = 1 - p;
     int hn[8];
     unsigned wrap = 0;
@@ -329,7 +330,7 @@ __device__ __forceinline__ void f16pipe2_site(PSpinor (&acc)[2], const char* in0
         _Pragma("unroll") for (int r = 0; r < 2; r++) {                                                         \
             uint4 d[3];                                                                                         \
             _Pragma("unroll") for (int kk = 0; kk < 3; kk++) d[kk] = sp[((slot * 2 + r) * 3 + kk) * T + t];     \
-            f16pipe_hop<DAG, (J)>(acc[r], d, scs[(slot * 2 + r) * T + t], U, wrap, g);                          \
+            pipe_hop<SP, DAG, (J)>(acc[r], d, scs[(slot * 2 + r) * T + t], U, wrap, g);                         \
         }                                                                                                       \
         if ((J) + D < 8) issue((J) + D);                                                                        \
         else __pipeline_commit();                                                                               \
@@ -339,9 +340,9 @@ __device__ __forceinline__ void f16pipe2_site(PSpinor (&acc)[2], const char* in0
 #undef WL_PIPE2_HOP
 }
 
-template <bool DAG, int NREG, int D, int TB>
-__global__ void __launch_bounds__(TB) __maxnreg__(NREG) hop_kernel_f16pipe2(const HopParams P) {
-    using SF = SpinorFmt<P_F16>;
+template <int SP, bool DAG, int NREG, int D, int TB>
+__global__ void __launch_bounds__(TB) __maxnreg__(NREG) hop_kernel_pipe2(const HopParams P) {
+    using SF = SpinorFmt<SP>;
     extern __shared__ __align__(16) unsigned char pipe2_smem[];
     constexpr int T = TB;
     const int t = threadIdx.x;
@@ -371,7 +372,7 @@ __global__ void __launch_bounds__(TB) __maxnreg__(NREG) hop_kernel_f16pipe2(cons
         const bool ok = h0 < g.Vh;
         const int h = ok ? h0 : 0;
         PSpinor acc[2];
-        f16pipe2_site<DAG, D, T>(acc, in, P.in_rstep, P.gauge, g, p, h, sp, lk, scs, t);
+        pipe2_site<SP, DAG, D, T>(acc, in, P.in_rstep, P.gauge, g, p, h, sp, lk, scs, t);
         if (!ok) continue;
 #pragma unroll
         for (int r = 0; r < 2; r++) {
@@ -420,10 +421,10 @@ __global__ void __launch_bounds__(TB) __maxnreg__(NREG) hop_kernel_f16pipe2(cons
     }
 }
 
-template <bool DAG, int D, int TB>
-void launch_f16pipe2_tb(const HopParams& P, int site_blocks, int ny, cudaStream_t st) {
+template <int SP, bool DAG, int D, int TB>
+void launch_pipe2_tb(const HopParams& P, int site_blocks, int ny, cudaStream_t st) {
     constexpr size_t per_thread = (size_t)D * (2 * (3 * 16 + 4) + 3 * 8);
-    auto k = hop_kernel_f16pipe2<DAG, 128, D, TB>;
+    auto k = hop_kernel_pipe2<SP, DAG, 128, D, TB>;
     static bool opted[64] = {};  // the larger dynamic shared memory, once per device
     int dev = 0;
     WL_CUDA(cudaGetDevice(&dev));
@@ -434,11 +435,11 @@ void launch_f16pipe2_tb(const HopParams& P, int site_blocks, int ny, cudaStream_
     }
     launch_dep_smem(k, dim3(site_blocks * (P.nrhs / 2), ny), dim3(TB), per_thread * TB, st, P);
 }
-template <bool DAG, int D>
-void launch_f16pipe2_d(const HopParams& P, int block, int site_blocks, int ny, cudaStream_t st) {
-    if (block == 64) launch_f16pipe2_tb<DAG, D, 64>(P, site_blocks, ny, st);
-    else if (block == 128) launch_f16pipe2_tb<DAG, D, 128>(P, site_blocks, ny, st);
-    else if (block == 256) launch_f16pipe2_tb<DAG, D, 256>(P, site_blocks, ny, st);
+template <int SP, bool DAG, int D>
+void launch_pipe2_d(const HopParams& P, int block, int site_blocks, int ny, cudaStream_t st) {
+    if (block == 64) launch_pipe2_tb<SP, DAG, D, 64>(P, site_blocks, ny, st);
+    else if (block == 128) launch_pipe2_tb<SP, DAG, D, 128>(P, site_blocks, ny, st);
+    else if (block == 256) launch_pipe2_tb<SP, DAG, D, 256>(P, site_blocks, ny, st);
     else throw Error(WILSON_ERR_ARG, "the pipelined F16 hop takes blocks of 64, 128 or 256 threads");
 }
 
@@ -467,28 +468,31 @@ void launch_ps_dag(const HopParams& P, int block, int site_blocks, int ny, int v
         case 20:
         case 21:
         case 22:
-            if constexpr (SP == P_F16 && GP == P_F16 && R == 12) {
-                if (variant == 20) launch_f16pipe_v<DAG, 20>(P, block, site_blocks, ny, st);
-                else if (variant == 21) launch_f16pipe_v<DAG, 21>(P, block, site_blocks, ny, st);
-                else launch_f16pipe_v<DAG, 22>(P, block, site_blocks, ny, st);
+            if constexpr ((SP == P_F16 || SP == P_BF16) && GP == SP && R == 12) {
+                if (variant == 20) launch_pipe_v<SP, DAG, 20>(P, block, site_blocks, ny, st);
+                else if (variant == 21) launch_pipe_v<SP, DAG, 21>(P, block, site_blocks, ny, st);
+                else launch_pipe_v<SP, DAG, 22>(P, block, site_blocks, ny, st);
                 break;
             }
-            throw Error(7, "the pipelined hop variants need F16 spinors and 12-real links");
+            throw Error(7, "the pipelined hop variants need F16/BF16 spinors and 12-real links");
         default: throw Error(7, "unknown sites-per-thread hop variant");
     }
 }
 
 }  // namespace
 
-void launch_hop_f16pipe2(const HopParams& P, int block, int site_blocks, int ny, bool dag, int variant,
-                         cudaStream_t st) {
+template <int SP>
+void launch_hop_pipe2(const HopParams& P, int block, int site_blocks, int ny, bool dag, int variant,
+                      cudaStream_t st) {
     WL_REQUIRE(P.nrhs >= 2 && P.nrhs % 2 == 0, "the two-RHS pipelined hop needs an even number of right-hand sides");
     const bool d3 = variant == kHopPipe2Variant + 1;
-    if (dag) d3 ? launch_f16pipe2_d<true, 3>(P, block, site_blocks, ny, st)
-                : launch_f16pipe2_d<true, 2>(P, block, site_blocks, ny, st);
-    else d3 ? launch_f16pipe2_d<false, 3>(P, block, site_blocks, ny, st)
-            : launch_f16pipe2_d<false, 2>(P, block, site_blocks, ny, st);
+    if (dag) d3 ? launch_pipe2_d<SP, true, 3>(P, block, site_blocks, ny, st)
+                : launch_pipe2_d<SP, true, 2>(P, block, site_blocks, ny, st);
+    else d3 ? launch_pipe2_d<SP, false, 3>(P, block, site_blocks, ny, st)
+            : launch_pipe2_d<SP, false, 2>(P, block, site_blocks, ny, st);
 }
+template void launch_hop_pipe2<P_F16>(const HopParams&, int, int, int, bool, int, cudaStream_t);
+template void launch_hop_pipe2<P_BF16>(const HopParams&, int, int, int, bool, int, cudaStream_t);
 
 template <int SP, int GP, int R>
 void launch_hop_ps(const HopParams& P, int block, int site_blocks, int ny, bool dag, int variant, cudaStream_t st) {

@@ -56,15 +56,16 @@ def test_batch_matches_oracle(w, oracle_mod, monkeypatch, inner, small_vh):
         assert 0 <= s["seconds"] <= info["device_seconds"] + 1e-6
 
 
-# WILSON_BATCH_HOP pins the inner hop of the device loop: the pipelined F16
-# stencil (variant 22, 64- and 128-thread blocks, 256-site tiles walked by
-# 4 or 2 sites per thread) and the paired stencil, on MIX through the loop.
-@pytest.mark.parametrize("hop", ["22:64", "22:128", "4:128"])
-def test_batch_inner_hop_variants(w, oracle_mod, monkeypatch, hop):
+# WILSON_BATCH_HOP pins the inner hop of the device loop: the pipelined
+# F16 / BF16 stencil (variant 22, 64- and 128-thread blocks, 256-site tiles
+# walked by 4 or 2 sites per thread) and the paired stencil, on MIX through
+# the loop.
+@pytest.mark.parametrize("hop,inner", [("22:64", "f16"), ("22:128", "f16"), ("4:128", "f16"), ("22:64", "bf16")])
+def test_batch_inner_hop_variants(w, oracle_mod, monkeypatch, hop, inner):
     monkeypatch.setenv("WILSON_BATCH_SMALL_VH", "0")
     monkeypatch.setenv("WILSON_BATCH_HOP", hop)
     probs, hf = make_batch(w, MIX)
-    rc, st, info = w.wilson_batch_solve(probs, w.solver_defaults(w.WILSON_F16))
+    rc, st, info = w.wilson_batch_solve(probs, w.solver_defaults(w.PREC[inner]))
     assert rc == 0 and not info["timed_out"] and info["tiles"] > 0
     for q, (dims, U, b, kappa), s in zip(probs, hf, st):
         assert s["status"] == 0
