@@ -35,13 +35,13 @@
 //   hop_kernel_ps  12-17 the paired stencil with 2 or 4 sites per thread, and
 //                        for F16 the projection on packed halves (dslash_spt.cu)
 //   hop_kernel_pm  18-19 the register-blocked form with the F16 packed projection
-//   hop_kernel_pipe 20-22 F16/BF16 with the neighbour data copied ahead (dslash_spt.cu)
+//   hop_kernel_pipe 20-22 F16/BF16 with the neighbour data copied ahead (dslash_pipe.cuh)
 //   hop_kernel / hop_kernel_p 23-25 with L2 prefetches of the site's links
 //                        (and neighbour spinors) when a thread takes its site
 //   hop_kernel_slab 26   t-slab streaming: neighbouring slices of a tile staged
 //                        in shared memory by bulk copies (dslash_slab.cu)
 //   hop_kernel_pipe2 27-28 the same pipeline with two right-hand sides per
-//                        thread sharing each hop's link (dslash_spt.cu)
+//                        thread sharing each hop's link (dslash_pipe.cuh)
 // Multi-RHS launches of the first two run the right-hand sides of a site
 // tile as consecutive blocks.  Every kernel starts with the programmatic-
 // dependent-launch wait, so it can be launched with that attribute.
@@ -1016,10 +1016,19 @@ void launch_hop_mma(const HopParams& P, int block, int site_blocks, int ny, bool
 // have given up since the library was loaded (synchronises the stream).
 template <int SP, int GP, int R>
 void launch_hop_slab(const HopParams& P, int block, bool dag, cudaStream_t st);
-// The two-RHS pipelined kernel (dslash_spt.cu; F16-12 or BF16-12, even nrhs).
+// The pipelined kernels (dslash_pipe.cuh, instantiated in dslash_pipe_f16.cu
+// and dslash_pipe_bf16.cu; F16-12 or BF16-12): one right-hand side per thread
+// (variants 20-22) and two (27, 28; even nrhs).
+template <int SP>
+void launch_hop_pipe(const HopParams& P, int block, int site_blocks, int ny, bool dag, int variant,
+                     cudaStream_t st);
 template <int SP>
 void launch_hop_pipe2(const HopParams& P, int block, int site_blocks, int ny, bool dag, int variant,
                       cudaStream_t st);
+extern template void launch_hop_pipe<P_F16>(const HopParams&, int, int, int, bool, int, cudaStream_t);
+extern template void launch_hop_pipe<P_BF16>(const HopParams&, int, int, int, bool, int, cudaStream_t);
+extern template void launch_hop_pipe2<P_F16>(const HopParams&, int, int, int, bool, int, cudaStream_t);
+extern template void launch_hop_pipe2<P_BF16>(const HopParams&, int, int, int, bool, int, cudaStream_t);
 bool hop_slab_fits(const Geom& g, int block);
 unsigned long long stage_timeouts(cudaStream_t st);
 // Sites per thread and the F16 packed projection (dslash_spt.cu; F32/F16/BF16).
