@@ -14,21 +14,21 @@ namespace {
 
 // ---------------------------------------------------------------------------
 // F16 / BF16 hop with the neighbour data copied ahead into shared memory
-// (variants 20-22: 2 / 3 / 3 hops ahead at 80 / 80 / 96 registers).  The F16 hop's
-// exact loads alone run at 0.93 of the copy bandwidth, the packed-projection
-// kernel at 0.6: its arithmetic waits on loads it cannot keep in flight at
-// the occupancy its registers allow.  Here each thread issues the raw data
-// of a hop (3 spinor chunks, the scale, 3 link chunks) with asynchronous
+// (variants 20-22: 2 / 3 / 3 hops ahead at 80 / 80 / 96 registers).  The F16
+// hop's exact loads alone run at 0.93 of the copy bandwidth, the packed-
+// projection kernel at 0.6: its arithmetic waits on loads it cannot keep in
+// flight at the occupancy its registers allow.  Here each thread issues the raw
+// data of a hop (3 spinor chunks, the scale, 3 link chunks) with asynchronous
 // copies (cp.async) into its own shared-memory slots, D hops ahead, so the
-// loads in flight hold no registers (pipe_site, shared with the batch's
-// tile kernel).  Before computing hop j the thread waits for that hop's copy
-// group (a hardware wait, no spin); after computing it, it reuses the slot
-// for hop j + D.  Slots are laid out [slot][chunk][thread] (conflict-free
-// warp accesses); a thread reads only what it copied, so no barrier is
-// needed.  The arithmetic is that of the packed-projection kernel for F16,
-// of the paired kernel for BF16 (exact conversion, projection in FP32).  A thread
-// past the lattice's end runs site 0 and stores nothing, so the warp does
-// not diverge inside the pipeline.
+// loads in flight hold no registers (pipe_site, shared with the batch's tile
+// kernel).  Before computing hop j the thread waits for that hop's copy group
+// (a hardware wait, no spin); after computing it, it reuses the slot for
+// hop j + D.  Slots are laid out [slot][chunk][thread] (conflict-free warp accesses);
+// a thread reads only what it copied, so no barrier is needed.  The arithmetic
+// is that of the packed-projection kernel for F16, of the paired kernel for
+// BF16 (exact conversion, projection in FP32).  A thread past the lattice's end
+// runs site 0 and stores nothing, so the warp does not diverge inside the
+// pipeline.
 // ---------------------------------------------------------------------------
 // TB: the block size (the launch's blockDim.x), a compile-time constant so
 // that every slot offset is an immediate; NREG: the register budget.
