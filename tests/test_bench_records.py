@@ -39,3 +39,16 @@ def test_oracle_solution_check_record(oracle_mod):
     assert good["oracle"]["true_rel_resid_max"] <= 1e-10
     assert good["oracle"]["rel_diff_vs_fp64_gpu_solution"] == 0.0
     assert bad["oracle"]["true_rel_resid_max"] > 1e-4
+
+
+def test_access_pattern_record_arithmetic():
+    """The access-pattern record: T_mem is the compulsory bytes at the copy
+    bandwidth, and the two ratios compare the probe with T_mem and the hop
+    with the probe (the headline's figures: 604 MB, 6791.7 GB/s)."""
+    byts = 576 * 1048576
+    rec = bench.access_record(byts, 88.0e-6, 89.9e-6, 6791.7)
+    assert abs(rec["t_mem_us"] - byts / 6791.7e9 * 1e6) < 0.01
+    assert abs(rec["access_over_t_mem"] - 88.0 / rec["t_mem_us"]) < 2e-3
+    assert abs(rec["hop_over_access"] - 89.9 / 88.0) < 1e-3
+    assert abs(rec["frac"] - byts / 88.0e-6 / 1e9 / 6791.7) < 1e-4
+    assert rec["us"] == 88.0 and rec["hop_us"] == 89.9
